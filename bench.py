@@ -1,0 +1,352 @@
+"""Benchmark of the GB300 GSPM step: GSPM steps/s on the 3M-node void + cuboids mesh.
+
+One "step" = one full GSPM time step (volume averages, both RHS assemblies, magnetostatic and
+mechanical CG, strain/field recovery, seven GSPM CG solves, projection) through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 (torchrun) runs independent replicas of the single-mesh
+step, one per GPU (the single-mesh path has no independent units to shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GSPM steps/s at 3M nodes, mixed+learned vs plain FP64 on 1 GB300; % HBM peak"
+FALLBACK_HBM = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def _workload(args):
+    from paper_2510_09812_gb300 import synth
+    if args.cells:
+        c = tuple(int(v) for v in args.cells.split(","))
+        h = 1024.0 / 228.0
+        return synth.void_cuboids_box(n_cells=c, box=tuple(v * h for v in c))
+    return synth.void_cuboids_box()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nme, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _kernel_src_hash():
+    with open(os.path.join(ROOT, "paper_2510_09812_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this kernel
+    source; else None."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for fn in sorted(os.listdir(d)):
+        if not fn.startswith(kernel) or workload not in fn:
+            continue
+        txt = open(os.path.join(d, fn)).read()
+        h = re.search(r"kernels_sha256:\s*([0-9a-f]+)", txt)
+        b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+        if h and b and h.group(1) == _kernel_src_hash():
+            return float(b.group(1))
+    return None
+
+
+def cpu_oracle_sample(wall_budget=25.0, steps=None, warmup=1):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload: a mesh built
+    with the same recipe (h, jitter, void + cuboids generator) but 40x40x10 cubes.  Returns
+    (steps/s scaled to the full mesh by node count, seconds per sample step, description)."""
+    from paper_2510_09812_gb300 import synth
+    from oracle.gspm import System
+    from oracle.mesh import WrappedMesh
+    h = 1024.0 / 228.0
+    cells = (40, 40, 10)
+    cfg = synth.void_cuboids_box(n_cells=cells, box=tuple(v * h for v in cells))
+    full_n = 228 * 228 * 57
+    wm = WrappedMesh.from_synth(cfg["mesh"])
+    s = System(wm, cfg["material"], cfg["dt"], cfg["alpha"])
+    m = np.array(cfg["m0"])
+    m[~s.mag] = 0.0
+    U, u = np.zeros(wm.n), np.zeros((wm.n, 3))
+    for _ in range(warmup):
+        m, U, u, _ = s.step(m, U, u, cfg["H"])
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        m, U, u, _ = s.step(m, U, u, cfg["H"])
+        k += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and k >= steps) or (steps is None and (el > wall_budget or k >= 20)):
+            break
+    per = el / k
+    desc = (f"oracle GSPM steps on the same recipe at 40x40x10 cubes ({wm.n} nodes, "
+            f"{cfg['mesh'].n_tets} tets), {k} timed after {warmup} warm-up; per-step time "
+            f"scaled by node count {wm.n}/{full_n} to the 3M-node mesh")
+    return (1.0 / per) * (wm.n / full_n), per, desc, k
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    per_steps = []
+    rate, per, desc, k = cpu_oracle_sample(steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "void_cuboids_1024x1024x256nm_2963088n", "precision": "f64",
+                       "solver": "CPU oracle (NumPy/SciPy, single thread)"},
+            "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2510_09812_gb300 import build
+    build.build()
+    from paper_2510_09812_gb300 import gspm
+
+    cfg = _workload(args)
+    mesh = cfg["mesh"]
+    H = cfg["H"]
+    peak, peak_kind = _peaks()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make(prec):
+        t0 = time.perf_counter()
+        ctx = gspm.Context(mesh, cfg["material"], cfg["dt"], cfg["alpha"], precision=prec,
+                           ordering=args.ordering, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
+        ctx.set_field(gspm.FIELD_M, cfg["m0"])
+        return ctx, time.perf_counter() - t0
+
+    def timed_steps(ctx, k, profile=("spmv_mech",)):
+        ctx.profile_enable(profile)
+        st_tot = {"it_mech": 0, "it_ms": 0, "it_gs": 0}
+        l0 = ctx.launch_count()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record()
+            for _ in range(k):
+                st = ctx.step(1, H)
+                for key in st_tot:
+                    st_tot[key] += st[key]
+            ev1.record()
+            barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = ctx.launch_count() - l0
+        prof = {c: ctx.profile_read(c) for c in profile}
+        ctx.profile_enable(())
+        return ms, st_tot, launches, prof, clk.summary()
+
+    precision = args.precision
+    ctx, t_load = make(precision)
+    info = ctx.info()
+    n = info["n_unique"]
+    for _ in range(args.warmup):
+        ctx.step(1, H)
+    ms, st, launches, prof, clocks = timed_steps(ctx, args.steps)
+    t_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * args.steps / (t_max / 1000.0)
+
+    # roofline of the dominant kernel: 3x3-block SELL SpMV of the mechanical CG
+    w = 4 if precision == "mixed" else 8
+    bytes_per_iter = (info["sell_entries"] * (9 * w + 4) + ((n + 31) // 32) * 12 + n * 3 * w * 2)
+    t_spmv, n_spmv = prof["spmv_mech"]
+    achieved = bytes_per_iter * st["it_mech"] / (t_spmv / 1000.0) / 1e9 if t_spmv > 0 else None
+    wl = cfg["name"]
+    traffic = _traffic("spmv_mech", "void_cuboids_3M") if args.cells is None else None
+
+    # per-class breakdown (separate, untimed pass)
+    classes = ["spmv_mech", "spmv_gs", "spmv_ms", "cg_vec", "cg_init", "rowops", "pointwise"]
+    bms, bst, _, bprof, _ = timed_steps(ctx, max(1, min(2, args.steps)), classes)
+    breakdown = {c: round(bprof[c][0] / max(1, min(2, args.steps)), 3) for c in classes}
+
+    # end to end through the C ABI with pinned host buffers: H2D m, one step, D2H m
+    mh = torch.tensor(cfg["m0"]).pin_memory()
+    mo = torch.empty_like(mh).pin_memory()
+    ke = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.set_field(gspm.FIELD_M, mh)
+        ctx.step(1, H, stats=False)
+        ctx.get_field(gspm.FIELD_M, mo)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": n * 3 * 8,
+           "d2h_bytes_per_step": n * 3 * 8}
+    ctx.close()
+
+    # plain FP64 GPU form on the same GPU (the comparison the metric names)
+    plain = None
+    if precision != "f64" and not args.skip_plain:
+        ctx64, t_load64 = make("f64")
+        for _ in range(args.warmup):
+            ctx64.step(1, H)
+        k64 = max(1, args.steps // 2)
+        ms64, st64, l64, prof64, _ = timed_steps(ctx64, k64)
+        t64, _ = prof64["spmv_mech"]
+        b64 = (info["sell_entries"] * (9 * 8 + 4) + ((n + 31) // 32) * 12 + n * 3 * 8 * 2)
+        plain = {"value": k64 / (ms64 / 1000.0), "unit": "steps/s", "steps": k64,
+                 "ms_per_step": ms64 / k64, "it_mech_per_step": st64["it_mech"] / k64,
+                 "spmv_mech_gbs": b64 * st64["it_mech"] / (t64 / 1000.0) / 1e9 if t64 else None}
+        ctx64.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.skip_cpu:
+        rate, per, desc, k = cpu_oracle_sample()
+        cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64" if precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": wl, "nodes": n, "tets": info["n_tets"],
+                   "magnetic_nodes": info["n_magnetic_nodes"], "precision": precision,
+                   "ordering": args.ordering, "field_A_per_m": list(map(float, H)),
+                   "dt_s": cfg["dt"], "alpha": cfg["alpha"], "rtol": 1e-7,
+                   "l2": f"inputs > L2: {info['device_bytes'] / 1e9:.2f} GB resident, "
+                         "no flush needed",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "mesh_load_s": round(t_load, 2)},
+        "node_updates_per_s": value * info["n_magnetic_nodes"],
+        "cg_iterations_per_step": {k: v / args.steps for k, v in st.items()},
+        "roofline": {"bound": "hbm", "kernel": "spmv_mech (SELL-32 3x3-block SpMV + p.q)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
+                     "peak_kind": peak_kind, "bytes_per_launch": bytes_per_iter,
+                     "launches_timed": n_spmv, "iterations_timed": st["it_mech"]},
+        "breakdown_ms_per_step": breakdown,
+        "plain_f64": plain,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--ordering", default="none", choices=["none", "rcm"])
+    ap.add_argument("--cells", default=None, help="smaller mesh of the same recipe, e.g. 64,64,16")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

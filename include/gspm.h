@@ -1,0 +1,252 @@
+/*
+ * gspm.h - C ABI of the GB300 (sm_103a) finite-element GSPM micromagnetics library.
+ *
+ * The library advances the Landau-Lifshitz equation on an unstructured, periodic mesh of linear
+ * tetrahedra with the Gauss-Seidel projection method (arXiv 2510.09812, App. B, Algorithm B.1),
+ * coupled to magnetostatics (Sec. 2.1, Eq. demag, weak form (a)) and to mechanical equilibrium
+ * with magnetostrictive eigenstrain (Eq. elasticity, weak form (b), Table A.1).  Every step of the
+ * path runs in the library's own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions
+ * -----------
+ * - Every function returns an int status (GSPM_OK = 0 or one of GSPM_E*); nothing throws across
+ *   the ABI.  gspm_last_error() returns a human-readable message for the calling thread's most
+ *   recent failure.
+ * - "Node order" in this header is the library's unique-node numbering: after the periodic wrap
+ *   (Sec. 2.5) each set of matching stored nodes becomes one unique node, numbered in order of
+ *   first appearance in the stored-node array.  Internally the library may renumber nodes
+ *   (reverse Cuthill-McKee); that order never crosses the ABI.
+ * - Nodal vector fields are arrays of structures: [n_unique][3] (m, u, fields), float64.
+ * - `where` = GSPM_HOST for host pointers (the library stages the copy) or GSPM_DEVICE for device
+ *   pointers visible to the context's device.  Device-pointer calls are asynchronous on the
+ *   context's stream unless stated otherwise; host-pointer calls synchronise that stream.
+ * - The library owns all device memory it allocates; the caller owns every pointer it passes
+ *   and may free it once the call returns (host) or once the stream has passed the call (device).
+ * - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef GSPM_H
+#define GSPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GSPM_API __attribute__((visibility("default")))
+#else
+#define GSPM_API
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define GSPM_OK 0
+#define GSPM_EINVAL 1    /* bad argument (null pointer, size, enum)                            */
+#define GSPM_EMESH 2     /* invalid mesh: index out of range, det(J) <= 0, non-finite coords,
+                            a tetrahedron collapsed by the periodic wrap                        */
+#define GSPM_ENOMEM 3    /* device or host allocation failed                                    */
+#define GSPM_ECUDA 4     /* a CUDA runtime call failed (message has the CUDA error string)      */
+#define GSPM_ENOCONV 5   /* a CG solve hit max_iter; the state was still advanced (best iterate) */
+#define GSPM_ETIMEOUT 6  /* a bounded device-side wait gave up                                  */
+#define GSPM_ESTATE 7    /* call not valid for this context (e.g. host-only context)           */
+
+/* ---- enums ------------------------------------------------------------------------------ */
+#define GSPM_HOST 0
+#define GSPM_DEVICE 1
+
+#define GSPM_PREC_F64 0    /* plain double precision everywhere                               */
+#define GSPM_PREC_MIXED 1  /* FP32 matrices, SpMV, assembly and pointwise work; FP64 CG inner
+                              products, residual norms, CG iterates x and r, volume averages    */
+
+#define GSPM_ORDER_NONE 0  /* keep the unique-node numbering                                   */
+#define GSPM_ORDER_RCM 1   /* reverse Cuthill-McKee renumbering (tie-breaks documented below)  */
+
+#define GSPM_FLAG_HOST_ONLY 1u        /* build host structures only; no CUDA call is made      */
+#define GSPM_FLAG_ROW2_PRINTED 2u     /* Algorithm B.1 second row exactly as printed (m^n_1,
+                                         g^n_1) instead of the Gauss-Seidel sweep (m*_1, g*_1)  */
+
+/* ---- inputs ----------------------------------------------------------------------------- */
+typedef struct gspm_mesh_desc {
+  int64_t n_nodes;               /* stored nodes (periodic images included)                    */
+  const double* coords;          /* host, [n_nodes][3], nm                                      */
+  int64_t n_tets;
+  const int32_t* tets;           /* host, [n_tets][4], stored-node indices, det(J) > 0          */
+  const uint8_t* elem_magnetic;  /* host, [n_tets]: 1 ferromagnetic host, 0 defect; NULL = all 1 */
+  double box_lo[3], box_hi[3];   /* periodic box (nm); faces at box_hi wrap onto box_lo         */
+  double wrap_tol;               /* nm; <= 0 selects 1e-6 x the shortest element edge           */
+} gspm_mesh_desc;
+
+typedef struct gspm_material {
+  double Ms;          /* saturation magnetisation m_s, A/m                                     */
+  double A;           /* exchange coefficient, J/m                                              */
+  double K1;          /* cubic anisotropy kappa_1, J/m^3                                        */
+  double lambda100;   /* magnetostriction constants (Table A.1)                                */
+  double lambda111;
+  double C11, C12, C44;  /* cubic elastic stiffness, Pa                                         */
+  double Nd[9];       /* demagnetising tensor of the enclosing ellipsoid (row-major)           */
+  double sigma_ext[6];/* external stress, Voigt order 11,22,33,23,13,12, Pa                     */
+  double gamma0;      /* mu0 * gyromagnetic ratio, m/(A s); <= 0 selects 2.2127615e5            */
+  double mu0;         /* H/m; <= 0 selects 1.25663706212e-6                                     */
+  double l_d;         /* model length scale (m) = unit of the mesh coordinates; <= 0 -> 1e-9   */
+} gspm_material;
+
+typedef struct gspm_options {
+  int precision;      /* GSPM_PREC_*                                                           */
+  int ordering;       /* GSPM_ORDER_*                                                          */
+  double dt;          /* time step, s (Delta tau = gamma0 m_s dt)                              */
+  double alpha;       /* damping constant                                                       */
+  double rtol_gs;     /* relative residual targets of the three CG families (Sec. 3.1: 1e-7) */
+  double rtol_ms;
+  double rtol_mech;
+  int max_iter;       /* per CG solve; exceeding it returns GSPM_ENOCONV                       */
+  unsigned flags;     /* GSPM_FLAG_*                                                           */
+  void* stream;       /* cudaStream_t for all work of the context; NULL = legacy default stream */
+} gspm_options;
+
+/* ---- outputs ---------------------------------------------------------------------------- */
+typedef struct gspm_mesh_info {
+  int64_t n_stored, n_unique, n_tets, n_magnetic_nodes, n_magnetic_tets;
+  int64_t nnz;             /* node-graph nonzeros (self included)                              */
+  int64_t sell_entries;    /* padded SELL-32 entries                                           */
+  double volume;           /* V(Omega_c), nm^3                                                 */
+  double volume_magnetic;  /* V(Omega_m), nm^3                                                 */
+  double eps;              /* A* Delta tau (nm^2), operator (1 - eps Lap) of Algorithm B.1     */
+  double dtau;             /* gamma0 m_s dt                                                    */
+  int64_t device_bytes;    /* device memory held by the context                               */
+} gspm_mesh_info;
+
+typedef struct gspm_step_stats {
+  int64_t steps;           /* steps taken by the call                                          */
+  int64_t it_ms, it_mech;  /* CG iterations summed over the call                               */
+  int64_t it_gs;           /* summed over the seven GSPM solves of every step                  */
+  int it_ms_last, it_mech_last;
+  int it_gs_last[8];       /* per GSPM solve of the last step, in solve order (7 for the
+                              Gauss-Seidel sweep, 8 with GSPM_FLAG_ROW2_PRINTED)            */
+  double res_ms_last, res_mech_last;  /* final recursive relative residuals of the last step   */
+  double dm_last;          /* <|m^{n+1} - m^n|> over magnetic nodes, last step                 */
+  double m_bar[3];         /* volume average of m over Omega_c before the last step            */
+  int noconv;              /* number of solves that hit max_iter                               */
+} gspm_step_stats;
+
+/* mesh export selectors (host copies of host-side structures; see gspm_mesh_export) */
+#define GSPM_EXPORT_UNIQUE_OF_STORED 0  /* int64 [n_stored]                                    */
+#define GSPM_EXPORT_ROWPTR 1            /* int64 [n_unique + 1], unique-node order             */
+#define GSPM_EXPORT_COLS 2              /* int64 [nnz], ascending per row, unique-node order   */
+#define GSPM_EXPORT_PERM 3              /* int64 [n_unique], perm[internal] = unique index     */
+#define GSPM_EXPORT_NODE_MAGNETIC 4     /* uint8 [n_unique]                                    */
+#define GSPM_EXPORT_LUMPED_MASS 5       /* double [n_unique], M_L,i = sum_{e ni i} V_e / 4      */
+
+/* fields readable / writable with gspm_get_field / gspm_set_field (unique-node order) */
+#define GSPM_FIELD_M 0       /* [n][3] magnetisation m (non-magnetic nodes forced to 0)       */
+#define GSPM_FIELD_U 1       /* [n]    reduced magnetostatic potential U = U~/m_s (nm)         */
+#define GSPM_FIELD_DISP 2    /* [n][3] displacement u (nm)                                     */
+#define GSPM_FIELD_HD 3      /* [n][3] local demagnetising field -grad U (reduced), read only  */
+#define GSPM_FIELD_STRAIN 4  /* [n][6] total strain E, Voigt 11,22,33,23,13,12 (tensor shear), read only */
+#define GSPM_FIELD_H 5       /* [n][3] local field h(m^n) of the last step (reduced), read only */
+
+/* operators for gspm_apply (per-kernel access; y = Op x in unique-node order, host or device) */
+#define GSPM_OP_K_MS 0       /* pinned K^ms (Eq. LHS), scalar                                  */
+#define GSPM_OP_A_EPS 1      /* M + eps K over Omega_m (identity rows off Omega_m), scalar     */
+#define GSPM_OP_A_AEPS 2     /* M + alpha eps K over Omega_m, scalar                          */
+#define GSPM_OP_M 3          /* consistent mass over Omega_m (F^GS of Eq. RHS_F), scalar      */
+#define GSPM_OP_K_MECH 4     /* pinned K^mech (Eq. LHS), x and y [n][3]                        */
+#define GSPM_OP_DIV 5        /* b_i = F^ms_{ij,a} x_{j,a}: x [n][3] -> y [n] (pinned entry 0)  */
+#define GSPM_OP_GRAD 6       /* y_{i,a} = (F^ms_a x)_i / M_L,i = -(d_a x)_i: x [n] -> y [n][3] */
+
+/* ---- lifecycle -------------------------------------------------------------------------- */
+
+/* Validate the mesh, apply the periodic wrap (Sec. 2.5: a node on a maximum face is identified
+ * with the node at the matching minimum-face position through a hash map of quantised wrapped
+ * coordinates floor((x - lo)/tol + 0.5)), build the node graph, optionally renumber it (RCM: start
+ * at the unvisited node of smallest degree, lowest index on ties; breadth-first, neighbours in
+ * (degree, index) order; all components; reversed), compute element geometry, assemble
+ * K^ms, K^mech, K^GS = M + eps K, F^ms, F^mech, F^GS (Eqs. LHS, RHS_F) in SELL-32 form, pin node 0
+ * (one DOF of K^ms, three of K^mech), upload everything to the current CUDA device, and set
+ * m = 0, U = 0, u = 0.  Errors: GSPM_EINVAL (null/size), GSPM_EMESH, GSPM_ENOMEM, GSPM_ECUDA. */
+GSPM_API int gspm_mesh_load(const gspm_mesh_desc* mesh, const gspm_material* mat,
+                            const gspm_options* opt, struct gspm_ctx** out);
+
+/* Free every resource of the context (waits for its stream). NULL is a no-op. */
+GSPM_API void gspm_destroy(struct gspm_ctx* ctx);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+GSPM_API const char* gspm_last_error(void);
+
+GSPM_API int gspm_mesh_info_get(const struct gspm_ctx* ctx, gspm_mesh_info* out);
+
+/* Copy a host-side structure (GSPM_EXPORT_*) into host memory `out` of `count` elements; count
+ * must equal the structure's length.  Works on host-only contexts. */
+GSPM_API int gspm_mesh_export(const struct gspm_ctx* ctx, int what, void* out, int64_t count);
+
+/* ---- state ------------------------------------------------------------------------------ */
+
+/* Set / read a nodal field (GSPM_FIELD_*), float64, unique-node order.  Setting M forces m = 0
+ * at nodes outside Omega_m (the caller supplies unit vectors elsewhere). */
+GSPM_API int gspm_set_field(struct gspm_ctx* ctx, int field, const double* data, int where);
+GSPM_API int gspm_get_field(struct gspm_ctx* ctx, int field, double* data, int where);
+
+/* ---- the hot path ----------------------------------------------------------------------- */
+
+/* Advance n_steps GSPM steps in place under the applied field H_ext (A/m, host array of 3).
+ * One step (App. B, Algorithm B.1, with Sec. 2.1-2.4):
+ *   m_bar (Sec. 2.4) -> b^ms = F^ms m (Eq. RHS_b) -> CG on pinned K^ms, x0 = previous U
+ *   -> h~_d = -grad U (F^ms / lumped mass) -> E0(m) (Table A.1), E_bar = <E0> + C^-1 sigma_ext
+ *   -> b^mech = F^mech E0 -> CG on pinned K^mech, x0 = previous u -> E = E_bar + sym grad u
+ *   -> h(m^n) = h_anis + H/m_s + h_me + h~_d - N_d m_bar
+ *   -> Gauss-Seidel stages with (M + eps K) g = M f (x0 = f), giving m*
+ *   -> h(m*) (local terms and far field at m*, h~_d and E held) -> (M + alpha eps K) m** = M f
+ *   -> m = m** / |m**| on magnetic nodes.
+ * stats may be NULL (then the call may return before the GPU finishes, except for the
+ * convergence checks of the CG loops, which read one flag per solve).  Returns GSPM_ENOCONV if
+ * any solve hit max_iter (the state is still advanced). */
+GSPM_API int gspm_step(struct gspm_ctx* ctx, int n_steps, const double H_ext[3],
+                       gspm_step_stats* stats);
+
+/* Mechanical equilibrium alone (steps E0 .. strain of gspm_step) for magnetisation m ([n][3],
+ * `where`); writes the displacement to u ([n][3], `where`, may be NULL) and keeps it as the
+ * context's u.  x0_mode: 0 = zero, 1 = the context's previous u, 2 = the array x0 ([n][3],
+ * `where`).  rtol <= 0 uses the context's rtol_mech.  iters / relres may be NULL.  Does not change
+ * the context's m.  Synchronises the stream. */
+GSPM_API int gspm_solve_elastic(struct gspm_ctx* ctx, const double* m, double* u, int where,
+                                int x0_mode, const double* x0, double rtol, int* iters,
+                                double* relres);
+
+/* Volume average over Omega_c (Sec. 2.4) of a nodal field with ncomp (1..9) interleaved
+ * components, [n][ncomp] float64 at `where`; result in out_host[ncomp].  Quadrature of the P1
+ * interpolant: sum_e V_e (1/4) sum_{k in e} g_k / V = sum_i (M_L,i / V) g_i.  FP64 accumulation
+ * with a fixed reduction order (bitwise reproducible for a given device).  Synchronises. */
+GSPM_API int gspm_volume_avg(struct gspm_ctx* ctx, const double* field, int where, int ncomp,
+                             double* out_host);
+
+/* y = Op x for one assembled operator (GSPM_OP_*), in the context's precision.  Synchronises
+ * when where = GSPM_HOST. */
+GSPM_API int gspm_apply(struct gspm_ctx* ctx, int op, const double* x, double* y, int where);
+
+/* Number of CUDA kernels the context has launched since creation (host-side counter). */
+GSPM_API int64_t gspm_launch_count(const struct gspm_ctx* ctx);
+
+/* ---- measurement ------------------------------------------------------------------------ */
+
+/* kernel classes for gspm_profile_* */
+#define GSPM_KCLASS_SPMV_MECH 0  /* 3x3-block SpMV + fused p.q of the mechanical CG (K^mech)  */
+#define GSPM_KCLASS_SPMV_GS 1    /* scalar multi-RHS SpMV + p.q of the GSPM CG solves         */
+#define GSPM_KCLASS_SPMV_MS 2    /* scalar SpMV + p.q of the magnetostatic CG (K^ms)          */
+#define GSPM_KCLASS_CG_VEC 3     /* CG vector updates (x, r with r.r; p)                       */
+#define GSPM_KCLASS_CG_INIT 4    /* CG start-up (residual, norms)                              */
+#define GSPM_KCLASS_ROWOPS 5     /* F^ms / G row kernels: RHS assembly, h~_d and strain        */
+#define GSPM_KCLASS_POINTWISE 6  /* E0, h(m), GSPM stages, projection, volume averages         */
+#define GSPM_KCLASS_COUNT 7
+
+/* Record CUDA events on the context's stream around every subsequent launch of the classes in
+ * class_mask (bit k = class k); 0 stops recording.  Each call clears the accumulated times. */
+GSPM_API int gspm_profile_enable(struct gspm_ctx* ctx, unsigned class_mask);
+
+/* Total device time (ms) and launch count recorded for one class since the last enable;
+ * synchronises the context's stream. */
+GSPM_API int gspm_profile_read(struct gspm_ctx* ctx, int kclass, double* total_ms,
+                               int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSPM_H */

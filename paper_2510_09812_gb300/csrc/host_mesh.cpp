@@ -1,0 +1,437 @@
+// Host mesh layer: validation, periodic wrap (Sec. 2.5), node graph, reverse Cuthill-McKee
+// renumbering, linear-tetrahedron geometry, and node-centric assembly of the FEM operators of
+// Eqs. LHS and RHS_F into SELL-32 arrays.  Runs once per mesh; parallel over rows with OpenMP
+// (each row is summed in a fixed order, so results do not depend on the thread count).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <numeric>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace gspm {
+
+int make_params(const gspm_material* m, const gspm_options* o, Params* p) {
+  if (!(m->Ms > 0) || !(o->dt > 0) || !(o->alpha >= 0) || !(m->A >= 0)) {
+    set_error("material/options: need Ms > 0, A >= 0, dt > 0, alpha >= 0");
+    return GSPM_EINVAL;
+  }
+  p->Ms = m->Ms;
+  p->mu0 = m->mu0 > 0 ? m->mu0 : 1.25663706212e-6;
+  p->gamma0 = m->gamma0 > 0 ? m->gamma0 : 2.2127615e5;
+  p->l_d = m->l_d > 0 ? m->l_d : 1e-9;
+  p->scale = p->mu0 * p->Ms * p->Ms;
+  p->A_star = 2.0 * m->A / (p->scale * p->l_d * p->l_d);
+  p->kappa = 2.0 * m->K1 / p->scale;
+  p->dtau = p->gamma0 * p->Ms * o->dt;
+  p->alpha = o->alpha;
+  p->eps = p->A_star * p->dtau;
+  p->C11 = m->C11; p->C12 = m->C12; p->C44 = m->C44;
+  p->l100 = m->lambda100; p->l111 = m->lambda111;
+  p->me_coef = 3.0 / p->scale;
+  for (int i = 0; i < 9; ++i) p->Nd[i] = m->Nd[i];
+  // E_ext = C^-1 sigma_ext for the cubic stiffness (closed-form inverse of the normal block;
+  // tensor shear strain = sigma / (2 C44))
+  const double d = (m->C11 - m->C12) * (m->C11 + 2.0 * m->C12);
+  if (!(d != 0.0) || !(m->C44 != 0.0)) {
+    set_error("material: singular elastic stiffness");
+    return GSPM_EINVAL;
+  }
+  const double S11 = (m->C11 + m->C12) / d, S12 = -m->C12 / d;
+  const double* s = m->sigma_ext;
+  p->E_ext[0] = S11 * s[0] + S12 * (s[1] + s[2]);
+  p->E_ext[1] = S11 * s[1] + S12 * (s[0] + s[2]);
+  p->E_ext[2] = S11 * s[2] + S12 * (s[0] + s[1]);
+  p->E_ext[3] = s[3] / (2.0 * m->C44);
+  p->E_ext[4] = s[4] / (2.0 * m->C44);
+  p->E_ext[5] = s[5] / (2.0 * m->C44);
+  return GSPM_OK;
+}
+
+namespace {
+
+struct Key {
+  int64_t x, y, z;
+  bool operator==(const Key& o) const { return x == o.x && y == o.y && z == o.z; }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = (uint64_t)k.x * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)k.y + 0xBF58476D1CE4E5B9ull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)k.z + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+
+// geometry of one tet from its four stored vertices: J = [x1-x0, x2-x0, x3-x0] (columns),
+// grad phi_1..3 = rows of J^-1, grad phi_0 = -sum; returns det J
+double tet_geometry(const double* x0, const double* x1, const double* x2, const double* x3,
+                    double g[12]) {
+  double J[3][3];
+  for (int a = 0; a < 3; ++a) {
+    J[a][0] = x1[a] - x0[a];
+    J[a][1] = x2[a] - x0[a];
+    J[a][2] = x3[a] - x0[a];
+  }
+  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  if (!(det > 0.0)) return det;
+  const double inv = 1.0 / det;
+  // inverse = adjugate / det; row r of J^-1 = grad phi_{r+1}
+  double Ji[3][3];
+  Ji[0][0] = c00 * inv;
+  Ji[1][0] = c01 * inv;
+  Ji[2][0] = c02 * inv;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * inv;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * inv;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * inv;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * inv;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * inv;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * inv;
+  for (int a = 0; a < 3; ++a) {
+    g[3 + a] = Ji[0][a];
+    g[6 + a] = Ji[1][a];
+    g[9 + a] = Ji[2][a];
+    g[a] = -(Ji[0][a] + Ji[1][a] + Ji[2][a]);
+  }
+  return det;
+}
+
+}  // namespace
+
+int host_mesh_build(const gspm_mesh_desc* d, int ordering, HostMesh* hm) {
+  if (!d || !d->coords || !d->tets || d->n_nodes <= 0 || d->n_tets <= 0) {
+    set_error("mesh_load: null pointer or empty mesh");
+    return GSPM_EINVAL;
+  }
+  if (d->n_nodes > INT32_MAX) {
+    set_error("mesh_load: more than 2^31-1 nodes");
+    return GSPM_EINVAL;
+  }
+  const int64_t ns = d->n_nodes, nt = d->n_tets;
+  hm->n_stored = ns;
+  hm->n_tets = nt;
+  for (int64_t i = 0; i < 3 * ns; ++i)
+    if (!std::isfinite(d->coords[i])) {
+      set_error("mesh_load: non-finite coordinate at node %lld", (long long)(i / 3));
+      return GSPM_EMESH;
+    }
+  for (int a = 0; a < 3; ++a)
+    if (!(d->box_hi[a] > d->box_lo[a])) {
+      set_error("mesh_load: empty box along axis %d", a);
+      return GSPM_EINVAL;
+    }
+  for (int64_t i = 0; i < 4 * nt; ++i)
+    if (d->tets[i] < 0 || d->tets[i] >= ns) {
+      set_error("mesh_load: tet %lld references node %d outside [0, %lld)", (long long)(i / 4),
+                d->tets[i], (long long)ns);
+      return GSPM_EMESH;
+    }
+  // geometry from stored (unwrapped) coordinates
+  hm->V.resize(nt);
+  hm->grads.resize(12 * nt);
+  double min_edge = INFINITY;
+  bool bad = false;
+  int64_t bad_tet = -1;
+#pragma omp parallel for reduction(min : min_edge)
+  for (int64_t e = 0; e < nt; ++e) {
+    const int32_t* t = d->tets + 4 * e;
+    const double* x[4] = {d->coords + 3 * (int64_t)t[0], d->coords + 3 * (int64_t)t[1],
+                          d->coords + 3 * (int64_t)t[2], d->coords + 3 * (int64_t)t[3]};
+    const double det = tet_geometry(x[0], x[1], x[2], x[3], &hm->grads[12 * e]);
+    if (!(det > 0.0)) {
+#pragma omp critical
+      {
+        if (!bad || e < bad_tet) bad_tet = e;
+        bad = true;
+      }
+    }
+    hm->V[e] = det / 6.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = i + 1; j < 4; ++j) {
+        const double dx = x[i][0] - x[j][0], dy = x[i][1] - x[j][1], dz = x[i][2] - x[j][2];
+        min_edge = std::min(min_edge, std::sqrt(dx * dx + dy * dy + dz * dz));
+      }
+  }
+  if (bad) {
+    set_error("mesh_load: tet %lld has det(J) <= 0", (long long)bad_tet);
+    return GSPM_EMESH;
+  }
+  // periodic wrap: hash map of quantised wrapped coordinates, ids by first occurrence
+  const double tol = d->wrap_tol > 0 ? d->wrap_tol : 1e-6 * min_edge;
+  hm->unique_of_stored.resize(ns);
+  {
+    std::unordered_map<Key, int64_t, KeyHash> table;
+    table.reserve((size_t)ns);
+    for (int64_t s = 0; s < ns; ++s) {
+      int64_t q[3];
+      for (int a = 0; a < 3; ++a) {
+        double x = d->coords[3 * s + a];
+        if (std::fabs(x - d->box_hi[a]) <= tol) x = d->box_lo[a];
+        q[a] = (int64_t)std::floor((x - d->box_lo[a]) / tol + 0.5);
+      }
+      auto it = table.emplace(Key{q[0], q[1], q[2]}, (int64_t)table.size()).first;
+      hm->unique_of_stored[s] = it->second;
+    }
+    hm->n = (int64_t)table.size();
+  }
+  const int64_t n = hm->n;
+  hm->tets_u.resize(4 * nt);
+  hm->elem_mag.resize(nt);
+  for (int64_t e = 0; e < nt; ++e) {
+    for (int k = 0; k < 4; ++k) hm->tets_u[4 * e + k] = hm->unique_of_stored[d->tets[4 * e + k]];
+    for (int k = 0; k < 4; ++k)
+      for (int l = k + 1; l < 4; ++l)
+        if (hm->tets_u[4 * e + k] == hm->tets_u[4 * e + l]) {
+          set_error("mesh_load: tet %lld collapses under the periodic wrap", (long long)e);
+          return GSPM_EMESH;
+        }
+    hm->elem_mag[e] = d->elem_magnetic ? (d->elem_magnetic[e] ? 1 : 0) : 1;
+  }
+  // node flags, lumped mass, volumes
+  hm->node_mag.assign(n, 0);
+  hm->ML.assign(n, 0.0);
+  hm->n_mag_tets = 0;
+  // volumes with Neumaier-compensated sums (they normalise every volume average)
+  double vs = 0.0, vc = 0.0, ms = 0.0, mc = 0.0;
+  auto nsum = [](double& s, double& c, double x) {
+    const double t = s + x;
+    c += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  };
+  for (int64_t e = 0; e < nt; ++e) {
+    nsum(vs, vc, hm->V[e]);
+    for (int k = 0; k < 4; ++k) hm->ML[hm->tets_u[4 * e + k]] += hm->V[e] / 4.0;
+    if (hm->elem_mag[e]) {
+      nsum(ms, mc, hm->V[e]);
+      ++hm->n_mag_tets;
+      for (int k = 0; k < 4; ++k) hm->node_mag[hm->tets_u[4 * e + k]] = 1;
+    }
+  }
+  hm->volume = vs + vc;
+  hm->volume_mag = ms + mc;
+  hm->n_mag_nodes = 0;
+  for (int64_t i = 0; i < n; ++i) hm->n_mag_nodes += hm->node_mag[i];
+  // node graph (self included), ascending columns
+  std::vector<int64_t> ntp(n + 1, 0), nti(4 * nt);
+  for (int64_t e = 0; e < nt; ++e)
+    for (int k = 0; k < 4; ++k) ++ntp[hm->tets_u[4 * e + k] + 1];
+  for (int64_t i = 0; i < n; ++i) ntp[i + 1] += ntp[i];
+  {
+    std::vector<int64_t> fill(ntp.begin(), ntp.end() - 1);
+    for (int64_t e = 0; e < nt; ++e)
+      for (int k = 0; k < 4; ++k) nti[fill[hm->tets_u[4 * e + k]]++] = e;
+  }
+  std::vector<std::vector<int64_t>> adj(n);
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<int64_t>& a = adj[i];
+    for (int64_t q = ntp[i]; q < ntp[i + 1]; ++q)
+      for (int k = 0; k < 4; ++k) a.push_back(hm->tets_u[4 * nti[q] + k]);
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+  }
+  hm->rowptr.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) hm->rowptr[i + 1] = hm->rowptr[i] + (int64_t)adj[i].size();
+  hm->cols.resize(hm->rowptr[n]);
+  for (int64_t i = 0; i < n; ++i)
+    std::copy(adj[i].begin(), adj[i].end(), hm->cols.begin() + hm->rowptr[i]);
+  // renumbering
+  hm->perm.resize(n);
+  if (ordering == GSPM_ORDER_RCM) {
+    std::vector<int64_t> deg(n);
+    for (int64_t i = 0; i < n; ++i) deg[i] = hm->rowptr[i + 1] - hm->rowptr[i] - 1;
+    auto less = [&](int64_t a, int64_t b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; };
+    std::vector<int64_t> by(n);
+    std::iota(by.begin(), by.end(), 0);
+    std::sort(by.begin(), by.end(), less);
+    std::vector<uint8_t> vis(n, 0);
+    std::vector<int64_t> order;
+    order.reserve(n);
+    std::deque<int64_t> q;
+    std::vector<int64_t> nxt;
+    for (int64_t st : by) {
+      if (vis[st]) continue;
+      vis[st] = 1;
+      q.push_back(st);
+      while (!q.empty()) {
+        const int64_t v = q.front();
+        q.pop_front();
+        order.push_back(v);
+        nxt.clear();
+        for (int64_t p = hm->rowptr[v]; p < hm->rowptr[v + 1]; ++p) {
+          const int64_t w = hm->cols[p];
+          if (w != v && !vis[w]) nxt.push_back(w);
+        }
+        std::sort(nxt.begin(), nxt.end(), less);
+        for (int64_t w : nxt) {
+          vis[w] = 1;
+          q.push_back(w);
+        }
+      }
+    }
+    for (int64_t i = 0; i < n; ++i) hm->perm[i] = order[n - 1 - i];
+  } else if (ordering == GSPM_ORDER_NONE) {
+    std::iota(hm->perm.begin(), hm->perm.end(), 0);
+  } else {
+    set_error("mesh_load: unknown ordering %d", ordering);
+    return GSPM_EINVAL;
+  }
+  hm->iperm.resize(n);
+  for (int64_t i = 0; i < n; ++i) hm->iperm[hm->perm[i]] = i;
+  return GSPM_OK;
+}
+
+void host_sell_build(const HostMesh& hm, HostSell* s) {
+  const int64_t n = hm.n;
+  s->n = n;
+  s->nslices = (n + kSell - 1) / kSell;
+  // internal-numbering rows: columns renumbered and re-sorted
+  s->rp.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t o = hm.perm[i];
+    s->rp[i + 1] = s->rp[i] + (hm.rowptr[o + 1] - hm.rowptr[o]);
+  }
+  s->ic.resize(s->rp[n]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t o = hm.perm[i];
+    int32_t* dst = &s->ic[s->rp[i]];
+    int64_t c = 0;
+    for (int64_t p = hm.rowptr[o]; p < hm.rowptr[o + 1]; ++p) dst[c++] = (int32_t)hm.iperm[hm.cols[p]];
+    std::sort(dst, dst + c);
+  }
+  s->sptr.assign(s->nslices + 1, 0);
+  s->slen.assign(s->nslices, 0);
+  for (int64_t sl = 0; sl < s->nslices; ++sl) {
+    int32_t mx = 0;
+    for (int64_t i = sl * kSell; i < std::min(n, (sl + 1) * kSell); ++i)
+      mx = std::max<int32_t>(mx, (int32_t)(s->rp[i + 1] - s->rp[i]));
+    s->slen[sl] = mx;
+    s->sptr[sl + 1] = s->sptr[sl] + (int64_t)mx * kSell;
+  }
+  s->entries = s->sptr[s->nslices];
+  s->col.assign(s->entries, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t sl = 0; sl < s->nslices; ++sl) {
+    for (int lane = 0; lane < kSell; ++lane) {
+      const int64_t i = sl * kSell + lane;
+      const int64_t len = i < n ? s->rp[i + 1] - s->rp[i] : 0;
+      for (int32_t k = 0; k < s->slen[sl]; ++k)
+        s->col[s->sptr[sl] + (int64_t)k * kSell + lane] =
+            k < len ? s->ic[s->rp[i] + k] : (int32_t)(i < n ? i : 0);
+    }
+  }
+}
+
+void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostOps* ops) {
+  const int64_t n = hm.n, E = s.entries;
+  ops->Kms.assign(E, 0.0);
+  ops->Aeps.assign(E, 0.0);
+  ops->Aaeps.assign(E, 0.0);
+  ops->M.assign(E, 0.0);
+  ops->F.assign(3 * E, 0.0);
+  ops->G.assign(3 * E, 0.0);
+  ops->Kmech.assign(9 * E, 0.0);
+  ops->ML.assign(n, 0.0);
+  ops->w.assign(n, 0.0);
+  ops->invML.assign(n, 0.0);
+  ops->mag.assign(n, 0);
+  ops->pin = hm.iperm[0];
+  // node -> incident tets, ascending tet index
+  std::vector<int64_t> ntp(n + 1, 0), nti(4 * hm.n_tets);
+  for (int64_t e = 0; e < hm.n_tets; ++e)
+    for (int k = 0; k < 4; ++k) ++ntp[hm.tets_u[4 * e + k] + 1];
+  for (int64_t i = 0; i < n; ++i) ntp[i + 1] += ntp[i];
+  {
+    std::vector<int64_t> fill(ntp.begin(), ntp.end() - 1);
+    for (int64_t e = 0; e < hm.n_tets; ++e)
+      for (int k = 0; k < 4; ++k) nti[fill[hm.tets_u[4 * e + k]]++] = e;
+  }
+  const double C11 = p.C11, C12 = p.C12, C44 = p.C44, eps = p.eps, aeps = p.alpha * p.eps;
+  const int64_t pin = ops->pin;
+#pragma omp parallel
+  {
+    std::vector<double> kms, km, mm, f, g, k9;
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t o = hm.perm[i];
+      const int32_t* rc = &s.ic[s.rp[i]];
+      const int len = (int)(s.rp[i + 1] - s.rp[i]);
+      kms.assign(len, 0.0); km.assign(len, 0.0); mm.assign(len, 0.0);
+      f.assign(3 * len, 0.0); g.assign(3 * len, 0.0); k9.assign(9 * len, 0.0);
+      double ml = 0.0;
+      for (int64_t q = ntp[o]; q < ntp[o + 1]; ++q) {
+        const int64_t e = nti[q];
+        const int64_t* t = &hm.tets_u[4 * e];
+        int k = 0;
+        while (t[k] != o) ++k;
+        const double V = hm.V[e];
+        const double* gk = &hm.grads[12 * e + 3 * k];
+        const bool me = hm.elem_mag[e] != 0;
+        ml += V / 4.0;
+        for (int l = 0; l < 4; ++l) {
+          const int32_t j = (int32_t)hm.iperm[t[l]];
+          int pos = 0;
+          while (rc[pos] != j) ++pos;
+          const double* gl = &hm.grads[12 * e + 3 * l];
+          const double dot = gk[0] * gl[0] + gk[1] * gl[1] + gk[2] * gl[2];
+          kms[pos] += V * dot;
+          if (me) {
+            km[pos] += V * dot;
+            mm[pos] += V * (k == l ? 2.0 : 1.0) / 20.0;
+          }
+          for (int a = 0; a < 3; ++a) {
+            f[3 * pos + a] += -(V / 4.0) * gl[a];   // -int phi_i d_a phi_j
+            g[3 * pos + a] += (V / 4.0) * gk[a];    //  int phi_j d_a phi_i
+          }
+          // cubic C: K_ab = d_ab [(C11 - C44) gk_a gl_a + C44 gk.gl] + (1 - d_ab)[C12 gk_a gl_b
+          //                + C44 gk_b gl_a]  (= sum_cd gk_c C_acbd gl_d)
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              const double v = a == b ? (C11 - C44) * gk[a] * gl[a] + C44 * dot
+                                      : C12 * gk[a] * gl[b] + C44 * gk[b] * gl[a];
+              k9[9 * pos + 3 * a + b] += V * v;
+            }
+        }
+      }
+      const int64_t sl = i / kSell, lane = i % kSell;
+      for (int pos = 0; pos < len; ++pos) {
+        const int64_t ent = s.sptr[sl] + (int64_t)pos * kSell + lane;
+        const int64_t vb = ent - lane;  // value base for B-valued matrices
+        const bool pinned = (i == pin) || (rc[pos] == pin);
+        const bool diag = rc[pos] == i;
+        ops->Kms[ent] = pinned ? (diag ? 1.0 : 0.0) : kms[pos];
+        ops->M[ent] = mm[pos];
+        ops->Aeps[ent] = mm[pos] + eps * km[pos];
+        ops->Aaeps[ent] = mm[pos] + aeps * km[pos];
+        for (int a = 0; a < 3; ++a) {
+          ops->F[vb * 3 + a * kSell + lane] = f[3 * pos + a];
+          ops->G[vb * 3 + a * kSell + lane] = g[3 * pos + a];
+        }
+        for (int b = 0; b < 9; ++b)
+          ops->Kmech[vb * 9 + b * kSell + lane] =
+              pinned ? ((diag && (b == 0 || b == 4 || b == 8)) ? 1.0 : 0.0) : k9[9 * pos + b];
+      }
+      ops->ML[i] = ml;
+      ops->w[i] = ml / hm.volume;
+      ops->invML[i] = 1.0 / ml;
+      ops->mag[i] = hm.node_mag[o];
+      if (!hm.node_mag[o]) {  // rows off Omega_m: identity in the GSPM operators
+        for (int pos = 0; pos < len; ++pos)
+          if (rc[pos] == i) {
+            const int64_t ent = s.sptr[sl] + (int64_t)pos * kSell + lane;
+            ops->Aeps[ent] = ops->Aaeps[ent] = 1.0;
+          }
+      }
+    }
+  }
+}
+
+}  // namespace gspm

@@ -1,0 +1,76 @@
+// Internal declarations of the GSPM library (host mesh layer, kernel launchers, context).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gspm.h"
+
+namespace gspm {
+
+constexpr int kSell = 32;  // SELL slice height = warp width: one thread per row, warp per slice
+
+void set_error(const char* fmt, ...);
+
+// Dimensionless constants of App. B and the material laws (SI inputs reduced once).
+struct Params {
+  double Ms, mu0, gamma0, l_d;
+  double scale;     // mu0 Ms^2
+  double A_star;    // 2A / (mu0 Ms^2 l_d^2)
+  double kappa;     // 2 K1 / (mu0 Ms^2)
+  double dtau;      // gamma0 Ms dt
+  double alpha;
+  double eps;       // A* dtau
+  double C11, C12, C44;
+  double l100, l111;
+  double me_coef;   // 3 / (mu0 Ms^2)
+  double Nd[9];
+  double E_ext[6];  // C^-1 sigma_ext, Voigt order, tensor shear components
+};
+int make_params(const gspm_material* mat, const gspm_options* opt, Params* p);
+
+// Host-side mesh after validation, periodic wrap and (optional) renumbering.
+struct HostMesh {
+  int64_t n_stored = 0, n_tets = 0, n = 0;  // n = unique nodes
+  std::vector<int64_t> unique_of_stored;     // [n_stored]
+  std::vector<int64_t> tets_u;               // [n_tets*4] unique (original) node ids
+  std::vector<uint8_t> elem_mag;             // [n_tets]
+  std::vector<double> V;                     // [n_tets]
+  std::vector<double> grads;                 // [n_tets*12], (k*3 + a) = d_a phi_k
+  std::vector<uint8_t> node_mag;             // [n] original numbering
+  std::vector<int64_t> rowptr, cols;         // node graph, original numbering, ascending
+  std::vector<int64_t> perm, iperm;          // perm[internal] = original, iperm = inverse
+  std::vector<double> ML;                    // lumped mass, original numbering
+  double volume = 0, volume_mag = 0;
+  int64_t n_mag_nodes = 0, n_mag_tets = 0;
+};
+int host_mesh_build(const gspm_mesh_desc* d, int ordering, HostMesh* hm);
+
+// SELL-32 layout of the node graph in internal numbering.  Entry e of row i (k-th column of
+// the row, ascending) sits at sptr[i/32] + k*32 + i%32.  A matrix with B values per entry stores
+// value b of entry e at (e - lane)*B + b*32 + lane (lane = i%32): all 32 rows of a slice read one
+// contiguous 32-value run per (k, b).
+struct HostSell {
+  int64_t n = 0, nslices = 0, entries = 0;
+  std::vector<int64_t> sptr;   // [nslices+1]
+  std::vector<int32_t> slen;   // [nslices]
+  std::vector<int32_t> col;    // [entries], padding points at the row itself
+  std::vector<int64_t> rp;     // internal-numbering row pointer into ic (unpadded)
+  std::vector<int32_t> ic;     // internal-numbering ascending columns
+};
+void host_sell_build(const HostMesh& hm, HostSell* s);
+
+// Assembled operators, double, SELL layout, internal numbering.
+struct HostOps {
+  std::vector<double> Kms, Aeps, Aaeps, M;  // scalar (B = 1)
+  std::vector<double> F, G;                 // B = 3: F_{ij,a} = -int phi_i d_a phi_j,
+                                            //        G_{ij,a} =  int phi_j d_a phi_i
+  std::vector<double> Kmech;                // B = 9, row-major 3x3 block (a*3 + b)
+  std::vector<double> ML, w, invML;         // internal numbering; w = M_L / V
+  std::vector<uint8_t> mag;                 // internal numbering
+  int64_t pin = 0;                          // internal index of unique node 0
+};
+void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostOps* ops);
+
+}  // namespace gspm

@@ -1,0 +1,104 @@
+"""C ABI without a GPU: exported symbols, host-only contexts, and the host mesh layer compared
+bit-exactly with the oracle's independent periodic wrap, node graph and RCM order."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.mesh import WrappedMesh, csr_pattern, rcm_order
+from paper_2510_09812_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"GSPM_API\s+[\w\s\*]+?\b(gspm_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(gspm_lib):
+    names = _declared_symbols()
+    assert "gspm_step" in names and len(names) >= 10
+    lib = ctypes.CDLL(gspm_lib._LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+MESHES = [
+    dict(cells=(6, 5, 4), box=(24.0, 20.0, 16.0), jitter=0.2, seed=3, defects=[]),
+    dict(cells=(8, 8, 4), box=(32.0, 32.0, 16.0), jitter=0.2, seed=4,
+         defects=[dict(kind="sphere", center=(16.0, 16.0, 8.0), radius=7.0),
+                  dict(kind="cuboid", center=(2.0, 30.0, 1.0), half_sides=(4.0, 3.0, 3.0))]),
+    dict(cells=(16, 16, 4), box=(64.0, 64.0, 16.0), jitter=0.0, seed=0, defects=[]),
+]
+
+
+@pytest.mark.parametrize("spec", MESHES)
+@pytest.mark.parametrize("ordering", ["none", "rcm"])
+def test_host_mesh_matches_oracle_bit_exactly(gspm_lib, spec, ordering):
+    mesh = synth.kuhn_box(spec["cells"], spec["box"], jitter=spec["jitter"], seed=spec["seed"],
+                          defects=spec["defects"])
+    ctx = gspm_lib.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, ordering=ordering,
+                           host_only=True)
+    wm = WrappedMesh.from_synth(mesh)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_UNIQUE_OF_STORED), wm.unique_of_stored)
+    rowptr, cols = csr_pattern(wm.tets, wm.n)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_ROWPTR), rowptr)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_COLS), cols)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_NODE_MAGNETIC).astype(bool),
+                          wm.node_magnetic)
+    perm = ctx.export(gspm_lib.EXPORT_PERM)
+    expect = rcm_order(wm.tets, wm.n) if ordering == "rcm" else np.arange(wm.n)
+    assert np.array_equal(perm, expect)
+    ML = ctx.export(gspm_lib.EXPORT_LUMPED_MASS)
+    from oracle import fem
+    assert np.allclose(ML, fem.lumped_mass(wm), rtol=1e-14, atol=0)
+    info = ctx.info()
+    assert info["n_unique"] == wm.n and info["n_tets"] == mesh.n_tets
+    assert info["volume"] == pytest.approx(wm.volume, rel=1e-14)
+    assert info["n_magnetic_nodes"] == int(wm.node_magnetic.sum())
+    assert info["device_bytes"] == 0
+
+
+def test_host_only_context_rejects_device_calls(gspm_lib):
+    mesh = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    ctx = gspm_lib.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, host_only=True)
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        ctx.step(1, [0, 0, 0])
+    assert e.value.code == gspm_lib.ESTATE
+
+
+def test_invalid_meshes_are_rejected(gspm_lib):
+    mat = synth.fe_like_material()
+    mesh = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    bad = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    bad.tets = bad.tets.copy()
+    bad.tets[5] = bad.tets[5][[0, 2, 1, 3]]                        # inverted tet
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(bad, mat, 1e-12, 0.5, host_only=True)
+    assert e.value.code == gspm_lib.EMESH and "det" in str(e.value)
+    bad2 = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    bad2.tets = bad2.tets.copy()
+    bad2.tets[0, 0] = mesh.n_stored + 7                              # out of range
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(bad2, mat, 1e-12, 0.5, host_only=True)
+    assert e.value.code == gspm_lib.EMESH
+    bad3 = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    bad3.coords = bad3.coords.copy()
+    bad3.coords[4, 1] = np.nan
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(bad3, mat, 1e-12, 0.5, host_only=True)
+    assert e.value.code == gspm_lib.EMESH
+    one = synth.kuhn_box((1, 2, 2), (1.0, 2.0, 2.0))                 # wrap collapses tets
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(one, mat, 1e-12, 0.5, host_only=True)
+    assert e.value.code == gspm_lib.EMESH and "collapses" in str(e.value)
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(mesh, mat, -1.0, 0.5, host_only=True)       # dt <= 0
+    assert e.value.code == gspm_lib.EINVAL
