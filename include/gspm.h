@@ -225,6 +225,34 @@ GSPM_API int gspm_apply(struct gspm_ctx* ctx, int op, const double* x, double* y
 /* Number of CUDA kernels the context has launched since creation (host-side counter). */
 GSPM_API int64_t gspm_launch_count(const struct gspm_ctx* ctx);
 
+/* ---- allocation-free variant ------------------------------------------------------------ */
+
+/* Volume average without any device allocation, for callers that cannot call cudaMalloc (for
+ * example code confined to another framework's fixed memory pool, or real-time loops and host
+ * callbacks that must not take cudaMalloc's implicit device synchronisation).  The paper has no
+ * counterpart; this is the reduction of gspm_volume_avg with caller-supplied weights.
+ *
+ * out[c] = sum_i weights[i] * field[i*ncomp + c], c < ncomp, accumulated in FP64 with a fixed
+ * reduction order.  field ([n][ncomp]), weights ([n]) and out ([ncomp]) are float64 DEVICE
+ * pointers owned by the caller; weights = M_L,i / V(Omega_c) (GSPM_EXPORT_LUMPED_MASS divided
+ * by gspm_mesh_info.volume) gives the Sec. 2.4 volume average.  The call is asynchronous on
+ * `stream` (a cudaStream_t, NULL = legacy default stream); it allocates nothing and calls no
+ * cudaMalloc/cudaFree.
+ *
+ * Scratch: a file-scope __device__ array of GSPM_NOALLOC_MAX_BLOCKS x 16 doubles plus a counter
+ * (about 256 KiB) that every GPU loading the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current) and caches it; make that first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's partial sums; the arrival counter is cleared on `stream` at
+ * the start of each call.  Calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race on the scratch and give wrong results: serialise them.
+ * Errors: GSPM_EINVAL for null pointers, n <= 0 or ncomp outside 1..GSPM_NOALLOC_MAX_COMP;
+ * GSPM_ECUDA if the symbol lookup, the counter clear or the launch fails. */
+#define GSPM_NOALLOC_MAX_COMP 9
+#define GSPM_NOALLOC_MAX_BLOCKS 2048
+GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights, int64_t n,
+                                     int ncomp, double* out, void* stream);
+
 /* ---- measurement ------------------------------------------------------------------------ */
 
 /* kernel classes for gspm_profile_* */

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgspm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["kernels.cu", "api.cu"]
+CUDA_SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
 CXX_SOURCES = ["host_mesh.cpp"]
 
 

@@ -90,6 +90,7 @@ def _load():
         "gspm_launch_count": (C.c_int64, [vp]),
         "gspm_profile_enable": (C.c_int, [vp, C.c_uint]),
         "gspm_profile_read": (C.c_int, [vp, C.c_int, _dp, C.POINTER(C.c_int64)]),
+        "gspm_volume_avg_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -298,3 +299,19 @@ class Context:
         k = KCLASS[cls] if isinstance(cls, str) else int(cls)
         _check(lib.gspm_profile_read(self._h, k, C.byref(ms), C.byref(cnt)), "gspm_profile_read")
         return ms.value, cnt.value
+
+
+def volume_avg_noalloc(field, weights, out, stream=0):
+    """gspm_volume_avg_noalloc on CUDA float64 tensors field [n][ncomp], weights [n], out
+    [ncomp]; asynchronous on `stream`, allocates nothing."""
+    for a in (field, weights, out):
+        if not _is_device(a):
+            raise ValueError("volume_avg_noalloc takes device tensors only")
+    n = weights.numel()
+    nc = field.numel() // max(n, 1)
+    pf, _, _ = _ptr(field, n * nc)
+    pw, _, _ = _ptr(weights, n)
+    po, _, _ = _ptr(out, nc)
+    _check(lib.gspm_volume_avg_noalloc(pf, pw, n, nc, po, C.c_void_p(int(stream))),
+           "gspm_volume_avg_noalloc")
+    return out
