@@ -27,6 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GSPM steps/s at 3M nodes, mixed+learned vs plain FP64 on 1 GB300; % HBM peak"
+WEIGHTS = os.path.join(ROOT, "paper_2510_09812_gb300", "weights", "warmstart_mpnn.npy")
 FALLBACK_HBM = 6800.0
 
 
@@ -51,12 +52,15 @@ def _workload(args):
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
 
-    def __init__(self, index):
+    def __init__(self, index, enabled=True):
         self.index = index
+        self.enabled = enabled
         self.proc = None
         self.path = None
 
     def __enter__(self):
+        if not self.enabled:
+            return self
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -158,6 +162,69 @@ def cpu_oracle_sample(wall_budget=25.0, steps=None, warmup=1):
     return (1.0 / per) * (wm.n / full_n), per, desc, k
 
 
+def run_batch(gspm, torch, args, barrier):
+    """64 independent meshes of log-uniform size 2k-200k nodes, each with its own inclusion and
+    applied field, stepped together (mixed precision) by gspm_batch_step; compared with the
+    same meshes stepped one after another in their own contexts (first 16 meshes)."""
+    from paper_2510_09812_gb300 import synth
+    members = [synth.batch_member(i) for i in range(args.batch_meshes)]
+    meshes = [c["mesh"] for c in members]
+    H = np.array([c["H"] for c in members])
+    t0 = time.perf_counter()
+    ctx = gspm.Context(meshes, members[0]["material"], members[0]["dt"], members[0]["alpha"],
+                       precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
+    t_load = time.perf_counter() - t0
+    ctx.set_field(gspm.FIELD_M, np.concatenate([c["m0"] for c in members]))
+    info = ctx.info()
+    ctx.batch_step(2, H, stats=False)
+    kb = max(1, min(args.steps, 4))
+    l0 = ctx.launch_count()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    st = ctx.batch_step(kb, H)
+    ev1.record()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - l0
+    ctx.close()
+    # the same first 16 meshes, one context each, stepped one after another
+    k16 = min(16, len(members))
+    seq_ctx = []
+    for c in members[:k16]:
+        x = gspm.Context(c["mesh"], c["material"], c["dt"], c["alpha"], precision="mixed",
+                         rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
+        x.set_field(gspm.FIELD_M, c["m0"])
+        x.step(2, c["H"], stats=False)
+        seq_ctx.append(x)
+    bctx = gspm.Context(meshes[:k16], members[0]["material"], members[0]["dt"],
+                        members[0]["alpha"], precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7,
+                        rtol_mech=1e-7)
+    bctx.set_field(gspm.FIELD_M, np.concatenate([c["m0"] for c in members[:k16]]))
+    bctx.batch_step(2, H[:k16], stats=False)
+    barrier()
+    t0 = time.perf_counter()
+    for x, c in zip(seq_ctx, members[:k16]):
+        x.step(1, c["H"], stats=False)
+    barrier()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bctx.batch_step(1, H[:k16], stats=False)
+    barrier()
+    t_bat = time.perf_counter() - t0
+    for x in seq_ctx:
+        x.close()
+    bctx.close()
+    return {"meshes": len(members), "nodes": info["n_unique"],
+            "min_nodes": min(m.n_unique for m in meshes), "max_nodes": max(m.n_unique for m in meshes),
+            "steps": kb, "ms_per_batch_step": ms / kb, "batch_steps_per_s": kb / (ms / 1000.0),
+            "node_updates_per_s": info["n_magnetic_nodes"] * kb / (ms / 1000.0),
+            "gpu_launches_per_batch_step": launches / kb, "load_s": round(t_load, 1),
+            "item_slices": info["item_slices"],
+            "first16_batched_vs_sequential_ms": [round(1000 * t_bat, 1), round(1000 * t_seq, 1)],
+            "mech_it_per_mesh_last_step": [s_["it_mech_last"] for s_ in st]}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -206,11 +273,23 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def make(prec):
+    weights = None
+    if os.path.exists(WEIGHTS):
+        weights = np.load(WEIGHTS)
+    x0_names = {"prev": gspm.X0_PREV, "zero": gspm.X0_ZERO, "extrapolate": gspm.X0_EXTRAPOLATE,
+                "learned": gspm.X0_LEARNED}
+    x0 = args.x0 if args.x0 != "auto" else ("learned" if weights is not None else "extrapolate")
+    if x0 == "learned" and weights is None:
+        raise SystemExit(f"--x0 learned needs trained weights at {WEIGHTS}")
+
+    def make(prec, mode="prev"):
         t0 = time.perf_counter()
         ctx = gspm.Context(mesh, cfg["material"], cfg["dt"], cfg["alpha"], precision=prec,
                            ordering=args.ordering, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
         ctx.set_field(gspm.FIELD_M, cfg["m0"])
+        if weights is not None:
+            ctx.mpnn_set_params(weights)
+        ctx.set_x0_mode(x0_names[mode])
         return ctx, time.perf_counter() - t0
 
     def timed_steps(ctx, k, profile=("spmv_mech",)):
@@ -219,7 +298,7 @@ def run_ours(args):
         l0 = ctx.launch_count()
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
+        with ClockSampler(local, enabled=not args.no_clocks) as clk:
             ev0.record()
             for _ in range(k):
                 st = ctx.step(1, H)
@@ -234,7 +313,7 @@ def run_ours(args):
         return ms, st_tot, launches, prof, clk.summary()
 
     precision = args.precision
-    ctx, t_load = make(precision)
+    ctx, t_load = make(precision, x0)
     info = ctx.info()
     n = info["n_unique"]
     for _ in range(args.warmup):
@@ -294,7 +373,25 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e = {"value": ws * ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": n * 3 * 8,
            "d2h_bytes_per_step": n * 3 * 8}
+
+    # mechanical-CG initial guesses compared over the same steps from the same state
+    x0_cmp = {}
+    if not args.skip_x0:
+        modes = ["prev", "extrapolate"] + (["learned"] if weights is not None else [])
+        kx = max(1, min(args.steps, 3))
+        for mode in modes:
+            restore()
+            ctx.set_x0_mode(x0_names[mode])
+            ms_x, st_x, _, _, _ = timed_steps(ctx, kx, ())
+            x0_cmp[mode] = {"it_mech_per_step": st_x["it_mech"] / kx,
+                            "ms_per_step": round(ms_x / kx, 2)}
+        ctx.set_x0_mode(x0_names[x0])
     ctx.close()
+
+    # batched uneven meshes (64 meshes, 2k-200k nodes) in one context
+    batched = None
+    if not args.skip_batch:
+        batched = run_batch(gspm, torch, args, barrier)
 
     # plain FP64 GPU form on the same GPU (the comparison the metric names)
     plain = None
@@ -339,6 +436,9 @@ def run_ours(args):
                      "launches_timed": n_spmv, "iterations_timed": st["it_mech"]},
         "breakdown_ms_per_step": breakdown,
         "plain_f64": plain,
+        "batched": batched,
+        "x0": x0,
+        "x0_comparison": x0_cmp,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -358,6 +458,13 @@ def main():
     ap.add_argument("--cells", default=None, help="smaller mesh of the same recipe, e.g. 64,64,16")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-x0", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-meshes", type=int, default=64)
+    ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampler (profiling)")
+    ap.add_argument("--x0", default="auto", choices=["auto", "prev", "zero", "extrapolate", "learned"],
+                    help="initial guess of the mechanical CG (auto: learned when trained weights "
+                         "exist, else extrapolation)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -64,6 +64,7 @@ extern "C" {
 #define GSPM_FLAG_HOST_ONLY 1u        /* build host structures only; no CUDA call is made      */
 #define GSPM_FLAG_ROW2_PRINTED 2u     /* Algorithm B.1 second row exactly as printed (m^n_1,
                                          g^n_1) instead of the Gauss-Seidel sweep (m*_1, g*_1)  */
+#define GSPM_FLAG_NO_AUTOTUNE 4u      /* skip the SpMV schedule autotuner (schedule 0)          */
 
 /* ---- inputs ----------------------------------------------------------------------------- */
 typedef struct gspm_mesh_desc {
@@ -113,6 +114,14 @@ typedef struct gspm_mesh_info {
   double eps;              /* A* Delta tau (nm^2), operator (1 - eps Lap) of Algorithm B.1     */
   double dtau;             /* gamma0 m_s dt                                                    */
   int64_t device_bytes;    /* device memory held by the context                               */
+  int n_segments;          /* meshes in the context (1 unless loaded with gspm_batch_load)     */
+  int item_slices;         /* slices per work item of the reducing kernels                    */
+  int spmv_schedule_block; /* SpMV schedule the autotuner chose for the 3x3-block operator:
+                              0 thread per row, 1 thread per row with 5-deep load prefetch,
+                              2 two threads per row                                             */
+  int spmv_schedule_scalar;/* ... and for the scalar operators                                 */
+  double spmv_ms_block[3]; /* measured ms per launch of each schedule (0 = not tuned)          */
+  double spmv_ms_scalar[3];
 } gspm_mesh_info;
 
 typedef struct gspm_step_stats {
@@ -143,6 +152,14 @@ typedef struct gspm_step_stats {
 #define GSPM_FIELD_HD 3      /* [n][3] local demagnetising field -grad U (reduced), read only  */
 #define GSPM_FIELD_STRAIN 4  /* [n][6] total strain E, Voigt 11,22,33,23,13,12 (tensor shear), read only */
 #define GSPM_FIELD_H 5       /* [n][3] local field h(m^n) of the last step (reduced), read only */
+#define GSPM_FIELD_DISP_PREV 6 /* [n][3] displacement of the solve before the last (history of
+                                  the extrapolated and learned initial guesses)                 */
+
+/* initial guess of the mechanical CG inside gspm_step (gspm_set_x0_mode) */
+#define GSPM_X0_PREV 0         /* previous step's displacement (default)                      */
+#define GSPM_X0_ZERO 1         /* cold start                                                   */
+#define GSPM_X0_EXTRAPOLATE 2  /* 2 u_prev - u_prev2                                           */
+#define GSPM_X0_LEARNED 3      /* 2 u_prev - u_prev2 + u_s * MPNN(features), see gspm_mpnn_*   */
 
 /* operators for gspm_apply (per-kernel access; y = Op x in unique-node order, host or device) */
 #define GSPM_OP_K_MS 0       /* pinned K^ms (Eq. LHS), scalar                                  */
@@ -165,6 +182,28 @@ typedef struct gspm_step_stats {
  * m = 0, U = 0, u = 0.  Errors: GSPM_EINVAL (null/size), GSPM_EMESH, GSPM_ENOMEM, GSPM_ECUDA. */
 GSPM_API int gspm_mesh_load(const gspm_mesh_desc* mesh, const gspm_material* mat,
                             const gspm_options* opt, struct gspm_ctx** out);
+
+/* Load several meshes into one context (a batch, e.g. meshes of uneven size or defect
+ * geometry): each mesh is prepared as by gspm_mesh_load and the batch is stored slice-aligned in
+ * one structure, so that one kernel sequence advances every mesh.  All meshes share the
+ * material and options; each keeps its own pin, volume averages, applied field and CG
+ * convergence (a mesh whose CG converged stops iterating while the others continue).
+ * Node numbering of the batch at the ABI: mesh 0's unique nodes, then mesh 1's, and so on
+ * (gspm_batch_segment gives each mesh's offset and count); fields are [sum n][...].
+ * gspm_volume_avg returns n_meshes x ncomp values; gspm_step applies one field to every mesh
+ * and its stats argument points to n_meshes structures; gspm_mesh_export is single-mesh only;
+ * the learned initial guess is single-mesh only. */
+GSPM_API int gspm_batch_load(const gspm_mesh_desc* meshes, int n_meshes, const gspm_material* mat,
+                             const gspm_options* opt, struct gspm_ctx** out);
+
+/* First ABI node and node count of mesh `seg` of a batch. */
+GSPM_API int gspm_batch_segment(const struct gspm_ctx* ctx, int seg, int64_t* node_offset,
+                                int64_t* n_nodes);
+
+/* gspm_step with one applied field per mesh: H_ext = [n_meshes][3] (A/m, host); stats (may be
+ * NULL) = [n_meshes]. */
+GSPM_API int gspm_batch_step(struct gspm_ctx* ctx, int n_steps, const double* H_ext,
+                             gspm_step_stats* stats);
 
 /* Free every resource of the context (waits for its stream). NULL is a no-op. */
 GSPM_API void gspm_destroy(struct gspm_ctx* ctx);
@@ -204,15 +243,17 @@ GSPM_API int gspm_step(struct gspm_ctx* ctx, int n_steps, const double H_ext[3],
 
 /* Mechanical equilibrium alone (steps E0 .. strain of gspm_step) for magnetisation m ([n][3],
  * `where`); writes the displacement to u ([n][3], `where`, may be NULL) and keeps it as the
- * context's u.  x0_mode: 0 = zero, 1 = the context's previous u, 2 = the array x0 ([n][3],
- * `where`).  rtol <= 0 uses the context's rtol_mech.  iters / relres may be NULL.  Does not change
- * the context's m.  Synchronises the stream. */
+ * context's u (the former u becomes u_prev2).  x0_mode: 0 = zero, 1 = the context's u, 2 = the
+ * array x0 ([n][3], `where`), 3 = extrapolation 2u - u_prev2, 4 = learned (gspm_mpnn_*).  rtol
+ * <= 0 uses the context's rtol_mech.  iters / relres may be NULL.  Does not change the context's
+ * m.  Synchronises the stream. */
 GSPM_API int gspm_solve_elastic(struct gspm_ctx* ctx, const double* m, double* u, int where,
                                 int x0_mode, const double* x0, double rtol, int* iters,
                                 double* relres);
 
 /* Volume average over Omega_c (Sec. 2.4) of a nodal field with ncomp (1..9) interleaved
- * components, [n][ncomp] float64 at `where`; result in out_host[ncomp].  Quadrature of the P1
+ * components, [n][ncomp] float64 at `where`; result in out_host[ncomp] (per mesh of a batch:
+ * out_host[n_meshes][ncomp]).  Quadrature of the P1
  * interpolant: sum_e V_e (1/4) sum_{k in e} g_k / V = sum_i (M_L,i / V) g_i.  FP64 accumulation
  * with a fixed reduction order (bitwise reproducible for a given device).  Synchronises. */
 GSPM_API int gspm_volume_avg(struct gspm_ctx* ctx, const double* field, int where, int ncomp,
@@ -253,6 +294,51 @@ GSPM_API int64_t gspm_launch_count(const struct gspm_ctx* ctx);
 GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights, int64_t n,
                                      int ncomp, double* out, void* stream);
 
+/* ---- learned warm start of the mechanical CG ------------------------------------------- */
+/* A message-passing network over the mesh (the paper has none; this is the build's learned
+ * initial guess, checked against its own FP64 CPU definition).  Per node, 16 features:
+ * m (3), E0(m) in Voigt order / lambda_s (6), u_prev / u_s (3), (u_prev - u_prev2) / u_s (3), 1,
+ * with lambda_s = max(|lambda100|, |lambda111|) and u_s = lambda_s * (V(Omega_c)/n)^(1/3).
+ * h0 = relu(f W_in + b_in); three layers h_l = relu([h, A h] W_l + b_l) with A the
+ * element-message average (A_ij = sum_{e containing i,j} V_e / (16 M_L,i)); y = h3 W_out + b_out.
+ * Prediction x0 = 2 u_prev - u_prev2 + u_s y.  Inference runs on the tensor cores (BF16 weights
+ * and activations, FP32 accumulation); training (backward, Adam) in FP32.  CG still runs to the
+ * same residual, so the prediction only changes the iteration count.
+ * Parameter layout (float32, GSPM_MPNN_PARAMS values): W_in [16][64], b_in [64],
+ * {W_l [128][64], b_l [64]} for l = 1..3, W_out [64][3], b_out [3]; all row-major [in][out]. */
+#define GSPM_MPNN_PARAMS 26051
+
+/* Select the mechanical CG's initial guess for gspm_step (GSPM_X0_*); GSPM_X0_LEARNED needs
+ * parameters (GSPM_ESTATE otherwise). */
+GSPM_API int gspm_set_x0_mode(struct gspm_ctx* ctx, int mode);
+
+/* Copy the network parameters in (host float32 [GSPM_MPNN_PARAMS]; resets Adam) or out. */
+GSPM_API int gspm_mpnn_set_params(struct gspm_ctx* ctx, const float* params, int64_t count);
+GSPM_API int gspm_mpnn_get_params(struct gspm_ctx* ctx, float* params, int64_t count);
+
+/* Run the network on m, u_prev, u_prev2 ([n][3] float64 at `where`; the u's may be NULL = 0).
+ * what = 0: raw output y [n][3]; what = 1: initial guess x0 = 2 u_prev - u_prev2 + u_s y. */
+GSPM_API int gspm_mpnn_predict(struct gspm_ctx* ctx, const double* m, const double* u_prev,
+                               const double* u_prev2, double* out, int what, int where);
+
+/* Device-resident training set of this mesh: reserve `capacity` pairs, then add pairs
+ * (m, u_prev, u_prev2) -> u* (u* = the displacement the plain solver found for m); the target
+ * stored is t = (u* - (2 u_prev - u_prev2)) / u_s.  index (may be NULL) receives the slot. */
+GSPM_API int gspm_mpnn_dataset_reserve(struct gspm_ctx* ctx, int capacity);
+GSPM_API int gspm_mpnn_dataset_add(struct gspm_ctx* ctx, const double* m, const double* u_prev,
+                                   const double* u_prev2, const double* u_star, int where,
+                                   int* index);
+
+/* Loss mean((y - t)^2) over nodes and components on stored pair `pair`, and its gradient with
+ * respect to every parameter (host float32 [GSPM_MPNN_PARAMS], may be NULL). */
+GSPM_API int gspm_mpnn_loss_grad(struct gspm_ctx* ctx, int pair, double* loss, float* grad);
+
+/* `iterations` Adam steps (lr, beta = 0.9 / 0.999, eps 1e-8), each on one stored pair drawn by a
+ * splitmix64 stream of `seed`; loss_first / loss_last (may be NULL) receive the losses of the first
+ * and last step (before their update). */
+GSPM_API int gspm_mpnn_train(struct gspm_ctx* ctx, int iterations, double lr, uint64_t seed,
+                             double* loss_first, double* loss_last);
+
 /* ---- measurement ------------------------------------------------------------------------ */
 
 /* kernel classes for gspm_profile_* */
@@ -263,7 +349,8 @@ GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights,
 #define GSPM_KCLASS_CG_INIT 4    /* CG start-up (residual, norms)                              */
 #define GSPM_KCLASS_ROWOPS 5     /* F^ms / G row kernels: RHS assembly, h~_d and strain        */
 #define GSPM_KCLASS_POINTWISE 6  /* E0, h(m), GSPM stages, projection, volume averages         */
-#define GSPM_KCLASS_COUNT 7
+#define GSPM_KCLASS_LEARNED 7    /* learned warm start inference (features, 4 layers, output)  */
+#define GSPM_KCLASS_COUNT 8
 
 /* Record CUDA events on the context's stream around every subsequent launch of the classes in
  * class_mask (bit k = class k); 0 stops recording.  Each call clears the accumulated times. */

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgspm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
+CUDA_SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "mpnn.cu"]
 CXX_SOURCES = ["host_mesh.cpp"]
 
 
@@ -36,6 +36,7 @@ def _cuda_home(nvcc: str) -> str:
 def _sources():
     return [os.path.join(CSRC, s) for s in CUDA_SOURCES + CXX_SOURCES] + [
         os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "kernels.cuh"),
+        os.path.join(CSRC, "mpnn.cuh"),
         os.path.join(INCLUDE, "gspm.h")]
 
 

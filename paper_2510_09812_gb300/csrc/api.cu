@@ -16,6 +16,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "mpnn.cuh"
 
 namespace gspm {
 
@@ -80,7 +81,7 @@ struct SolveInfo {
 class EngineBase {
  public:
   virtual ~EngineBase() = default;
-  virtual int step(int n_steps, const double H[3], gspm_step_stats* st) = 0;
+  virtual int step(int n_steps, const double* H, bool per_segment, gspm_step_stats* st) = 0;
   virtual int solve_elastic(const double* m, double* u, int where, int x0_mode, const double* x0,
                             double rtol, int* iters, double* relres) = 0;
   virtual int volume_avg(const double* f, int where, int nc, double* out) = 0;
@@ -88,35 +89,51 @@ class EngineBase {
   virtual int set_field(int field, const double* data, int where) = 0;
   virtual int get_field(int field, double* data, int where) = 0;
   virtual int64_t device_bytes() const = 0;
+  virtual void tune_info(int* vb, int* vs, float* tb, float* ts, int* item_slices) const = 0;
   virtual int profile_enable(unsigned mask) = 0;
   virtual int profile_read(int cls, double* ms, int64_t* launches) = 0;
+  virtual int set_x0_mode(int mode) = 0;
+  virtual int mpnn_params(float* out, const float* in, int64_t count) = 0;
+  virtual int mpnn_predict(const double* m, const double* up, const double* up2, double* out,
+                           int what, int where) = 0;
+  virtual int mpnn_dataset_reserve(int capacity) = 0;
+  virtual int mpnn_dataset_add(const double* m, const double* up, const double* up2,
+                               const double* ustar, int where, int* index) = 0;
+  virtual int mpnn_loss_grad(int pair, double* loss, float* grad) = 0;
+  virtual int mpnn_train(int iters, double lr, uint64_t seed, double* l0, double* l1) = 0;
 };
 
 template <typename T>
 class Engine final : public EngineBase {
  public:
-  Engine(const HostMesh& hm, const HostSell& hs, const HostOps& ops, const Params& P,
-         const gspm_options& opt, cudaStream_t stream, int64_t* counter)
-      : hm_(hm), P_(P), opt_(opt) {
-    n_ = hm.n;
+  Engine(const HostBatch& hb, const Params& P, const gspm_options& opt, cudaStream_t stream,
+         int64_t* counter)
+      : hb_(hb), P_(P), opt_(opt) {
+    n_ = hb.sell.n;
     ld_ = (n_ + 31) / 32 * 32;
-    nslices_ = hs.nslices;
-    entries_ = hs.entries;
-    pin_ = ops.pin;
-    nmag_ = hm.n_mag_nodes;
+    nslices_ = hb.sell.nslices;
+    entries_ = hb.sell.entries;
+    nseg_ = (int)hb.seg_row0.size();
+    nmag_ = hb.n_mag_nodes;
+    nodes_ = hb.n_nodes;
     L_.stream = stream;
     L_.counter = counter;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     L_.max_blocks = std::max(1, sms) * 8;
+    L_.sms = std::max(1, sms);
   }
   ~Engine() override {
     if (host_state_) cudaFreeHost(host_state_);
+    if (host_active_) cudaFreeHost(host_active_);
+    if (host_scal_) cudaFreeHost(host_scal_);
     for (cudaEvent_t e : prof_ev_) cudaEventDestroy(e);
   }
 
-  int init(const HostSell& hs, const HostOps& ops) {
+  int init() {
+    const HostSell& hs = hb_.sell;
+    const HostOps& ops = hb_.ops;
     const int64_t n = n_, ld = ld_, E = entries_;
     ST(mem_.alloc(&sptr_, nslices_ + 1));
     ST(mem_.alloc(&slen_, nslices_));
@@ -139,7 +156,8 @@ class Engine final : public EngineBase {
     CK(cudaMemcpy(invML_, ops.invML.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(w_, ops.w.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(mag_, ops.mag.data(), n, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(perm_, hm_.perm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(perm_, hb_.perm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+    ST(init_segments());
     ST(mem_.alloc(&m_, 3 * ld));
     ST(mem_.alloc(&ms_, 3 * ld));
     ST(mem_.alloc(&h_, 3 * ld));
@@ -149,6 +167,18 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&sig0_, 6 * n));
     ST(mem_.alloc(&U_, ld));
     ST(mem_.alloc(&u_, 3 * n));
+    ST(mem_.alloc(&u2_, 3 * n));
+    ST(mem_.alloc(&utmp_, 3 * n));
+    ST(mem_.alloc(&uin_, 3 * n));
+    ST(mem_.alloc(&uin2_, 3 * n));
+    {
+      std::vector<float> a(ops.Agg.begin(), ops.Agg.end()), at(ops.AggT.begin(), ops.AggT.end());
+      ST(mem_.alloc(&agg_, (int64_t)a.size()));
+      ST(mem_.alloc(&aggT_, (int64_t)at.size()));
+      CK(cudaMemcpy(agg_, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(aggT_, at.data(), at.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    h_scale_ = hb_.seg_h[0];
     ST(mem_.alloc(&b_, 3 * ld));
     ST(mem_.alloc(&r_, 3 * ld));
     ST(mem_.alloc(&x_, 3 * ld));
@@ -157,29 +187,82 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&stage_, 9 * n));
     ST(mem_.alloc(&tin_, 3 * ld));
     ST(mem_.alloc(&tout_, 3 * ld));
-    ST(mem_.alloc(&cg_, kSolveSlots));
-    ST(mem_.alloc(&scal_, 32));
-    ST(mem_.alloc(&red_.partial, (int64_t)L_.max_blocks * kRedComp));
-    ST(mem_.alloc(&red_.counter, 1));
-    CK(cudaMemset(red_.counter, 0, sizeof(unsigned)));
-    CK(cudaMemset(scal_, 0, 32 * sizeof(double)));
+    ST(mem_.alloc(&cg_, (int64_t)kSolveSlots * nseg_));
+    ST(mem_.alloc(&nactive_, kSolveSlots));
+    ST(mem_.alloc(&scal_, (int64_t)kScalPerSeg * nseg_ + 8));
+    CK(cudaMemset(scal_, 0, ((int64_t)kScalPerSeg * nseg_ + 8) * sizeof(double)));
+    CK(cudaMemset(nactive_, 0, kSolveSlots * sizeof(int)));
     CK(cudaMemset(m_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(ms_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(h_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(hd_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(E_, 0, 6 * ld * sizeof(T)));
-    CK(cudaMemset(U_, 0, ld * sizeof(double)));
-    CK(cudaMemset(u_, 0, 3 * n * sizeof(double)));
-    CK(cudaMemset(x_, 0, 3 * ld * sizeof(double)));
+    CK(cudaMemset(U_, 0, ld * sizeof(T)));
+    CK(cudaMemset(u_, 0, 3 * n * sizeof(T)));
+    CK(cudaMemset(u2_, 0, 3 * n * sizeof(T)));
+    CK(cudaMemset(x_, 0, 3 * ld * sizeof(T)));
+    CK(cudaMemset(r_, 0, 3 * ld * sizeof(T)));
+    CK(cudaMemset(b_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(p_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(q_, 0, 3 * ld * sizeof(T)));
-    CK(cudaMemset(cg_, 0, kSolveSlots * sizeof(CGState)));
-    // E_ext (added to <E0> when forming E_bar)
-    CK(cudaMemcpy(scal_ + kEext, P_.E_ext, 6 * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMallocHost(&host_state_, sizeof(CGState)));
+    CK(cudaMemset(cg_, 0, (int64_t)kSolveSlots * nseg_ * sizeof(CGState)));
+    // E_ext (added to <E0> when forming E_bar) and 1 / (magnetic nodes) per segment
+    CK(cudaMemcpy(eext(), P_.E_ext, 6 * sizeof(double), cudaMemcpyHostToDevice));
+    {
+      std::vector<double> inv(nseg_);
+      for (int s = 0; s < nseg_; ++s)
+        inv[s] = hb_.seg_nmag[s] > 0 ? 1.0 / (double)hb_.seg_nmag[s] : 0.0;
+      CK(cudaMemcpy(inv_nmag(), inv.data(), nseg_ * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMallocHost(&host_state_, (int64_t)nseg_ * sizeof(CGState)));
+    CK(cudaMallocHost(&host_active_, sizeof(int)));
+    CK(cudaMallocHost(&host_scal_, ((int64_t)kScalPerSeg * nseg_ + 8) * sizeof(double)));
     for (int k = 0; k < kSolveSlots; ++k) pred_[k] = 8;
     CK(cudaDeviceSynchronize());
+    if (!(opt_.flags & GSPM_FLAG_NO_AUTOTUNE)) ST(autotune());
     return GSPM_OK;
+  }
+
+  // Project autotuner: time every SpMV schedule on this mesh's own operators (K^mech for the
+  // 3x3-block kernels, K^ms for the scalar ones; five launches each after one warm-up, CUDA
+  // events on the context's stream) and keep the fastest.
+  int autotune() {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_variant = [&](int B, const T* val, int var, float* ms) -> int {
+      CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var));
+      CK(cudaEventRecord(e0, L_.stream));
+      for (int k = 0; k < 5; ++k) CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var));
+      CK(cudaEventRecord(e1, L_.stream));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(ms, e0, e1));
+      return GSPM_OK;
+    };
+    float best_b = 1e30f, best_s = 1e30f;
+    for (int v = 0; v < kSpmvVariants; ++v) {
+      float t = 0.f;
+      ST(time_variant(9, Kmech_, v, &t));
+      tune_ms_block_[v] = t / 5.f;
+      if (t < best_b) { best_b = t; var_block_ = v; }
+      ST(time_variant(1, Kms_, v, &t));
+      tune_ms_scalar_[v] = t / 5.f;
+      if (t < best_s) { best_s = t; var_scalar_ = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GSPM_OK;
+  }
+
+ public:
+  void tune_info(int* vb, int* vs, float* tb, float* ts, int* item_slices) const override {
+    *vb = var_block_;
+    *vs = var_scalar_;
+    *item_slices = item_slices_;
+    for (int v = 0; v < kSpmvVariants; ++v) {
+      tb[v] = tune_ms_block_[v];
+      ts[v] = tune_ms_scalar_[v];
+    }
   }
 
   int64_t device_bytes() const override { return mem_.bytes; }
@@ -212,38 +295,40 @@ class Engine final : public EngineBase {
   }
 
   // ---------------------------------------------------------------- one GSPM step
-  int step(int n_steps, const double H[3], gspm_step_stats* st) override {
-    DevParams D = dev_params(H);
-    gspm_step_stats acc;
-    memset(&acc, 0, sizeof(acc));
+  // H: applied field (A/m), three values per segment when per_segment, else one for all.
+  // st: per-segment statistics (nseg entries) or NULL.
+  int step(int n_steps, const double* H, bool per_segment, gspm_step_stats* st) override {
+    DevParams D = dev_params();
+    std::vector<gspm_step_stats> acc(nseg_);
+    for (auto& a : acc) memset(&a, 0, sizeof(a));
     const int64_t n = n_, ld = ld_;
-    double* mbar = scal_ + kMbar;
-    double* mbar_s = scal_ + kMbarS;
-    double* Ebar = scal_ + kEbar;
-    double* dm = scal_ + kDm;
     const int printed = (opt_.flags & GSPM_FLAG_ROW2_PRINTED) ? 1 : 0;
-    for (int s = 0; s < n_steps; ++s) {
+    for (int s = 0; s < nseg_; ++s)
+      for (int a = 0; a < 3; ++a)
+        host_scal_[3 * s + a] = (per_segment ? H[3 * s + a] : H[a]) / P_.Ms;
+    CK(cudaMemcpyAsync(hz(), host_scal_, 3 * nseg_ * sizeof(double), cudaMemcpyHostToDevice,
+                       L_.stream));
+    std::vector<SolveInfo> ims, imech, ig[8];
+    for (int stp = 0; stp < n_steps; ++stp) {
       // a1 volume average of m (Sec. 2.4)
-      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, n, 3, m_, ld, 1, nullptr, w_, mbar, nullptr, red_));
+      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, m_, ld, 1, nullptr, w_, mbar(), nullptr, red_));
       // a2 b^ms / m_s = F^ms m (Eq. RHS_b), a3 CG on pinned K^ms, x0 = previous U
-      TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, F_, m_, ld, b_, pin_));
-      SolveInfo ims;
-      ST(solve_general(kSlotMs, Kms_, 1, b_, U_, n, opt_.rtol_ms, &ims));
+      TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, SG_, F_, m_, ld, b_));
+      ST(solve_general(kSlotMs, Kms_, 1, b_, U_, opt_.rtol_ms, &ims));
       // a4 local demagnetising field h~_d = -grad U
       TK(GSPM_KCLASS_ROWOPS, launch_fgrad<T>(L_, A_, F_, U_, invML_, hd_, ld));
       // a5 E0(m), sigma0 = C E0, E_bar = <E0> + C^-1 sigma_ext
       TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, m_, ld, mag_, D, E0_, sig0_));
-      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, n, 6, E0_, ld, 1, nullptr, w_, Ebar, scal_ + kEext, red_));
-      // a6 b^mech = F^mech E0, a7 CG on pinned K^mech, x0 = previous u
-      TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, G_, sig0_, b_, pin_));
-      SolveInfo imech;
-      ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, 3 * n, opt_.rtol_mech, &imech));
+      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
+      // a6 b^mech = F^mech E0, a7 CG on pinned K^mech, x0 per the initial-guess mode
+      TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_));
+      ST(mech_initial_guess(m_, x0_mode_));
+      ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, opt_.rtol_mech, &imech));
       // a8 strain E = E_bar + sym grad u
-      TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, F_, u_, invML_, Ebar, E_, ld));
+      TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
       // a9 h(m^n)
-      TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, m_, hd_, E_, ld, mbar, mag_, D, 0, 0.0, h_, nullptr));
+      TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, m_, hd_, E_, ld, mbar(), hz(), mag_, D, 0, 0.0, h_, nullptr));
       // a10 Gauss-Seidel stages (Algorithm B.1 steps 1-2), (M + eps K) g = M f, x0 = f
-      SolveInfo ig[8];
       int ngs = 0;
       if (!printed) {
         TK(GSPM_KCLASS_POINTWISE, launch_gs_prep<T>(L_, n, ld, m_, h_, P_.dtau, 1, 2, x_));
@@ -263,44 +348,46 @@ class Engine final : public EngineBase {
         ngs = 5;
       }
       // a11 h(m*) with h~_d and E held, far field from m_bar*; f = m* + alpha dtau h*
-      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, n, 3, ms_, ld, 1, nullptr, w_, mbar_s, nullptr, red_));
-      TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, ms_, hd_, E_, ld, mbar_s, mag_, D, 1, P_.alpha * P_.dtau,
-                          nullptr, x_));
+      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, ms_, ld, 1, nullptr, w_, mbar_s(), nullptr, red_));
+      TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, ms_, hd_, E_, ld, mbar_s(), hz(), mag_, D, 1, P_.alpha * P_.dtau, nullptr, x_));
       // a12 (M + alpha eps K) m** = M f, three right-hand sides
       ST(solve_gs(kSlotGsD, Aaeps_, 0, 3, &ig[ngs]));
       ngs += 3;
       // a13 projection and <|dm|>
-      TK(GSPM_KCLASS_POINTWISE, launch_project<T>(L_, n, ld, x_, mag_, m_, dm,
-                           nmag_ > 0 ? 1.0 / (double)nmag_ : 0.0, red_));
-      acc.steps += 1;
-      acc.it_ms += ims.iters;
-      acc.it_mech += imech.iters;
-      acc.it_ms_last = ims.iters;
-      acc.it_mech_last = imech.iters;
-      acc.res_ms_last = ims.relres;
-      acc.res_mech_last = imech.relres;
-      acc.noconv += ims.noconv + imech.noconv;
-      for (int k = 0; k < 8; ++k) {
-        acc.it_gs_last[k] = k < ngs ? ig[k].iters : 0;
-        if (k < ngs) {
-          acc.it_gs += ig[k].iters;
-          acc.noconv += ig[k].noconv;
+      TK(GSPM_KCLASS_POINTWISE, launch_project<T>(L_, SG_, ld, x_, mag_, m_, dmv(), inv_nmag(), red_));
+      for (int sg = 0; sg < nseg_; ++sg) {
+        gspm_step_stats& a = acc[sg];
+        a.steps += 1;
+        a.it_ms += ims[sg].iters;
+        a.it_mech += imech[sg].iters;
+        a.it_ms_last = ims[sg].iters;
+        a.it_mech_last = imech[sg].iters;
+        a.res_ms_last = ims[sg].relres;
+        a.res_mech_last = imech[sg].relres;
+        a.noconv += ims[sg].noconv + imech[sg].noconv;
+        for (int k = 0; k < 8; ++k) {
+          a.it_gs_last[k] = k < ngs ? ig[k][sg].iters : 0;
+          if (k < ngs) {
+            a.it_gs += ig[k][sg].iters;
+            a.noconv += ig[k][sg].noconv;
+          }
         }
       }
     }
+    int noconv = 0;
+    for (auto& a : acc) noconv += a.noconv;
     if (st) {
-      double hs[4];
-      CK(cudaMemcpyAsync(hs, scal_ + kMbar, 3 * sizeof(double), cudaMemcpyDeviceToHost, L_.stream));
-      CK(cudaMemcpyAsync(hs + 3, dm, sizeof(double), cudaMemcpyDeviceToHost, L_.stream));
+      CK(cudaMemcpyAsync(host_scal_, scal_, 13 * nseg_ * sizeof(double), cudaMemcpyDeviceToHost,
+                         L_.stream));
       CK(cudaStreamSynchronize(L_.stream));
-      acc.m_bar[0] = hs[0];
-      acc.m_bar[1] = hs[1];
-      acc.m_bar[2] = hs[2];
-      acc.dm_last = hs[3];
-      *st = acc;
+      for (int sg = 0; sg < nseg_; ++sg) {
+        for (int a = 0; a < 3; ++a) acc[sg].m_bar[a] = host_scal_[3 * sg + a];
+        acc[sg].dm_last = host_scal_[12 * nseg_ + sg];
+        st[sg] = acc[sg];
+      }
     }
     CK(cudaGetLastError());
-    return acc.noconv ? GSPM_ENOCONV : GSPM_OK;
+    return noconv ? GSPM_ENOCONV : GSPM_OK;
   }
 
   int solve_elastic(const double* m, double* u, int where, int x0_mode, const double* x0,
@@ -310,33 +397,44 @@ class Engine final : public EngineBase {
       set_error("solve_elastic: m is NULL");
       return GSPM_EINVAL;
     }
-    DevParams D = dev_params(nullptr);
+    DevParams D = dev_params();
     // magnetisation into the m* buffer (the context's m is left alone)
     ST(import_field(m, where, 3, ms_, ld, 1, mag_));
-    if (x0_mode == 0) {
-      CK(cudaMemsetAsync(u_, 0, 3 * n * sizeof(double), L_.stream));
-    } else if (x0_mode == 2) {
+    if (x0_mode == 2) {
       if (!x0) {
         set_error("solve_elastic: x0_mode 2 needs x0");
         return GSPM_EINVAL;
       }
-      ST(import_field(x0, where, 3, u_, 1, 3, nullptr));
-    } else if (x0_mode != 1) {
-      set_error("solve_elastic: bad x0_mode %d", x0_mode);
-      return GSPM_EINVAL;
+      ST(import_field(x0, where, 3, utmp_, 1, 3, nullptr));
+      CK(cudaMemcpyAsync(u2_, u_, 3 * n * sizeof(T), cudaMemcpyDeviceToDevice, L_.stream));
+      CK(cudaMemcpyAsync(u_, utmp_, 3 * n * sizeof(T), cudaMemcpyDeviceToDevice, L_.stream));
+    } else {
+      static const int map[5] = {GSPM_X0_ZERO, GSPM_X0_PREV, -1, GSPM_X0_EXTRAPOLATE,
+                                 GSPM_X0_LEARNED};
+      if (x0_mode < 0 || x0_mode > 4) {
+        set_error("solve_elastic: bad x0_mode %d", x0_mode);
+        return GSPM_EINVAL;
+      }
+      ST(mech_initial_guess(ms_, map[x0_mode]));
     }
     TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, ms_, ld, mag_, D, E0_, sig0_));
-    TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, n, 6, E0_, ld, 1, nullptr, w_, scal_ + kEbar, scal_ + kEext, red_));
-    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, G_, sig0_, b_, pin_));
-    SolveInfo info;
-    ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, 3 * n,
-                     rtol > 0 ? rtol : opt_.rtol_mech, &info));
-    TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, F_, u_, invML_, scal_ + kEbar, E_, ld));
+    TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
+    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_));
+    std::vector<SolveInfo> info;
+    ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, rtol > 0 ? rtol : opt_.rtol_mech, &info));
+    TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
     if (u) ST(export_field(u_, 1, 3, 3, u, where));
     CK(cudaStreamSynchronize(L_.stream));
-    if (iters) *iters = info.iters;
-    if (relres) *relres = info.relres;
-    return info.noconv ? GSPM_ENOCONV : GSPM_OK;
+    int it = 0, nc = 0;
+    double rel = 0.0;
+    for (auto& i : info) {
+      it = std::max(it, i.iters);
+      rel = std::max(rel, i.relres);
+      nc += i.noconv;
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    return nc ? GSPM_ENOCONV : GSPM_OK;
   }
 
   int volume_avg(const double* f, int where, int nc, double* out) override {
@@ -346,11 +444,12 @@ class Engine final : public EngineBase {
     }
     const double* src = f;
     if (where == GSPM_HOST) {
-      CK(cudaMemcpyAsync(stage_, f, n_ * nc * sizeof(double), cudaMemcpyHostToDevice, L_.stream));
+      CK(cudaMemcpyAsync(stage_, f, nodes_ * nc * sizeof(double), cudaMemcpyHostToDevice,
+                         L_.stream));
       src = stage_;
     }
-    CK(launch_wsum<double>(L_, n_, nc, src, 1, nc, perm_, w_, scal_ + kAvg, nullptr, red_));
-    CK(cudaMemcpyAsync(out, scal_ + kAvg, nc * sizeof(double), cudaMemcpyDeviceToHost, L_.stream));
+    CK(launch_wsum<double>(L_, SG_, nc, src, 1, nc, perm_, w_, avg(), nullptr, red_));
+    CK(cudaMemcpyAsync(out, avg(), nseg_ * nc * sizeof(double), cudaMemcpyDeviceToHost, L_.stream));
     CK(cudaStreamSynchronize(L_.stream));
     return GSPM_OK;
   }
@@ -366,18 +465,18 @@ class Engine final : public EngineBase {
         const T* val = op == GSPM_OP_K_MS ? Kms_ : op == GSPM_OP_A_EPS ? Aeps_
                      : op == GSPM_OP_A_AEPS ? Aaeps_ : M_;
         ST(import_field(x, where, 1, tin_, 1, 1, nullptr));
-        CK(launch_spmv<T>(L_, A_, val, 1, tin_, tout_));
+        CK(launch_spmv<T>(L_, A_, val, 1, tin_, tout_, var_scalar_));
         ST(export_field(tout_, 1, 1, 1, y, where));
         break;
       }
       case GSPM_OP_K_MECH:
         ST(import_field(x, where, 3, tin_, 1, 3, nullptr));
-        CK(launch_spmv<T>(L_, A_, Kmech_, 9, tin_, tout_));
+        CK(launch_spmv<T>(L_, A_, Kmech_, 9, tin_, tout_, var_block_));
         ST(export_field(tout_, 1, 3, 3, y, where));
         break;
       case GSPM_OP_DIV:
         ST(import_field(x, where, 3, tin_, ld, 1, nullptr));
-        CK(launch_fdiv<T>(L_, A_, F_, tin_, ld, b_, pin_));
+        CK(launch_fdiv<T>(L_, A_, SG_, F_, tin_, ld, b_));
         ST(export_field(b_, 1, 1, 1, y, where));
         break;
       case GSPM_OP_GRAD:
@@ -403,11 +502,18 @@ class Engine final : public EngineBase {
       case GSPM_FIELD_M: ST(import_field(data, where, 3, m_, ld, 1, mag_)); break;
       case GSPM_FIELD_U:
         ST(import_field(data, where, 1, U_, 1, 1, nullptr));
-        CK(cudaMemsetAsync(U_ + pin_, 0, sizeof(double), L_.stream));
+        for (int sg = 0; sg < nseg_; ++sg)
+          CK(cudaMemsetAsync(U_ + hb_.seg_pin[sg], 0, sizeof(T), L_.stream));
         break;
       case GSPM_FIELD_DISP:
         ST(import_field(data, where, 3, u_, 1, 3, nullptr));
-        CK(cudaMemsetAsync(u_ + 3 * pin_, 0, 3 * sizeof(double), L_.stream));
+        for (int sg = 0; sg < nseg_; ++sg)
+          CK(cudaMemsetAsync(u_ + 3 * hb_.seg_pin[sg], 0, 3 * sizeof(T), L_.stream));
+        break;
+      case GSPM_FIELD_DISP_PREV:
+        ST(import_field(data, where, 3, u2_, 1, 3, nullptr));
+        for (int sg = 0; sg < nseg_; ++sg)
+          CK(cudaMemsetAsync(u2_ + 3 * hb_.seg_pin[sg], 0, 3 * sizeof(T), L_.stream));
         break;
       default:
         set_error("set_field: field %d is not writable", field);
@@ -427,6 +533,7 @@ class Engine final : public EngineBase {
       case GSPM_FIELD_M: ST(export_field(m_, ld, 1, 3, data, where)); break;
       case GSPM_FIELD_U: ST(export_field(U_, 1, 1, 1, data, where)); break;
       case GSPM_FIELD_DISP: ST(export_field(u_, 1, 3, 3, data, where)); break;
+      case GSPM_FIELD_DISP_PREV: ST(export_field(u2_, 1, 3, 3, data, where)); break;
       case GSPM_FIELD_HD: ST(export_field(hd_, ld, 1, 3, data, where)); break;
       case GSPM_FIELD_STRAIN: ST(export_field(E_, ld, 1, 6, data, where)); break;
       case GSPM_FIELD_H: ST(export_field(h_, ld, 1, 3, data, where)); break;
@@ -438,10 +545,159 @@ class Engine final : public EngineBase {
     return GSPM_OK;
   }
 
+
+  int set_x0_mode(int mode) override {
+    if (mode < GSPM_X0_PREV || mode > GSPM_X0_LEARNED) {
+      set_error("set_x0_mode: bad mode %d", mode);
+      return GSPM_EINVAL;
+    }
+    if (mode == GSPM_X0_LEARNED && nseg_ != 1) {
+      set_error("set_x0_mode: the learned initial guess is single-mesh only");
+      return GSPM_ESTATE;
+    }
+    if (mode == GSPM_X0_LEARNED && !net_ready_) {
+      set_error("set_x0_mode: the learned warm start needs parameters (gspm_mpnn_set_params)");
+      return GSPM_ESTATE;
+    }
+    x0_mode_ = mode;
+    return GSPM_OK;
+  }
+
+  // out != NULL: read parameters; in != NULL: write them (and refresh the BF16 copies)
+  int mpnn_params(float* out, const float* in, int64_t count) override {
+    if (count != kParams) {
+      set_error("mpnn params: count %lld, the network has %d", (long long)count, kParams);
+      return GSPM_EINVAL;
+    }
+    ST(net_alloc());
+    if (in) {
+      CK(cudaMemcpyAsync(params_, in, kParams * sizeof(float), cudaMemcpyHostToDevice, L_.stream));
+      CK(cudaMemsetAsync(adam_m_, 0, kParams * sizeof(float), L_.stream));
+      CK(cudaMemsetAsync(adam_v_, 0, kParams * sizeof(float), L_.stream));
+      adam_t_ = 0;
+      CK(mpnn_refresh_bf16(L_, WinT_, WT_, params_));
+      CK(cudaStreamSynchronize(L_.stream));
+      net_ready_ = true;
+    }
+    if (out) {
+      CK(cudaMemcpyAsync(out, params_, kParams * sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
+      CK(cudaStreamSynchronize(L_.stream));
+    }
+    return GSPM_OK;
+  }
+
+  int mpnn_predict(const double* m, const double* up, const double* up2, double* out, int what,
+                   int where) override {
+    if (!net_ready_) {
+      set_error("mpnn_predict: no parameters set");
+      return GSPM_ESTATE;
+    }
+    if (!m || !out || (what != 0 && what != 1)) {
+      set_error("mpnn_predict: need m, out and what in {0, 1}");
+      return GSPM_EINVAL;
+    }
+    ST(import_field(m, where, 3, ms_, ld_, 1, mag_));
+    if (up) ST(import_field(up, where, 3, uin_, 1, 3, nullptr));
+    else CK(cudaMemsetAsync(uin_, 0, 3 * n_ * sizeof(T), L_.stream));
+    if (up2) ST(import_field(up2, where, 3, uin2_, 1, 3, nullptr));
+    else CK(cudaMemsetAsync(uin2_, 0, 3 * n_ * sizeof(T), L_.stream));
+    ST(net_forward(ms_, uin_, uin2_, nullptr));
+    if (what == 0) {
+      CK(mpnn_output<T>(L_, n_, net_, H_[kLayers], 0, Y_, nullptr, nullptr, 0.0, nullptr));
+      CK((launch_convert<float, T>(L_, 3 * n_, Y_, utmp_)));
+    } else {
+      CK(mpnn_output(L_, n_, net_, H_[kLayers], 1, nullptr, uin_, uin2_, u_scale(), utmp_));
+    }
+    ST(export_field(utmp_, 1, 3, 3, out, where));
+    CK(cudaStreamSynchronize(L_.stream));
+    return GSPM_OK;
+  }
+
+  int mpnn_dataset_reserve(int capacity) override {
+    if (capacity < 1) {
+      set_error("mpnn_dataset_reserve: capacity must be positive");
+      return GSPM_EINVAL;
+    }
+    ST(net_alloc());
+    if (ds_F_) {
+      set_error("mpnn_dataset_reserve: dataset already reserved");
+      return GSPM_ESTATE;
+    }
+    ST(mem_.alloc(&ds_F_, (int64_t)capacity * n_ * kFeat));
+    ST(mem_.alloc(&ds_T_, (int64_t)capacity * n_ * 3));
+    ds_cap_ = capacity;
+    ds_n_ = 0;
+    return GSPM_OK;
+  }
+
+  // one (m, u_prev, u_prev2) -> u* pair: stores the features and the target
+  // t = (u* - (2 u_prev - u_prev2)) / u_s
+  int mpnn_dataset_add(const double* m, const double* up, const double* up2, const double* ustar,
+                       int where, int* index) override {
+    if (!ds_F_ || ds_n_ >= ds_cap_) {
+      set_error("mpnn_dataset_add: dataset not reserved or full");
+      return GSPM_ESTATE;
+    }
+    if (!m || !ustar) {
+      set_error("mpnn_dataset_add: need m and u*");
+      return GSPM_EINVAL;
+    }
+    ST(import_field(m, where, 3, ms_, ld_, 1, mag_));
+    if (up) ST(import_field(up, where, 3, uin_, 1, 3, nullptr));
+    else CK(cudaMemsetAsync(uin_, 0, 3 * n_ * sizeof(T), L_.stream));
+    if (up2) ST(import_field(up2, where, 3, uin2_, 1, 3, nullptr));
+    else CK(cudaMemsetAsync(uin2_, 0, 3 * n_ * sizeof(T), L_.stream));
+    ST(import_field(ustar, where, 3, utmp_, 1, 3, nullptr));
+    __nv_bfloat16* F = ds_F_ + (int64_t)ds_n_ * n_ * kFeat;
+    CK(mpnn_features<T>(L_, n_, ms_, ld_, mag_, uin_, uin2_, P_.l100, P_.l111, l_scale(),
+                        u_scale(), F));
+    CK(launch_target(ds_T_ + (int64_t)ds_n_ * n_ * 3));
+    if (index) *index = ds_n_;
+    ++ds_n_;
+    if (where == GSPM_HOST) CK(cudaStreamSynchronize(L_.stream));
+    return GSPM_OK;
+  }
+
+  int mpnn_loss_grad(int pair, double* loss, float* grad) override {
+    if (!net_ready_ || pair < 0 || pair >= ds_n_) {
+      set_error("mpnn_loss_grad: need parameters and a stored pair");
+      return GSPM_EINVAL;
+    }
+    ST(net_step(pair, /*update=*/false, 0.0));
+    float l = 0.f;
+    CK(cudaMemcpyAsync(&l, loss_, sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
+    if (grad) CK(cudaMemcpyAsync(grad, grad_, kParams * sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
+    CK(cudaStreamSynchronize(L_.stream));
+    if (loss) *loss = (double)l / (3.0 * (double)n_);
+    return GSPM_OK;
+  }
+
+  // iterations of Adam, each on one stored pair drawn with a splitmix64 stream of `seed`
+  int mpnn_train(int iters, double lr, uint64_t seed, double* l0, double* l1) override {
+    if (!net_ready_ || ds_n_ < 1 || iters < 1) {
+      set_error("mpnn_train: need parameters, a non-empty dataset and iterations >= 1");
+      return GSPM_EINVAL;
+    }
+    float lf = 0.f, ll = 0.f;
+    for (int it = 0; it < iters; ++it) {
+      uint64_t z = seed + (uint64_t)(it + 1) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const int pair = (int)(z % (uint64_t)ds_n_);
+      ST(net_step(pair, /*update=*/true, lr));
+      if (it == 0) CK(cudaMemcpyAsync(&lf, loss_, sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
+    }
+    CK(cudaMemcpyAsync(&ll, loss_, sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
+    CK(cudaStreamSynchronize(L_.stream));
+    if (l0) *l0 = (double)lf / (3.0 * (double)n_);
+    if (l1) *l1 = (double)ll / (3.0 * (double)n_);
+    return GSPM_OK;
+  }
+
  private:
   static constexpr int kSlotMs = 0, kSlotMech = 1, kSlotGs0 = 2, kSlotGs1 = 3, kSlotGs2 = 4,
                        kSlotGsD = 5, kSolveSlots = 6;
-  static constexpr int kMbar = 0, kMbarS = 3, kEbar = 6, kEext = 12, kDm = 18, kAvg = 20;
 
   template <typename X>
   int upload(T** dst, const std::vector<X>& src) {
@@ -455,7 +711,7 @@ class Engine final : public EngineBase {
     return GSPM_OK;
   }
 
-  DevParams dev_params(const double* H) const {
+  DevParams dev_params() const {
     DevParams D;
     D.kappa = P_.kappa;
     D.me_coef = P_.me_coef;
@@ -464,7 +720,6 @@ class Engine final : public EngineBase {
     D.C11 = P_.C11;
     D.C12 = P_.C12;
     D.C44 = P_.C44;
-    for (int a = 0; a < 3; ++a) D.hz[a] = H ? H[a] / P_.Ms : 0.0;
     for (int k = 0; k < 9; ++k) D.Nd[k] = P_.Nd[k];
     D.dtau = P_.dtau;
     D.alpha = P_.alpha;
@@ -477,7 +732,8 @@ class Engine final : public EngineBase {
                    const uint8_t* mask) {
     const double* s = src;
     if (where == GSPM_HOST) {
-      CK(cudaMemcpyAsync(stage_, src, n_ * nc * sizeof(double), cudaMemcpyHostToDevice, L_.stream));
+      CK(cudaMemcpyAsync(stage_, src, nodes_ * nc * sizeof(double), cudaMemcpyHostToDevice,
+                         L_.stream));
       s = stage_;
     } else if (where != GSPM_DEVICE) {
       set_error("bad `where` %d", where);
@@ -493,7 +749,8 @@ class Engine final : public EngineBase {
       CK(launch_export<X>(L_, n_, nc, src, cs, ns, perm_, dst));
     } else if (where == GSPM_HOST) {
       CK(launch_export<X>(L_, n_, nc, src, cs, ns, perm_, stage_));
-      CK(cudaMemcpyAsync(dst, stage_, n_ * nc * sizeof(double), cudaMemcpyDeviceToHost, L_.stream));
+      CK(cudaMemcpyAsync(dst, stage_, nodes_ * nc * sizeof(double), cudaMemcpyDeviceToHost,
+                         L_.stream));
     } else {
       set_error("bad `where` %d", where);
       return GSPM_EINVAL;
@@ -501,75 +758,276 @@ class Engine final : public EngineBase {
     return GSPM_OK;
   }
 
-  // Launch CG iterations in chunks; after each chunk read the device status block once.
+  // Launch CG iterations in chunks; after each chunk read the number of still-active
+  // segments (one int), then the per-segment status blocks once at the end.
   template <class Iter>
-  int cg_loop(int slot, Iter iter, SolveInfo* info) {
-    CGState* st = cg_ + slot;
+  int cg_loop(int slot, Iter iter, std::vector<SolveInfo>* info) {
+    CGState* st = cg_ + (int64_t)slot * nseg_;
     int chunk = std::max(1, pred_[slot]);
     int launched = 0;
     for (;;) {
       for (int c = 0; c < chunk; ++c) ST(iter());
       launched += chunk;
-      CK(cudaMemcpyAsync(host_state_, st, sizeof(CGState), cudaMemcpyDeviceToHost, L_.stream));
+      CK(cudaMemcpyAsync(host_active_, nactive_ + slot, sizeof(int), cudaMemcpyDeviceToHost,
+                         L_.stream));
       CK(cudaStreamSynchronize(L_.stream));
-      if (!host_state_->active || launched > opt_.max_iter + 1) break;
+      if (*host_active_ <= 0 || launched > opt_.max_iter + 1) break;
       // first solve of a kind: grow geometrically; afterwards small top-up chunks
       chunk = seen_[slot] ? 3 : std::max(2, std::min(32, launched / 4));
     }
-    int it = 0;
-    double rel = 0.0;
-    for (int k = 0; k < host_state_->nr; ++k) {
-      it = std::max(it, host_state_->r[k].iters);
-      const double bb = host_state_->r[k].bb;
-      rel = std::max(rel, bb > 0 ? std::sqrt(host_state_->r[k].rr / bb) : 0.0);
+    CK(cudaMemcpyAsync(host_state_, st, nseg_ * sizeof(CGState), cudaMemcpyDeviceToHost,
+                       L_.stream));
+    CK(cudaStreamSynchronize(L_.stream));
+    info->assign(nseg_, SolveInfo());
+    int itmax = 0;
+    for (int sg = 0; sg < nseg_; ++sg) {
+      const CGState& c = host_state_[sg];
+      int it = 0;
+      double rel = 0.0;
+      for (int k = 0; k < c.nr; ++k) {
+        it = std::max(it, c.r[k].iters);
+        const double bb = c.r[k].bb;
+        rel = std::max(rel, bb > 0 ? std::sqrt(c.r[k].rr / bb) : 0.0);
+      }
+      (*info)[sg].iters = it;
+      (*info)[sg].relres = rel;
+      (*info)[sg].noconv = c.noconv;
+      itmax = std::max(itmax, it);
     }
-    pred_[slot] = std::max(1, it);
+    pred_[slot] = std::max(1, itmax);
     seen_[slot] = 1;
-    info->iters = it;
-    info->relres = rel;
-    info->noconv = host_state_->noconv;
     return GSPM_OK;
   }
 
   // K x = b for the pinned Omega_c systems (B = 1 scalar K^ms, B = 9 block K^mech)
-  int solve_general(int slot, const T* val, int B, const double* b, double* x, int64_t len,
-                    double rtol, SolveInfo* info) {
-    CGState* st = cg_ + slot;
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, val, B, b, x, r_, p_, st, rtol, opt_.max_iter, red_));
+  int solve_general(int slot, const T* val, int B, const T* b, T* x, double rtol,
+                    std::vector<SolveInfo>* info) {
+    CGState* st = cg_ + (int64_t)slot * nseg_;
+    int* na = nactive_ + slot;
+    const int epr = B == 9 ? 3 : 1;
+    const int64_t len = epr * n_;
+    CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_));
     auto iter = [&]() -> int {
-      TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, val, B, 1, len, p_, q_, st, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, len, 1, len, x, r_, p_, q_, st, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, len, 1, len, r_, p_, st));
+      TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, epr, 1, len, x, r_, p_, q_, st, na, red_));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, epr, 1, len, r_, p_, st));
       return GSPM_OK;
     };
     ST(cg_loop(slot, iter, info));
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_zero(L_, len, x, st));
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_zero<T>(L_, SG_, epr, x, st));
     return GSPM_OK;
   }
 
-  // (M + c eps K) g = M f for nr right-hand sides held in x slots [slot0, slot0 + nr)
-  int solve_gs(int slot, const T* aval, int slot0, int nr, SolveInfo* info) {
-    CGState* st = cg_ + slot;
-    double* x = x_ + slot0 * ld_;
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_init_gs<T>(L_, A_, aval, M_, nr, ld_, x, r_, p_, st, opt_.rtol_gs, opt_.max_iter,
-                            red_));
+  // (M + c eps K) g = M f for nr right-hand sides held in x slots [slot0, slot0 + nr); info[k]
+  // receives, per segment, the solve of right-hand side k
+  int solve_gs(int slot, const T* aval, int slot0, int nr, std::vector<SolveInfo>* info) {
+    CGState* st = cg_ + (int64_t)slot * nseg_;
+    int* na = nactive_ + slot;
+    T* x = x_ + slot0 * ld_;
+    CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_init_gs<T>(L_, A_, SG_, aval, M_, nr, ld_, x, r_, p_, st, na, opt_.rtol_gs, opt_.max_iter, red_));
     auto iter = [&]() -> int {
-      TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, aval, 1, nr, ld_, p_, q_, st, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, n_, nr, ld_, x, r_, p_, q_, st, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, n_, nr, ld_, r_, p_, st));
+      TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, SG_, aval, 1, nr, ld_, p_, q_, st, red_, var_scalar_));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, 1, nr, ld_, x, r_, p_, q_, st, na, red_));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st));
       return GSPM_OK;
     };
-    SolveInfo tot;
+    std::vector<SolveInfo> tot;
     ST(cg_loop(slot, iter, &tot));
     for (int k = 0; k < nr; ++k) {
-      info[k].iters = host_state_->r[k].iters;
-      const double bb = host_state_->r[k].bb;
-      info[k].relres = bb > 0 ? std::sqrt(host_state_->r[k].rr / bb) : 0.0;
-      info[k].noconv = 0;
+      info[k].assign(nseg_, SolveInfo());
+      for (int sg = 0; sg < nseg_; ++sg) {
+        const CGRhs& c = host_state_[sg].r[k];
+        info[k][sg].iters = c.iters;
+        info[k][sg].relres = c.bb > 0 ? std::sqrt(c.rr / c.bb) : 0.0;
+        info[k][sg].noconv = k == 0 ? tot[sg].noconv : 0;
+      }
     }
-    info[0].noconv = tot.noconv;
     return GSPM_OK;
   }
+
+  // per-segment device scalars: m_bar [3S], m_bar* [3S], E_bar [6S], <|dm|> [S], H/m_s [3S],
+  // 1/(magnetic nodes) [S], volume averages [9S]; then C^-1 sigma_ext [6]
+  static constexpr int kScalPerSeg = 26;
+  double* mbar() const { return scal_; }
+  double* mbar_s() const { return scal_ + 3 * nseg_; }
+  double* ebar() const { return scal_ + 6 * nseg_; }
+  double* dmv() const { return scal_ + 12 * nseg_; }
+  double* hz() const { return scal_ + 13 * nseg_; }
+  double* inv_nmag() const { return scal_ + 16 * nseg_; }
+  double* avg() const { return scal_ + 17 * nseg_; }
+  double* eext() const { return scal_ + 26 * nseg_; }
+
+  // segment tables and the work items of the reducing kernels
+  int init_segments() {
+    const int S = nseg_;
+    // items of about `item_slices_` slices: enough items for ~4 per resident block slot
+    const int64_t resident = (int64_t)L_.sms * 6;
+    int64_t u = nslices_ / std::max<int64_t>(1, 4 * resident);
+    item_slices_ = (int)std::max<int64_t>(1, std::min<int64_t>(64, u));
+    std::vector<int32_t> iseg, isl0, isl1, sitem0(S), snit(S);
+    for (int sg = 0; sg < S; ++sg) {
+      sitem0[sg] = (int32_t)iseg.size();
+      const int64_t a = hb_.seg_sl0[sg], b = a + hb_.seg_nsl[sg];
+      for (int64_t x = a; x < b; x += item_slices_) {
+        iseg.push_back(sg);
+        isl0.push_back((int32_t)x);
+        isl1.push_back((int32_t)std::min<int64_t>(b, x + item_slices_));
+      }
+      snit[sg] = (int32_t)iseg.size() - sitem0[sg];
+    }
+    nitems_ = (int)iseg.size();
+    int32_t *d_sos, *d_iseg, *d_isl0, *d_isl1, *d_si0, *d_sni;
+    int64_t *d_r0, *d_nr, *d_pin;
+    unsigned* d_cnt;
+    ST(mem_.alloc(&d_sos, nslices_));
+    ST(mem_.alloc(&d_iseg, nitems_));
+    ST(mem_.alloc(&d_isl0, nitems_));
+    ST(mem_.alloc(&d_isl1, nitems_));
+    ST(mem_.alloc(&d_si0, S));
+    ST(mem_.alloc(&d_sni, S));
+    ST(mem_.alloc(&d_r0, S));
+    ST(mem_.alloc(&d_nr, S));
+    ST(mem_.alloc(&d_pin, S));
+    ST(mem_.alloc(&d_cnt, S));
+    CK(cudaMemcpy(d_sos, hb_.seg_of_slice.data(), nslices_ * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_iseg, iseg.data(), nitems_ * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_isl0, isl0.data(), nitems_ * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_isl1, isl1.data(), nitems_ * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_si0, sitem0.data(), S * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_sni, snit.data(), S * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_r0, hb_.seg_row0.data(), S * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_nr, hb_.seg_nrow.data(), S * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_pin, hb_.seg_pin.data(), S * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemset(d_cnt, 0, S * sizeof(unsigned)));
+    SG_ = DSeg{S, nitems_, d_sos, d_iseg, d_isl0, d_isl1, d_si0, d_sni, d_r0, d_nr, d_pin, d_cnt};
+    ST(mem_.alloc(&red_.partial, (int64_t)nitems_ * kRedComp));
+    return GSPM_OK;
+  }
+
+  double l_scale() const { return std::max(std::fabs(P_.l100), std::fabs(P_.l111)) > 0
+                                      ? std::max(std::fabs(P_.l100), std::fabs(P_.l111)) : 1.0; }
+  double u_scale() const { return l_scale() * h_scale_; }
+
+  int net_alloc() {
+    if (params_) return GSPM_OK;
+    if (nseg_ != 1) {
+      set_error("the learned initial guess is single-mesh only");
+      return GSPM_ESTATE;
+    }
+    CK(mpnn_setup_smem());
+    ST(mem_.alloc(&params_, kParams));
+    ST(mem_.alloc(&grad_, kParams));
+    ST(mem_.alloc(&adam_m_, kParams));
+    ST(mem_.alloc(&adam_v_, kParams));
+    ST(mem_.alloc(&loss_, 4));
+    ST(mem_.alloc(&WinT_, kHid * kFeat));
+    for (int l = 0; l < kLayers; ++l) ST(mem_.alloc(&WT_[l], kHid * 2 * kHid));
+    ST(mem_.alloc(&F_in_, n_ * kFeat));
+    for (int l = 0; l <= kLayers; ++l) ST(mem_.alloc(&H_[l], n_ * kHid));
+    ST(mem_.alloc(&Y_, 3 * n_));
+    net_.WinT = WinT_;
+    net_.b_in = params_ + kOffBin;
+    for (int l = 0; l < kLayers; ++l) {
+      net_.WT[l] = WT_[l];
+      net_.Wf[l] = params_ + kOffW[l];
+      net_.b[l] = params_ + kOffW[l] + 2 * kHid * kHid;
+    }
+    net_.Wout = params_ + kOffWout;
+    net_.bout = params_ + kOffBout;
+    net_.A = agg_;
+    net_.At = aggT_;
+    return GSPM_OK;
+  }
+
+  int net_train_alloc() {
+    if (dHa_) return GSPM_OK;
+    for (int l = 0; l < kLayers; ++l) ST(mem_.alloc(&Z_[l], n_ * kHid));
+    ST(mem_.alloc(&dHa_, n_ * kHid));
+    ST(mem_.alloc(&dHb_, n_ * kHid));
+    ST(mem_.alloc(&dZ_, n_ * kHid));
+    ST(mem_.alloc(&part_, (int64_t)L_.max_blocks * (2 * kHid * kHid + kHid)));
+    return GSPM_OK;
+  }
+
+  // features of (m, up, up2) into F_in_, then the forward pass (Z saved when training)
+  int net_forward(const T* m, const T* up, const T* up2, __nv_bfloat16* const* Z) {
+    CK(mpnn_features<T>(L_, n_, m, ld_, mag_, up, up2, P_.l100, P_.l111, l_scale(), u_scale(),
+                        F_in_));
+    CK(mpnn_forward(L_, n_, A_, net_, F_in_, H_, Z));
+    return GSPM_OK;
+  }
+
+  int net_step(int pair, bool update, double lr) {
+    ST(net_train_alloc());
+    const __nv_bfloat16* F = ds_F_ + (int64_t)pair * n_ * kFeat;
+    CK(mpnn_forward(L_, n_, A_, net_, F, H_, Z_));
+    CK(mpnn_output<T>(L_, n_, net_, H_[kLayers], 0, Y_, nullptr, nullptr, 0.0, nullptr));
+    CK(mpnn_backward(L_, n_, A_, net_, F, H_, Z_, Y_, ds_T_ + (int64_t)pair * n_ * 3, dHa_, dHb_,
+                     dZ_, part_, grad_, loss_));
+    if (update) {
+      ++adam_t_;
+      CK(mpnn_adam(L_, params_, grad_, adam_m_, adam_v_, (float)lr, adam_t_));
+      CK(mpnn_refresh_bf16(L_, WinT_, WT_, params_));
+    }
+    return GSPM_OK;
+  }
+
+  // t = (u* - (2 up - up2)) / u_s from utmp_ (u*), uin_, uin2_
+  cudaError_t launch_target(float* t) {
+    return launch_scaled_diff<T>(L_, 3 * n_, utmp_, uin_, uin2_, 1.0 / u_scale(), t);
+  }
+
+  // x0 of the mechanical CG, leaving u_prev2 <- u_prev and u <- x0 (u_prev = u on entry)
+  int mech_initial_guess(const T* m, int mode) {
+    const int64_t len = 3 * n_;
+    switch (mode) {
+      case GSPM_X0_PREV:
+        CK(cudaMemcpyAsync(u2_, u_, len * sizeof(T), cudaMemcpyDeviceToDevice, L_.stream));
+        break;
+      case GSPM_X0_ZERO:
+        CK(cudaMemcpyAsync(u2_, u_, len * sizeof(T), cudaMemcpyDeviceToDevice, L_.stream));
+        CK(cudaMemsetAsync(u_, 0, len * sizeof(T), L_.stream));
+        break;
+      case GSPM_X0_EXTRAPOLATE:
+        TK(GSPM_KCLASS_POINTWISE, launch_extrapolate<T>(L_, len, u_, u2_));
+        break;
+      case GSPM_X0_LEARNED:
+        if (!net_ready_) {
+          set_error("learned warm start requested without parameters");
+          return GSPM_ESTATE;
+        }
+        ST(timed(GSPM_KCLASS_LEARNED, [&]() -> int {
+          ST(net_forward(m, u_, u2_, nullptr));
+          CK(mpnn_output(L_, n_, net_, H_[kLayers], 1, nullptr, u_, u2_, u_scale(), utmp_));
+          return GSPM_OK;
+        }));
+        CK(cudaMemcpyAsync(u2_, u_, len * sizeof(T), cudaMemcpyDeviceToDevice, L_.stream));
+        CK(cudaMemcpyAsync(u_, utmp_, len * sizeof(T), cudaMemcpyDeviceToDevice, L_.stream));
+        CK(cudaMemsetAsync(u_ + 3 * hb_.seg_pin[0], 0, 3 * sizeof(T), L_.stream));
+        break;
+      default:
+        set_error("bad x0 mode %d", mode);
+        return GSPM_EINVAL;
+    }
+    return GSPM_OK;
+  }
+
+  // learned warm start state
+  int x0_mode_ = GSPM_X0_PREV;
+  bool net_ready_ = false;
+  double h_scale_ = 1.0;
+  float *params_ = nullptr, *grad_ = nullptr, *adam_m_ = nullptr, *adam_v_ = nullptr,
+        *loss_ = nullptr, *Y_ = nullptr, *agg_ = nullptr, *aggT_ = nullptr, *dHa_ = nullptr,
+        *dHb_ = nullptr, *dZ_ = nullptr, *part_ = nullptr, *ds_T_ = nullptr;
+  __nv_bfloat16 *WinT_ = nullptr, *F_in_ = nullptr, *ds_F_ = nullptr;
+  __nv_bfloat16* WT_[3] = {};
+  __nv_bfloat16* H_[4] = {};
+  __nv_bfloat16* Z_[3] = {};
+  int adam_t_ = 0, ds_cap_ = 0, ds_n_ = 0;
+  MpnnDev net_{};
+  T *u2_ = nullptr, *utmp_ = nullptr, *uin_ = nullptr, *uin2_ = nullptr;
 
   // launch f() bracketed by CUDA events when class cls is being profiled
   template <class Fn>
@@ -595,12 +1053,17 @@ class Engine final : public EngineBase {
   size_t prof_used_ = 0;
   std::vector<int> prof_cls_;
   std::vector<cudaEvent_t> prof_ev_;
-  const HostMesh& hm_;
+  const HostBatch& hb_;
   Params P_;
   gspm_options opt_;
   Launch L_;
   DevMem mem_;
-  int64_t n_ = 0, ld_ = 0, nslices_ = 0, entries_ = 0, pin_ = 0, nmag_ = 0;
+  int64_t n_ = 0, ld_ = 0, nslices_ = 0, entries_ = 0, nmag_ = 0, nodes_ = 0;
+  int nseg_ = 1, nitems_ = 0, item_slices_ = 1;
+  DSeg SG_{};
+  int* nactive_ = nullptr;
+  int* host_active_ = nullptr;
+  double* host_scal_ = nullptr;
   DSell A_{};
   int64_t* sptr_ = nullptr;
   int32_t* slen_ = nullptr;
@@ -612,12 +1075,14 @@ class Engine final : public EngineBase {
   int64_t* perm_ = nullptr;
   T *m_ = nullptr, *ms_ = nullptr, *h_ = nullptr, *hd_ = nullptr, *E_ = nullptr, *E0_ = nullptr,
     *sig0_ = nullptr, *p_ = nullptr, *q_ = nullptr, *tin_ = nullptr, *tout_ = nullptr;
-  double *U_ = nullptr, *u_ = nullptr, *b_ = nullptr, *r_ = nullptr, *x_ = nullptr,
-         *stage_ = nullptr, *scal_ = nullptr;
+  T *U_ = nullptr, *u_ = nullptr, *b_ = nullptr, *r_ = nullptr, *x_ = nullptr;
+  double *stage_ = nullptr, *scal_ = nullptr;
   CGState* cg_ = nullptr;
   CGState* host_state_ = nullptr;
   Red red_{};
   int pred_[kSolveSlots];
+  int var_block_ = 0, var_scalar_ = 0;
+  float tune_ms_block_[kSpmvVariants] = {}, tune_ms_scalar_[kSpmvVariants] = {};
   int seen_[kSolveSlots] = {};
 };
 
@@ -626,8 +1091,8 @@ class Engine final : public EngineBase {
 using namespace gspm;
 
 struct gspm_ctx {
-  HostMesh hm;
-  HostSell hs;
+  std::vector<HostMesh> hm;   // per segment (host structures, exports)
+  HostBatch hb;               // concatenated batch (device layout)
   Params P;
   gspm_options opt;
   bool host_only = false;
@@ -635,14 +1100,10 @@ struct gspm_ctx {
   std::unique_ptr<EngineBase> eng;
 };
 
-extern "C" {
-
-const char* gspm_last_error(void) { return g_err.c_str(); }
-
-int gspm_mesh_load(const gspm_mesh_desc* mesh, const gspm_material* mat,
-                   const gspm_options* opt, gspm_ctx** out) {
-  if (!mesh || !mat || !opt || !out) {
-    set_error("mesh_load: null argument");
+static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_material* mat,
+                      const gspm_options* opt, gspm_ctx** out) {
+  if (!meshes || nmesh < 1 || !mat || !opt || !out) {
+    set_error("mesh_load: null argument or no mesh");
     return GSPM_EINVAL;
   }
   *out = nullptr;
@@ -658,23 +1119,69 @@ int gspm_mesh_load(const gspm_mesh_desc* mesh, const gspm_material* mat,
   c->opt = *opt;
   c->host_only = (opt->flags & GSPM_FLAG_HOST_ONLY) != 0;
   ST(make_params(mat, opt, &c->P));
-  ST(host_mesh_build(mesh, opt->ordering, &c->hm));
-  host_sell_build(c->hm, &c->hs);
-  if (!c->host_only) {
-    HostOps ops;
-    host_assemble(c->hm, c->hs, c->P, &ops);
+  c->hm.resize(nmesh);
+  std::vector<HostSell> hs(nmesh);
+  std::vector<HostOps> ops(nmesh);
+  for (int k = 0; k < nmesh; ++k) {
+    const int st = host_mesh_build(meshes + k, opt->ordering, &c->hm[k]);
+    if (st != GSPM_OK) {
+      if (nmesh > 1) {
+        std::string msg = g_err;
+        set_error("mesh %d: %s", k, msg.c_str());
+      }
+      return st;
+    }
+    host_sell_build(c->hm[k], &hs[k]);
+    if (!c->host_only) host_assemble(c->hm[k], hs[k], c->P, &ops[k]);
+  }
+  if (c->host_only) {
+    c->hb.sell = std::move(hs[0]);
+    c->hb.n_nodes = 0;
+    for (auto& h : c->hm) c->hb.n_nodes += h.n;
+  } else {
+    host_batch_build(c->hm, hs, ops, &c->hb);
     cudaStream_t s = (cudaStream_t)opt->stream;
     if (opt->precision == GSPM_PREC_F64) {
-      auto e = std::make_unique<Engine<double>>(c->hm, c->hs, ops, c->P, c->opt, s, &c->launches);
-      ST(e->init(c->hs, ops));
+      auto e = std::make_unique<Engine<double>>(c->hb, c->P, c->opt, s, &c->launches);
+      ST(e->init());
       c->eng = std::move(e);
     } else {
-      auto e = std::make_unique<Engine<float>>(c->hm, c->hs, ops, c->P, c->opt, s, &c->launches);
-      ST(e->init(c->hs, ops));
+      auto e = std::make_unique<Engine<float>>(c->hb, c->P, c->opt, s, &c->launches);
+      ST(e->init());
       c->eng = std::move(e);
     }
+    // operator values now live on the device
+    c->hb.ops = HostOps();
+    c->hb.sell.col.clear();
+    c->hb.sell.col.shrink_to_fit();
   }
   *out = c.release();
+  return GSPM_OK;
+}
+
+extern "C" {
+
+const char* gspm_last_error(void) { return g_err.c_str(); }
+
+int gspm_mesh_load(const gspm_mesh_desc* mesh, const gspm_material* mat,
+                   const gspm_options* opt, gspm_ctx** out) {
+  return load_batch(mesh, 1, mat, opt, out);
+}
+
+int gspm_batch_load(const gspm_mesh_desc* meshes, int n_meshes, const gspm_material* mat,
+                    const gspm_options* opt, gspm_ctx** out) {
+  return load_batch(meshes, n_meshes, mat, opt, out);
+}
+
+int gspm_batch_segment(const gspm_ctx* ctx, int seg, int64_t* node_offset, int64_t* n_nodes) {
+  if (!ctx || seg < 0 || seg >= (int)ctx->hm.size()) {
+    set_error("batch_segment: bad context or segment %d", seg);
+    return GSPM_EINVAL;
+  }
+  int64_t off = 0;
+  for (int k = 0; k < seg; ++k) off += ctx->hm[k].n;
+  if (node_offset) *node_offset = off;
+  if (n_nodes) *n_nodes = ctx->hm[seg].n;
   return GSPM_OK;
 }
 
@@ -689,18 +1196,34 @@ int gspm_mesh_info_get(const gspm_ctx* ctx, gspm_mesh_info* out) {
     set_error("mesh_info: null argument");
     return GSPM_EINVAL;
   }
-  out->n_stored = ctx->hm.n_stored;
-  out->n_unique = ctx->hm.n;
-  out->n_tets = ctx->hm.n_tets;
-  out->n_magnetic_nodes = ctx->hm.n_mag_nodes;
-  out->n_magnetic_tets = ctx->hm.n_mag_tets;
-  out->nnz = ctx->hm.rowptr.empty() ? 0 : ctx->hm.rowptr.back();
-  out->sell_entries = ctx->hs.entries;
-  out->volume = ctx->hm.volume;
-  out->volume_magnetic = ctx->hm.volume_mag;
+  memset(out, 0, sizeof(*out));
+  for (const HostMesh& h : ctx->hm) {
+    out->n_stored += h.n_stored;
+    out->n_unique += h.n;
+    out->n_tets += h.n_tets;
+    out->n_magnetic_nodes += h.n_mag_nodes;
+    out->n_magnetic_tets += h.n_mag_tets;
+    out->nnz += h.rowptr.empty() ? 0 : h.rowptr.back();
+    out->volume += h.volume;
+    out->volume_magnetic += h.volume_mag;
+  }
+  out->sell_entries = ctx->hb.sell.entries;
+  out->n_segments = (int)ctx->hm.size();
   out->eps = ctx->P.eps;
   out->dtau = ctx->P.dtau;
   out->device_bytes = ctx->eng ? ctx->eng->device_bytes() : 0;
+  if (ctx->eng) {
+    float tb[kSpmvVariants], ts[kSpmvVariants];
+    int vb = 0, vs = 0, is = 0;
+    ctx->eng->tune_info(&vb, &vs, tb, ts, &is);
+    out->spmv_schedule_block = vb;
+    out->spmv_schedule_scalar = vs;
+    out->item_slices = is;
+    for (int v = 0; v < kSpmvVariants && v < 3; ++v) {
+      out->spmv_ms_block[v] = tb[v];
+      out->spmv_ms_scalar[v] = ts[v];
+    }
+  }
   return GSPM_OK;
 }
 
@@ -709,7 +1232,11 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
     set_error("mesh_export: null argument");
     return GSPM_EINVAL;
   }
-  const HostMesh& hm = ctx->hm;
+  if (ctx->hm.size() != 1) {
+    set_error("mesh_export: only for single-mesh contexts");
+    return GSPM_ESTATE;
+  }
+  const HostMesh& hm = ctx->hm[0];
   auto put = [&](const void* src, int64_t len, size_t elem) -> int {
     if (count != len) {
       set_error("mesh_export: count %lld, structure has %lld", (long long)count, (long long)len);
@@ -759,7 +1286,16 @@ int gspm_step(gspm_ctx* ctx, int n_steps, const double H_ext[3], gspm_step_stats
     set_error("step: need n_steps >= 0 and H_ext");
     return GSPM_EINVAL;
   }
-  return ctx->eng->step(n_steps, H_ext, stats);
+  return ctx->eng->step(n_steps, H_ext, false, stats);
+}
+
+int gspm_batch_step(gspm_ctx* ctx, int n_steps, const double* H_ext, gspm_step_stats* stats) {
+  NEED_ENGINE(ctx);
+  if (n_steps < 0 || !H_ext) {
+    set_error("batch_step: need n_steps >= 0 and H_ext");
+    return GSPM_EINVAL;
+  }
+  return ctx->eng->step(n_steps, H_ext, true, stats);
 }
 
 int gspm_solve_elastic(gspm_ctx* ctx, const double* m, double* u, int where, int x0_mode,
@@ -779,6 +1315,57 @@ int gspm_apply(gspm_ctx* ctx, int op, const double* x, double* y, int where) {
 }
 
 int64_t gspm_launch_count(const gspm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gspm_set_x0_mode(gspm_ctx* ctx, int mode) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->set_x0_mode(mode);
+}
+
+int gspm_mpnn_set_params(gspm_ctx* ctx, const float* params, int64_t count) {
+  NEED_ENGINE(ctx);
+  if (!params) {
+    set_error("mpnn_set_params: null pointer");
+    return GSPM_EINVAL;
+  }
+  return ctx->eng->mpnn_params(nullptr, params, count);
+}
+
+int gspm_mpnn_get_params(gspm_ctx* ctx, float* params, int64_t count) {
+  NEED_ENGINE(ctx);
+  if (!params) {
+    set_error("mpnn_get_params: null pointer");
+    return GSPM_EINVAL;
+  }
+  return ctx->eng->mpnn_params(params, nullptr, count);
+}
+
+int gspm_mpnn_predict(gspm_ctx* ctx, const double* m, const double* u_prev, const double* u_prev2,
+                      double* out, int what, int where) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->mpnn_predict(m, u_prev, u_prev2, out, what, where);
+}
+
+int gspm_mpnn_dataset_reserve(gspm_ctx* ctx, int capacity) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->mpnn_dataset_reserve(capacity);
+}
+
+int gspm_mpnn_dataset_add(gspm_ctx* ctx, const double* m, const double* u_prev,
+                          const double* u_prev2, const double* u_star, int where, int* index) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->mpnn_dataset_add(m, u_prev, u_prev2, u_star, where, index);
+}
+
+int gspm_mpnn_loss_grad(gspm_ctx* ctx, int pair, double* loss, float* grad) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->mpnn_loss_grad(pair, loss, grad);
+}
+
+int gspm_mpnn_train(gspm_ctx* ctx, int iterations, double lr, uint64_t seed, double* loss_first,
+                    double* loss_last) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->mpnn_train(iterations, lr, seed, loss_first, loss_last);
+}
 
 int gspm_profile_enable(gspm_ctx* ctx, unsigned class_mask) {
   NEED_ENGINE(ctx);

@@ -339,6 +339,8 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
   ops->F.assign(3 * E, 0.0);
   ops->G.assign(3 * E, 0.0);
   ops->Kmech.assign(9 * E, 0.0);
+  ops->Agg.assign(E, 0.0);
+  ops->AggT.assign(E, 0.0);
   ops->ML.assign(n, 0.0);
   ops->w.assign(n, 0.0);
   ops->invML.assign(n, 0.0);
@@ -358,7 +360,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
   const int64_t pin = ops->pin;
 #pragma omp parallel
   {
-    std::vector<double> kms, km, mm, f, g, k9;
+    std::vector<double> kms, km, mm, f, g, k9, bb;
 #pragma omp for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
       const int64_t o = hm.perm[i];
@@ -366,6 +368,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
       const int len = (int)(s.rp[i + 1] - s.rp[i]);
       kms.assign(len, 0.0); km.assign(len, 0.0); mm.assign(len, 0.0);
       f.assign(3 * len, 0.0); g.assign(3 * len, 0.0); k9.assign(9 * len, 0.0);
+      bb.assign(len, 0.0);
       double ml = 0.0;
       for (int64_t q = ntp[o]; q < ntp[o + 1]; ++q) {
         const int64_t e = nti[q];
@@ -383,6 +386,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
           const double* gl = &hm.grads[12 * e + 3 * l];
           const double dot = gk[0] * gl[0] + gk[1] * gl[1] + gk[2] * gl[2];
           kms[pos] += V * dot;
+          bb[pos] += V / 4.0;  // B_ij = sum_{e containing i, j} V_e / 4
           if (me) {
             km[pos] += V * dot;
             mm[pos] += V * (k == l ? 2.0 : 1.0) / 20.0;
@@ -419,6 +423,8 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
           ops->Kmech[vb * 9 + b * kSell + lane] =
               pinned ? ((diag && (b == 0 || b == 4 || b == 8)) ? 1.0 : 0.0) : k9[9 * pos + b];
       }
+      for (int pos = 0; pos < len; ++pos)
+        ops->Agg[s.sptr[sl] + (int64_t)pos * kSell + lane] = bb[pos] / (4.0 * ml);
       ops->ML[i] = ml;
       ops->w[i] = ml / hm.volume;
       ops->invML[i] = 1.0 / ml;
@@ -432,6 +438,100 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
       }
     }
   }
+  // A^T at (i, j) = A_ji = B_ij / (4 M_L,j)  (B is symmetric)
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t sl = i / kSell, lane = i % kSell;
+    const int len = (int)(s.rp[i + 1] - s.rp[i]);
+    for (int pos = 0; pos < len; ++pos) {
+      const int64_t ent = s.sptr[sl] + (int64_t)pos * kSell + lane;
+      const int32_t j = s.ic[s.rp[i] + pos];
+      ops->AggT[ent] = ops->Agg[ent] * ops->ML[i] / ops->ML[j];
+    }
+  }
+}
+
+void host_batch_build(std::vector<HostMesh>& hm, std::vector<HostSell>& hs,
+                      std::vector<HostOps>& ops, HostBatch* b) {
+  const int S = (int)hm.size();
+  b->seg_row0.resize(S);
+  b->seg_nrow.resize(S);
+  b->seg_pin.resize(S);
+  b->seg_sl0.resize(S);
+  b->seg_nsl.resize(S);
+  b->seg_node0.resize(S);
+  b->seg_nmag.resize(S);
+  b->seg_h.resize(S);
+  int64_t sl = 0, node = 0, entries = 0;
+  for (int s = 0; s < S; ++s) {
+    b->seg_sl0[s] = sl;
+    b->seg_nsl[s] = hs[s].nslices;
+    b->seg_row0[s] = sl * kSell;
+    b->seg_nrow[s] = hm[s].n;
+    b->seg_pin[s] = b->seg_row0[s] + ops[s].pin;
+    b->seg_node0[s] = node;
+    b->seg_nmag[s] = hm[s].n_mag_nodes;
+    b->seg_h[s] = std::cbrt(hm[s].volume / (double)hm[s].n);
+    sl += hs[s].nslices;
+    node += hm[s].n;
+    entries += hs[s].entries;
+  }
+  b->n_nodes = node;
+  b->n_mag_nodes = 0;
+  for (int s = 0; s < S; ++s) b->n_mag_nodes += hm[s].n_mag_nodes;
+  b->seg_of_slice.resize(sl);
+  for (int s = 0; s < S; ++s)
+    for (int64_t k = 0; k < hs[s].nslices; ++k) b->seg_of_slice[b->seg_sl0[s] + k] = s;
+  if (S == 1) {  // no copies for a single mesh
+    b->sell = std::move(hs[0]);
+    b->ops = std::move(ops[0]);
+    b->perm = hm[0].perm;
+    return;
+  }
+  const int64_t rows = b->seg_row0[S - 1] + hm[S - 1].n;
+  HostSell& c = b->sell;
+  c.n = rows;
+  c.nslices = sl;
+  c.entries = entries;
+  c.sptr.assign(sl + 1, 0);
+  c.slen.assign(sl, 0);
+  c.col.assign(entries, 0);
+  HostOps& o = b->ops;
+  o.Kms.resize(entries); o.Aeps.resize(entries); o.Aaeps.resize(entries); o.M.resize(entries);
+  o.Agg.resize(entries); o.AggT.resize(entries);
+  o.F.resize(3 * entries); o.G.resize(3 * entries); o.Kmech.resize(9 * entries);
+  o.ML.assign(rows, 1.0); o.w.assign(rows, 0.0); o.invML.assign(rows, 0.0);
+  o.mag.assign(rows, 0);
+  b->perm.assign(rows, -1);
+  int64_t e0 = 0;
+  for (int s = 0; s < S; ++s) {
+    const HostSell& h = hs[s];
+    const int64_t r0 = b->seg_row0[s], s0 = b->seg_sl0[s];
+    for (int64_t k = 0; k < h.nslices; ++k) {
+      c.sptr[s0 + k] = e0 + h.sptr[k];
+      c.slen[s0 + k] = h.slen[k];
+    }
+    for (int64_t e = 0; e < h.entries; ++e) c.col[e0 + e] = (int32_t)(h.col[e] + r0);
+    auto cp = [&](std::vector<double>& dst, const std::vector<double>& src, int64_t B) {
+      std::copy(src.begin(), src.end(), dst.begin() + e0 * B);
+    };
+    cp(o.Kms, ops[s].Kms, 1); cp(o.Aeps, ops[s].Aeps, 1); cp(o.Aaeps, ops[s].Aaeps, 1);
+    cp(o.M, ops[s].M, 1); cp(o.Agg, ops[s].Agg, 1); cp(o.AggT, ops[s].AggT, 1);
+    cp(o.F, ops[s].F, 3); cp(o.G, ops[s].G, 3); cp(o.Kmech, ops[s].Kmech, 9);
+    for (int64_t i = 0; i < hm[s].n; ++i) {
+      o.ML[r0 + i] = ops[s].ML[i];
+      o.w[r0 + i] = ops[s].w[i];
+      o.invML[r0 + i] = ops[s].invML[i];
+      o.mag[r0 + i] = ops[s].mag[i];
+      b->perm[r0 + i] = b->seg_node0[s] + hm[s].perm[i];
+    }
+    e0 += h.entries;
+    // release the per-mesh copies as we go
+    ops[s] = HostOps();
+    hs[s].col.clear();
+    hs[s].col.shrink_to_fit();
+  }
+  c.sptr[sl] = e0;
 }
 
 }  // namespace gspm

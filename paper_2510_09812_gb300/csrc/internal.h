@@ -67,10 +67,28 @@ struct HostOps {
   std::vector<double> F, G;                 // B = 3: F_{ij,a} = -int phi_i d_a phi_j,
                                             //        G_{ij,a} =  int phi_j d_a phi_i
   std::vector<double> Kmech;                // B = 9, row-major 3x3 block (a*3 + b)
+  std::vector<double> Agg, AggT;            // B = 1: element-message averaging A and A^T
   std::vector<double> ML, w, invML;         // internal numbering; w = M_L / V
   std::vector<uint8_t> mag;                 // internal numbering
   int64_t pin = 0;                          // internal index of unique node 0
 };
 void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostOps* ops);
+
+// A batch of meshes ("segments") concatenated slice-aligned: segment s owns the rows
+// [seg_row0[s], seg_row0[s] + seg_nrow[s]) (its last slice padded with empty rows when another
+// segment follows) and the ABI nodes [seg_node0[s], seg_node0[s] + seg_nrow[s]).
+struct HostBatch {
+  HostSell sell;                       // combined node graph (n = all rows incl. padding)
+  HostOps ops;                         // combined values and per-row arrays
+  std::vector<int64_t> perm;           // [rows] ABI node of each row, -1 for padding
+  std::vector<int32_t> seg_of_slice;   // [nslices]
+  std::vector<int64_t> seg_row0, seg_nrow, seg_pin, seg_sl0, seg_nsl, seg_node0, seg_nmag;
+  std::vector<double> seg_h;           // node spacing (V / n)^(1/3)
+  int64_t n_nodes = 0;                 // ABI nodes of the batch
+  int64_t n_mag_nodes = 0;
+};
+// Consumes (moves from) the per-mesh pieces.
+void host_batch_build(std::vector<HostMesh>& hm, std::vector<HostSell>& hs,
+                      std::vector<HostOps>& ops, HostBatch* b);
 
 }  // namespace gspm

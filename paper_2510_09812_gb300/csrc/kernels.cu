@@ -1,9 +1,20 @@
 // GSPM kernels for sm_103a.  The path is HBM-bound: sparse row gathers over a SELL-32 node graph
 // (one thread per node row, one warp per 32-row slice, every (k, b) value run of a slice one
-// coalesced 128/256-byte load), FP64 grid reductions with a fixed summation order, and fused
+// coalesced 128/256-byte load), FP64 reductions with a fixed summation order, and fused
 // pointwise updates.  Matrix values and column indices are streamed with evict-first loads so
 // that the gathered vectors stay resident in L2.
+//
+// A context holds one or more meshes ("segments", a batch), concatenated slice-aligned in one
+// SELL structure.  Everything that reduces (CG inner products, volume averages, the projection's
+// <|dm|>) runs over a static list of work items (segment, slice range): each item leaves one
+// partial per component and the last item of a segment to arrive sums that segment's partials in
+// item order, so results are per mesh and bitwise reproducible.  CG scalars, pins, applied
+// fields and volume averages are per segment; a segment whose CG converged skips its items.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "kernels.cuh"
 
@@ -19,12 +30,15 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// Deterministic grid reduction (last-block pattern).  Every block reduces its NC values with a
-// fixed warp/block tree, writes one partial per component, and the last block to arrive sums
-// the partials in block order with the same tree.  Returns true in the last block, whose
-// threads then find the totals in res[0..NC).
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// Block reduction of NC values into partial[item]; the last item of `seg` to arrive sums the
+// segment's item partials in item order and returns true (totals in res[0..NC), valid in every
+// thread of that block).
 template <int NC>
-__device__ __forceinline__ bool grid_reduce(double (&v)[NC], const Red& red, double* res) {
+__device__ __forceinline__ bool seg_reduce(double (&v)[NC], int item, int seg, const DSeg& G,
+                                           const Red& red, double* res) {
   __shared__ double sm[NC][32];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -38,22 +52,23 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NC], const Red& red, dou
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const double x = warp_sum(lane < nw ? sm[c][lane] : 0.0);
-      if (lane == 0) red.partial[(int64_t)blockIdx.x * kRedComp + c] = x;
+      if (lane == 0) red.partial[(int64_t)item * kRedComp + c] = x;
     }
   }
   if (threadIdx.x == 0) {
     __threadfence();
-    const unsigned t = atomicAdd(red.counter, 1u);
-    am_last = (t == gridDim.x - 1);
+    const unsigned t = atomicAdd(G.counter + seg, 1u);
+    am_last = (t == (unsigned)G.seg_nitems[seg] - 1u);
   }
   __syncthreads();
   if (!am_last) return false;
   __threadfence();
+  const int i0 = G.seg_item0[seg], ni = G.seg_nitems[seg];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     double acc = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      acc += __ldcg(red.partial + (int64_t)b * kRedComp + c);
+    for (int b = threadIdx.x; b < ni; b += blockDim.x)
+      acc += __ldcg(red.partial + (int64_t)(i0 + b) * kRedComp + c);
     acc = warp_sum(acc);
     if (lane == 0) sm[c][warp] = acc;
   }
@@ -65,20 +80,22 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NC], const Red& red, dou
       if (lane == 0) res[c] = x;
     }
   }
-  if (threadIdx.x == 0) *red.counter = 0u;
+  if (threadIdx.x == 0) G.counter[seg] = 0u;
   __syncthreads();
   return true;
 }
 
-__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
-__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+__device__ __forceinline__ bool row_valid(const DSeg& G, int seg, int64_t row) {
+  return row - G.seg_row0[seg] < G.seg_nrow[seg];
+}
 
-// y_r(row) = sum_k A(row, k) x_r(col(row, k)) for one row of a scalar SELL matrix.
+// y_r(row) = sum_k A(row, k) x_r(col(row, k)) for one row of a scalar SELL matrix, neighbours
+// k = k0, k0 + kstep, ...
 template <typename V, typename X, typename Acc, int NR>
 __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restrict__ val,
                                                 int64_t s, int lane, const X* __restrict__ x,
                                                 int64_t ld, const int (&skip)[NR],
-                                                Acc (&acc)[NR]) {
+                                                Acc (&acc)[NR], int k0 = 0, int kstep = 1) {
   const int64_t base = A.sptr[s];
   const int len = A.slen[s];
   const int32_t* cp = A.col + base + lane;
@@ -86,7 +103,7 @@ __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restr
 #pragma unroll
   for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
 #pragma unroll 4
-  for (int k = 0; k < len; ++k) {
+  for (int k = k0; k < len; k += kstep) {
     const int j = __ldcs(cp + (int64_t)k * 32);
     const Acc a = (Acc)__ldcs(vp + (int64_t)k * 32);
 #pragma unroll
@@ -96,81 +113,150 @@ __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restr
 }
 
 // 3x3-block row: y(row, a) = sum_k sum_b A(row, k)_ab x(col, b); x, y arrays of [n][3].
-template <typename V, typename X, typename Acc>
+template <typename V, typename X, typename Acc, int VAR>
 __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restrict__ val,
                                                int64_t s, int lane, const X* __restrict__ x,
-                                               Acc (&acc)[3]) {
+                                               Acc (&acc)[3], int k0 = 0, int kstep = 1) {
   const int64_t base = A.sptr[s];
   const int len = A.slen[s];
   const int32_t* cp = A.col + base + lane;
   const V* vp = val + base * 9 + lane;
   acc[0] = acc[1] = acc[2] = Acc(0);
-#pragma unroll 2
-  for (int k = 0; k < len; ++k) {
-    const int64_t j = __ldcs(cp + (int64_t)k * 32);
-    const V* bp = vp + (int64_t)k * 288;
-    const Acc x0 = (Acc)__ldg(x + 3 * j), x1 = (Acc)__ldg(x + 3 * j + 1),
-              x2 = (Acc)__ldg(x + 3 * j + 2);
+  if (VAR == 1) {
+    // five neighbours per round: all loads first, then the FMAs
+    for (int kb = k0; kb < len; kb += 5 * kstep) {
+      int64_t j[5];
+      V w[5][9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      acc[a] += (Acc)__ldcs(bp + (3 * a + 0) * 32) * x0;
-      acc[a] += (Acc)__ldcs(bp + (3 * a + 1) * 32) * x1;
-      acc[a] += (Acc)__ldcs(bp + (3 * a + 2) * 32) * x2;
+      for (int u = 0; u < 5; ++u) {
+        const int k = kb + u * kstep;
+        const bool ok = k < len;
+        j[u] = ok ? (int64_t)__ldcs(cp + (int64_t)k * 32) : 0;
+        const V* bp = vp + (int64_t)(ok ? k : 0) * 288;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) w[u][e] = ok ? __ldcs(bp + e * 32) : V(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 5; ++u) {
+        const Acc x0 = (Acc)__ldg(x + 3 * j[u]), x1 = (Acc)__ldg(x + 3 * j[u] + 1),
+                  x2 = (Acc)__ldg(x + 3 * j[u] + 2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          acc[a] += (Acc)w[u][3 * a] * x0 + (Acc)w[u][3 * a + 1] * x1 + (Acc)w[u][3 * a + 2] * x2;
+      }
+    }
+  } else {
+#pragma unroll 2
+    for (int k = k0; k < len; k += kstep) {
+      const int64_t j = __ldcs(cp + (int64_t)k * 32);
+      const V* bp = vp + (int64_t)k * 288;
+      const Acc x0 = (Acc)__ldg(x + 3 * j), x1 = (Acc)__ldg(x + 3 * j + 1),
+                x2 = (Acc)__ldg(x + 3 * j + 2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc[a] += (Acc)__ldcs(bp + (3 * a + 0) * 32) * x0;
+        acc[a] += (Acc)__ldcs(bp + (3 * a + 1) * 32) * x1;
+        acc[a] += (Acc)__ldcs(bp + (3 * a + 2) * 32) * x2;
+      }
     }
   }
 }
 
+// Work unit of the SELL kernels for schedule VAR: one slice per warp (VAR 0, 1), or half a slice
+// per warp with two lanes per row (VAR 2).  unit_row() gives, for this lane, the slice, the SELL
+// lane of its row, and the first neighbour and stride it handles.
+template <int VAR>
+__device__ __forceinline__ void unit_row(int64_t u, int lane, int64_t& s, int& sl, int& k0,
+                                         int& kstep) {
+  if (VAR == 2) {
+    s = u >> 1;
+    sl = (int)(u & 1) * 16 + (lane & 15);
+    k0 = lane >> 4;
+    kstep = 2;
+  } else {
+    s = u;
+    sl = lane;
+    k0 = 0;
+    kstep = 1;
+  }
+}
+template <int VAR>
+__device__ __forceinline__ int units_per_slice() {
+  return VAR == 2 ? 2 : 1;
+}
+// combine the two partial row results of VAR 2 (lanes l and l+16); true on the lane that owns
+// the row's result
+template <int VAR, typename Acc, int N>
+__device__ __forceinline__ bool unit_combine(Acc (&acc)[N], int lane) {
+  if (VAR != 2) return true;
+#pragma unroll
+  for (int a = 0; a < N; ++a) acc[a] += __shfl_xor_sync(kFull, acc[a], 16);
+  return lane < 16;
+}
+
 // ------------------------------------------------------------------------------------------
-// volume average: out[c] = sum_i w_i f(i, c) (+ add[c]); Sec. 2.4 with nodal weights M_L,i / V
+// volume average per segment: out[seg*nc + c] = sum_i w_i f(i, c) (+ add[c]); Sec. 2.4 with
+// nodal weights M_L,i / V(segment)
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_wsum(int64_t n, int nc, const T* __restrict__ f,
+__global__ void __launch_bounds__(kBlock) k_wsum(DSeg G, int nc, const T* __restrict__ f,
                                                  int64_t cs, int64_t ns,
                                                  const int64_t* __restrict__ perm,
                                                  const double* __restrict__ w, double* out,
                                                  const double* add, Red red) {
-  double v[9];
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    double v[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) v[c] = 0.0;
-  for (int64_t i = gtid(); i < n; i += gstride()) {
-    const double wi = w[i];
-    const int64_t src = perm ? perm[i] : i;
+    for (int c = 0; c < 9; ++c) v[c] = 0.0;
+    const int64_t r0 = (int64_t)G.item_sl0[item] * 32, r1 = (int64_t)G.item_sl1[item] * 32;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      if (!row_valid(G, seg, i)) continue;
+      const double wi = w[i];
+      const int64_t src = perm ? perm[i] : i;
 #pragma unroll
-    for (int c = 0; c < 9; ++c)
-      if (c < nc) v[c] += wi * (double)f[src * ns + c * cs];
+      for (int c = 0; c < 9; ++c)
+        if (c < nc) v[c] += wi * (double)f[src * ns + c * cs];
+    }
+    __shared__ double res[9];
+    if (seg_reduce<9>(v, item, seg, G, red, res) && threadIdx.x == 0)
+      for (int c = 0; c < nc; ++c) out[seg * nc + c] = res[c] + (add ? add[c] : 0.0);
   }
-  __shared__ double res[9];
-  if (grid_reduce<9>(v, red, res) && threadIdx.x == 0)
-    for (int c = 0; c < nc; ++c) out[c] = res[c] + (add ? add[c] : 0.0);
 }
 
 // ------------------------------------------------------------------------------------------
-// plain SpMV (operator access)
+// plain SpMV (operator access, autotuning)
 // ------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int VAR>
 __global__ void __launch_bounds__(kBlock) k_spmv1(DSell A, const T* __restrict__ val,
                                                   const T* __restrict__ x, T* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   const int skip[1] = {0};
-  for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
+  for (int64_t u = gtid() >> 5; u < A.nslices * units_per_slice<VAR>(); u += nw) {
+    int64_t s;
+    int sl, k0, ks;
+    unit_row<VAR>(u, lane, s, sl, k0, ks);
     T acc[1];
-    sell_scalar_row<T, T, T, 1>(A, val, s, lane, x, 0, skip, acc);
-    const int64_t row = s * 32 + lane;
-    if (row < A.n) y[row] = acc[0];
+    sell_scalar_row<T, T, T, 1>(A, val, s, sl, x, 0, skip, acc, k0, ks);
+    const int64_t row = s * 32 + sl;
+    if (unit_combine<VAR>(acc, lane) && row < A.n) y[row] = acc[0];
   }
 }
 
-template <typename T>
+template <typename T, int VAR>
 __global__ void __launch_bounds__(kBlock) k_spmv9(DSell A, const T* __restrict__ val,
                                                   const T* __restrict__ x, T* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
-  for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
+  for (int64_t u = gtid() >> 5; u < A.nslices * units_per_slice<VAR>(); u += nw) {
+    int64_t s;
+    int sl, k0, ks;
+    unit_row<VAR>(u, lane, s, sl, k0, ks);
     T acc[3];
-    sell_block_row<T, T, T>(A, val, s, lane, x, acc);
-    const int64_t row = s * 32 + lane;
-    if (row < A.n) {
+    sell_block_row<T, T, T, VAR>(A, val, s, sl, x, acc, k0, ks);
+    const int64_t row = s * 32 + sl;
+    if (unit_combine<VAR>(acc, lane) && row < A.n) {
       y[3 * row] = acc[0];
       y[3 * row + 1] = acc[1];
       y[3 * row + 2] = acc[2];
@@ -179,10 +265,11 @@ __global__ void __launch_bounds__(kBlock) k_spmv9(DSell A, const T* __restrict__
 }
 
 // ------------------------------------------------------------------------------------------
-// conjugate gradients (Sec. 2.5, unpreconditioned), all scalars on the device
+// conjugate gradients (Sec. 2.5, unpreconditioned), all scalars on the device, per segment
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void cg_start(CGState* st, int nr, const double* bb, const double* rr,
-                                         double rtol, int max_iter, int allow_zero_x) {
+__device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, const double* bb,
+                                         const double* rr, double rtol, int max_iter,
+                                         int allow_zero_x) {
   int any = 0, zero = 0;
   for (int k = 0; k < 3; ++k) {
     CGRhs& q = st->r[k];
@@ -204,235 +291,275 @@ __device__ __forceinline__ void cg_start(CGState* st, int nr, const double* bb, 
   st->max_iter = max_iter;
   st->noconv = 0;
   st->zero_x = allow_zero_x ? zero : 0;
+  if (any) atomicAdd(nactive, 1);
 }
 
 // r = b - A x, p = r (scalar B = 1 or 3x3 block B = 9), one right-hand side
 template <typename T, int B>
-__global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, const T* __restrict__ val,
-                                                    const double* __restrict__ b,
-                                                    const double* __restrict__ x,
-                                                    double* __restrict__ r, T* __restrict__ p,
-                                                    CGState* st, double rtol, int max_iter,
-                                                    Red red) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = gstride() >> 5;
-  double v[2] = {0.0, 0.0};  // rr, bb
-  for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
-    const int64_t row = s * 32 + lane;
-    if (B == 1) {
-      double acc[1];
-      const int skip[1] = {0};
-      sell_scalar_row<T, double, double, 1>(A, val, s, lane, x, 0, skip, acc);
-      if (row < A.n) {
-        const double rv = b[row] - acc[0];
-        r[row] = rv;
-        p[row] = (T)rv;
-        v[0] += rv * rv;
-        v[1] += b[row] * b[row];
-      }
-    } else {
-      double acc[3];
-      sell_block_row<T, double, double>(A, val, s, lane, x, acc);
-      if (row < A.n) {
+__global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, const T* __restrict__ val,
+                                                    const T* __restrict__ b,
+                                                    const T* __restrict__ x,
+                                                    T* __restrict__ r, T* __restrict__ p,
+                                                    CGState* st, int* nactive, double rtol,
+                                                    int max_iter, Red red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    double v[2] = {0.0, 0.0};  // rr, bb
+    for (int64_t s = G.item_sl0[item] + warp; s < G.item_sl1[item]; s += kBlock / 32) {
+      const int64_t row = s * 32 + lane;
+      const bool ok = row_valid(G, seg, row);
+      if (B == 1) {
+        double acc[1];
+        const int skip[1] = {0};
+        sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, acc);
+        if (ok) {
+          const T rv = (T)((double)b[row] - acc[0]);
+          r[row] = rv;
+          p[row] = rv;
+          v[0] += (double)rv * (double)rv;
+          v[1] += (double)b[row] * (double)b[row];
+        }
+      } else {
+        double acc[3];
+        sell_block_row<T, T, double, 0>(A, val, s, lane, x, acc);
+        if (ok) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const double rv = b[3 * row + a] - acc[a];
-          r[3 * row + a] = rv;
-          p[3 * row + a] = (T)rv;
-          v[0] += rv * rv;
-          v[1] += b[3 * row + a] * b[3 * row + a];
+          for (int a = 0; a < 3; ++a) {
+            const T rv = (T)((double)b[3 * row + a] - acc[a]);
+            r[3 * row + a] = rv;
+            p[3 * row + a] = rv;
+            v[0] += (double)rv * (double)rv;
+            v[1] += (double)b[3 * row + a] * (double)b[3 * row + a];
+          }
         }
       }
     }
-  }
-  __shared__ double res[2];
-  if (grid_reduce<2>(v, red, res) && threadIdx.x == 0) {
-    const double bb[1] = {res[1]}, rr[1] = {res[0]};
-    cg_start(st, 1, bb, rr, rtol, max_iter, 1);
+    __shared__ double res[2];
+    if (seg_reduce<2>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+      const double bb[1] = {res[1]}, rr[1] = {res[0]};
+      cg_start(st + seg, nactive, 1, bb, rr, rtol, max_iter, 1);
+    }
   }
 }
 
 // GSPM systems (M + c eps K) g = M f with x0 = f already in x: b = M x, r = b - A x, p = r
 template <typename T, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, const T* __restrict__ aval,
+__global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G,
+                                                       const T* __restrict__ aval,
                                                        const T* __restrict__ mval, int64_t ld,
-                                                       const double* __restrict__ x,
-                                                       double* __restrict__ r,
-                                                       T* __restrict__ p, CGState* st,
-                                                       double rtol, int max_iter, Red red) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = gstride() >> 5;
+                                                       const T* __restrict__ x,
+                                                       T* __restrict__ r, T* __restrict__ p,
+                                                       CGState* st, int* nactive, double rtol,
+                                                       int max_iter, Red red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int skip[NR] = {};
-  double v[2 * NR];
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    double v[2 * NR];
 #pragma unroll
-  for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
-  for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
-    double ax[NR], mx[NR];
-    sell_scalar_row<T, double, double, NR>(A, aval, s, lane, x, ld, skip, ax);
-    sell_scalar_row<T, double, double, NR>(A, mval, s, lane, x, ld, skip, mx);
-    const int64_t row = s * 32 + lane;
-    if (row < A.n) {
+    for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
+    for (int64_t s = G.item_sl0[item] + warp; s < G.item_sl1[item]; s += kBlock / 32) {
+      double ax[NR], mx[NR];
+      sell_scalar_row<T, T, double, NR>(A, aval, s, lane, x, ld, skip, ax);
+      sell_scalar_row<T, T, double, NR>(A, mval, s, lane, x, ld, skip, mx);
+      const int64_t row = s * 32 + lane;
+      if (row_valid(G, seg, row)) {
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        const double rv = mx[k] - ax[k];
-        r[k * ld + row] = rv;
-        p[k * ld + row] = (T)rv;
-        v[2 * k] += rv * rv;
-        v[2 * k + 1] += mx[k] * mx[k];
+        for (int k = 0; k < NR; ++k) {
+          const T rv = (T)(mx[k] - ax[k]);
+          r[k * ld + row] = rv;
+          p[k * ld + row] = rv;
+          v[2 * k] += (double)rv * (double)rv;
+          v[2 * k + 1] += mx[k] * mx[k];
+        }
       }
     }
-  }
-  __shared__ double res[2 * NR];
-  if (grid_reduce<2 * NR>(v, red, res) && threadIdx.x == 0) {
-    double bb[NR], rr[NR];
-    for (int k = 0; k < NR; ++k) {
-      rr[k] = res[2 * k];
-      bb[k] = res[2 * k + 1];
+    __shared__ double res[2 * NR];
+    if (seg_reduce<2 * NR>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+      double bb[NR], rr[NR];
+      for (int k = 0; k < NR; ++k) {
+        rr[k] = res[2 * k];
+        bb[k] = res[2 * k + 1];
+      }
+      cg_start(st + seg, nactive, NR, bb, rr, rtol, max_iter, 0);
     }
-    cg_start(st, NR, bb, rr, rtol, max_iter, 0);
   }
 }
 
-// q = A p with the p.q dot fused; last block forms alpha = rr / p.q
-template <typename T, int B, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, const T* __restrict__ val, int64_t ld,
-                                                    const T* __restrict__ p, T* __restrict__ q,
-                                                    CGState* st, Red red) {
-  if (!st->active) return;
-  int skip[NR];
+// q = A p with the p.q dot fused; the segment's last item forms alpha = rr / p.q
+template <typename T, int B, int NR, int VAR>
+__global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, const T* __restrict__ val,
+                                                    int64_t ld, const T* __restrict__ p,
+                                                    T* __restrict__ q, CGState* st, Red red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    CGState* sg = st + seg;
+    if (!sg->active) continue;
+    int skip[NR];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) skip[k] = st->r[k].done;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = gstride() >> 5;
-  double v[NR];
+    for (int k = 0; k < NR; ++k) skip[k] = sg->r[k].done;
+    double v[NR];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) v[k] = 0.0;
-  for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
-    const int64_t row = s * 32 + lane;
-    if (B == 1) {
-      T acc[NR];
-      sell_scalar_row<T, T, T, NR>(A, val, s, lane, p, ld, skip, acc);
-      if (row < A.n) {
+    for (int k = 0; k < NR; ++k) v[k] = 0.0;
+    const int64_t u0 = (int64_t)G.item_sl0[item] * units_per_slice<VAR>();
+    const int64_t u1 = (int64_t)G.item_sl1[item] * units_per_slice<VAR>();
+    for (int64_t u = u0 + warp; u < u1; u += kBlock / 32) {
+      int64_t s;
+      int sl, k0, ks;
+      unit_row<VAR>(u, lane, s, sl, k0, ks);
+      const int64_t row = s * 32 + sl;
+      if (B == 1) {
+        T acc[NR];
+        sell_scalar_row<T, T, T, NR>(A, val, s, sl, p, ld, skip, acc, k0, ks);
+        if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k)
-          if (!skip[k]) {
-            q[k * ld + row] = acc[k];
-            v[k] += (double)p[k * ld + row] * (double)acc[k];
+          for (int k = 0; k < NR; ++k)
+            if (!skip[k]) {
+              q[k * ld + row] = acc[k];
+              v[k] += (double)p[k * ld + row] * (double)acc[k];
+            }
+        }
+      } else {
+        T acc[3];
+        sell_block_row<T, T, T, VAR>(A, val, s, sl, p, acc, k0, ks);
+        if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            q[3 * row + a] = acc[a];
+            v[0] += (double)p[3 * row + a] * (double)acc[a];
           }
+        }
       }
-    } else {
-      T acc[3];
-      sell_block_row<T, T, T>(A, val, s, lane, p, acc);
-      if (row < A.n) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          q[3 * row + a] = acc[a];
-          v[0] += (double)p[3 * row + a] * (double)acc[a];
+    }
+    __shared__ double res[NR];
+    if (seg_reduce<NR>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+      for (int k = 0; k < NR; ++k) {
+        CGRhs& c = sg->r[k];
+        if (c.done) continue;
+        c.pq = res[k];
+        if (res[k] > 0.0) {
+          c.alpha = c.rr / res[k];
+        } else {  // p = 0: nothing left to reduce
+          c.alpha = 0.0;
+          c.done = 1;
         }
       }
     }
   }
-  __shared__ double res[NR];
-  if (grid_reduce<NR>(v, red, res) && threadIdx.x == 0) {
-    for (int k = 0; k < NR; ++k) {
-      CGRhs& c = st->r[k];
-      if (c.done) continue;
-      c.pq = res[k];
-      if (res[k] > 0.0) {
-        c.alpha = c.rr / res[k];
-      } else {  // p = 0: nothing left to reduce
-        c.alpha = 0.0;
-        c.done = 1;
-      }
-    }
-  }
 }
 
-// x += alpha p, r -= alpha q, r.r fused; last block forms beta and the stopping decision
+// x += alpha p, r -= alpha q, r.r fused; the segment's last item forms beta and decides
+// convergence.  Vectors hold epr elements per row (1: scalar SoA with stride ld; 3: [n][3]).
 template <typename T, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_update(int64_t len, int64_t ld, double* __restrict__ x,
-                                                      double* __restrict__ r,
+__global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, int epr, int64_t ld,
+                                                      T* __restrict__ x, T* __restrict__ r,
                                                       const T* __restrict__ p,
                                                       const T* __restrict__ q, CGState* st,
-                                                      Red red) {
-  if (!st->active) return;
-  int skip[NR];
-  double al[NR];
+                                                      int* nactive, Red red) {
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    CGState* sg = st + seg;
+    if (!sg->active) continue;
+    int skip[NR];
+    T al[NR];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    skip[k] = st->r[k].done;
-    al[k] = st->r[k].alpha;
-  }
-  double v[NR];
-#pragma unroll
-  for (int k = 0; k < NR; ++k) v[k] = 0.0;
-  for (int64_t i = gtid(); i < len; i += gstride()) {
-#pragma unroll
-    for (int k = 0; k < NR; ++k)
-      if (!skip[k]) {
-        const int64_t o = k * ld + i;
-        x[o] += al[k] * (double)p[o];
-        const double rv = r[o] - al[k] * (double)q[o];
-        r[o] = rv;
-        v[k] += rv * rv;
-      }
-  }
-  __shared__ double res[NR];
-  if (grid_reduce<NR>(v, red, res) && threadIdx.x == 0) {
-    int any = 0;
     for (int k = 0; k < NR; ++k) {
-      CGRhs& c = st->r[k];
-      if (c.done) continue;
-      c.iters += 1;
-      c.beta = res[k] / c.rr;
-      c.rr = res[k];
-      if (res[k] < c.tol2) {
-        c.done = 1;
-      } else if (c.iters >= st->max_iter) {
-        c.done = 1;
-        st->noconv += 1;
-      }
-      any |= !c.done;
+      skip[k] = sg->r[k].done;
+      al[k] = (T)sg->r[k].alpha;
     }
-    st->active = any;
+    double v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = 0.0;
+    const int64_t e0 = (int64_t)G.item_sl0[item] * 32 * epr;
+    const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
+    const int64_t rhi = (int64_t)G.item_sl1[item] * 32;
+    const int64_t e1 = (rhi < rend ? rhi : rend) * epr;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k)
+        if (!skip[k]) {
+          const int64_t o = k * ld + i;
+          x[o] += al[k] * p[o];
+          const T rv = r[o] - al[k] * q[o];
+          r[o] = rv;
+          v[k] += (double)(rv * rv);
+        }
+    }
+    __shared__ double res[NR];
+    if (seg_reduce<NR>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+      int any = 0;
+      for (int k = 0; k < NR; ++k) {
+        CGRhs& c = sg->r[k];
+        if (c.done) continue;
+        c.iters += 1;
+        c.beta = res[k] / c.rr;
+        c.rr = res[k];
+        if (res[k] < c.tol2) {
+          c.done = 1;
+        } else if (c.iters >= sg->max_iter) {
+          c.done = 1;
+          sg->noconv += 1;
+        }
+        any |= !c.done;
+      }
+      sg->active = any;
+      if (!any) atomicSub(nactive, 1);
+    }
   }
 }
 
 template <typename T, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_pupdate(int64_t len, int64_t ld,
-                                                       const double* __restrict__ r,
+__global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, int epr, int64_t ld,
+                                                       const T* __restrict__ r,
                                                        T* __restrict__ p, const CGState* st) {
-  if (!st->active) return;
-  int skip[NR];
-  double be[NR];
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    const CGState* sg = st + seg;
+    if (!sg->active) continue;
+    int skip[NR];
+    T be[NR];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    skip[k] = st->r[k].done;
-    be[k] = st->r[k].beta;
-  }
-  for (int64_t i = gtid(); i < len; i += gstride()) {
+    for (int k = 0; k < NR; ++k) {
+      skip[k] = sg->r[k].done;
+      be[k] = (T)sg->r[k].beta;
+    }
+    const int64_t e0 = (int64_t)G.item_sl0[item] * 32 * epr;
+    const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
+    const int64_t rhi = (int64_t)G.item_sl1[item] * 32;
+    const int64_t e1 = (rhi < rend ? rhi : rend) * epr;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < NR; ++k)
-      if (!skip[k]) {
-        const int64_t o = k * ld + i;
-        p[o] = (T)(r[o] + be[k] * (double)p[o]);
-      }
+      for (int k = 0; k < NR; ++k)
+        if (!skip[k]) {
+          const int64_t o = k * ld + i;
+          p[o] = r[o] + be[k] * p[o];
+        }
+    }
   }
 }
 
-__global__ void k_cg_zero(int64_t len, double* x, const CGState* st) {
-  if (!st->zero_x) return;
-  for (int64_t i = gtid(); i < len; i += gstride()) x[i] = 0.0;
+// x = 0 for segments whose right-hand side vanished
+template <typename T>
+__global__ void k_cg_zero(DSeg G, int epr, T* x, const CGState* st) {
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    if (!st[seg].zero_x) continue;
+    const int64_t e0 = (int64_t)G.item_sl0[item] * 32 * epr;
+    const int64_t e1 = (int64_t)G.item_sl1[item] * 32 * epr;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) x[i] = T(0);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
 // F^ms / G operators (Sec. 2.3): right-hand sides and derivatives as row gathers
 // ------------------------------------------------------------------------------------------
-// b_i = sum_j F_{ij,a} m_{j,a}  (Eq. RHS_b divided by m_s); pinned entry 0
+// b_i = sum_j F_{ij,a} m_{j,a}  (Eq. RHS_b divided by m_s); the segment's pinned entry is 0
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, const T* __restrict__ Fv,
+__global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, DSeg G, const T* __restrict__ Fv,
                                                  const T* __restrict__ m, int64_t ld,
-                                                 double* __restrict__ b, int64_t pin) {
+                                                 T* __restrict__ b) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
@@ -449,14 +576,14 @@ __global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, const T* __restrict__ 
              __ldcs(fp + 64) * __ldg(m + 2 * ld + j);
     }
     const int64_t row = s * 32 + lane;
-    if (row < A.n) b[row] = row == pin ? 0.0 : (double)acc;
+    if (row < A.n) b[row] = row == G.seg_pin[G.seg_of_slice[s]] ? T(0) : acc;
   }
 }
 
 // h~_d,a = (F_a U)_i / M_L,i  (= -grad U, Sec. 2.3 with the lumped-mass normalisation)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_fgrad(DSell A, const T* __restrict__ Fv,
-                                                  const double* __restrict__ U,
+                                                  const T* __restrict__ U,
                                                   const double* __restrict__ invML,
                                                   T* __restrict__ hd, int64_t ld) {
   const int lane = threadIdx.x & 31;
@@ -486,11 +613,11 @@ __global__ void __launch_bounds__(kBlock) k_fgrad(DSell A, const T* __restrict__
   }
 }
 
-// E = E_bar + sym grad u with grad_a u_b = -(F_a u_b)_i / M_L,i; E stored SoA Voigt
+// E = E_bar(segment) + sym grad u with grad_a u_b = -(F_a u_b)_i / M_L,i; E stored SoA Voigt
 // (11, 22, 33, 23, 13, 12) with tensor shear components
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, const T* __restrict__ Fv,
-                                                    const double* __restrict__ u,
+__global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, DSeg G, const T* __restrict__ Fv,
+                                                    const T* __restrict__ u,
                                                     const double* __restrict__ invML,
                                                     const double* __restrict__ Ebar,
                                                     T* __restrict__ E, int64_t ld) {
@@ -515,23 +642,24 @@ __global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, const T* __restrict
     }
     const int64_t row = s * 32 + lane;
     if (row < A.n) {
+      const double* eb = Ebar + 6 * G.seg_of_slice[s];
       const T im = -(T)invML[row];  // g[a][b] * im = d_a u_b
-      E[row] = (T)Ebar[0] + g[0][0] * im;
-      E[ld + row] = (T)Ebar[1] + g[1][1] * im;
-      E[2 * ld + row] = (T)Ebar[2] + g[2][2] * im;
-      E[3 * ld + row] = (T)Ebar[3] + T(0.5) * (g[1][2] + g[2][1]) * im;
-      E[4 * ld + row] = (T)Ebar[4] + T(0.5) * (g[0][2] + g[2][0]) * im;
-      E[5 * ld + row] = (T)Ebar[5] + T(0.5) * (g[0][1] + g[1][0]) * im;
+      E[row] = (T)eb[0] + g[0][0] * im;
+      E[ld + row] = (T)eb[1] + g[1][1] * im;
+      E[2 * ld + row] = (T)eb[2] + g[2][2] * im;
+      E[3 * ld + row] = (T)eb[3] + T(0.5) * (g[1][2] + g[2][1]) * im;
+      E[4 * ld + row] = (T)eb[4] + T(0.5) * (g[0][2] + g[2][0]) * im;
+      E[5 * ld + row] = (T)eb[5] + T(0.5) * (g[0][1] + g[1][0]) * im;
     }
   }
 }
 
 // b^mech_(i,a) = sum_j sum_c G_{ij,c} sigma0_{j,ac}, sigma0 = C E0 (nodal, [n][6] Voigt);
-// pinned node's entries 0  (= F^mech E0 of Eq. RHS_b for a spatially uniform C)
+// the segment's pinned node's entries are 0  (= F^mech E0 of Eq. RHS_b for a uniform C)
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, const T* __restrict__ Gv,
+__global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, DSeg G, const T* __restrict__ Gv,
                                                  const T* __restrict__ sig0,
-                                                 double* __restrict__ b, int64_t pin) {
+                                                 T* __restrict__ b) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
@@ -554,10 +682,10 @@ __global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, const T* __restrict__ 
     }
     const int64_t row = s * 32 + lane;
     if (row < A.n) {
-      const bool pz = row == pin;
-      b[3 * row] = pz ? 0.0 : (double)b0;
-      b[3 * row + 1] = pz ? 0.0 : (double)b1;
-      b[3 * row + 2] = pz ? 0.0 : (double)b2;
+      const bool pz = row == G.seg_pin[G.seg_of_slice[s]];
+      b[3 * row] = pz ? T(0) : b0;
+      b[3 * row + 1] = pz ? T(0) : b1;
+      b[3 * row + 2] = pz ? T(0) : b2;
     }
   }
 }
@@ -608,25 +736,25 @@ __global__ void __launch_bounds__(kBlock) k_e0(int64_t n, const T* __restrict__ 
 }
 
 // h = -kappa m_a (|m|^2 - m_a^2) + H/m_s + (3/(mu0 ms^2)) [l100 m_a s_aa + l111 (m_b s_ab +
-// m_c s_ac)] + h~_d - N_d m_bar, with s = C (E - E0(m)); zero off Omega_m
+// m_c s_ac)] + h~_d - N_d m_bar, with s = C (E - E0(m)), H and m_bar of the node's segment;
+// zero off Omega_m
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_hfield(int64_t n, const T* __restrict__ m,
+__global__ void __launch_bounds__(kBlock) k_hfield(int64_t n, DSeg G, const T* __restrict__ m,
                                                    const T* __restrict__ hd,
                                                    const T* __restrict__ E, int64_t ld,
                                                    const double* __restrict__ mbar,
+                                                   const double* __restrict__ hz,
                                                    const uint8_t* __restrict__ mag, DevParams P,
                                                    int mode, double coef, T* __restrict__ h,
-                                                   double* __restrict__ x) {
-  T far[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    far[a] = (T)(P.hz[a] - (P.Nd[3 * a] * mbar[0] + P.Nd[3 * a + 1] * mbar[1] +
-                            P.Nd[3 * a + 2] * mbar[2]));
+                                                   T* __restrict__ x) {
   const T kap = (T)P.kappa, mec = (T)P.me_coef, l100 = (T)P.l100, l111 = (T)P.l111;
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const T mv[3] = {m[i], m[ld + i], m[2 * ld + i]};
     T hv[3] = {T(0), T(0), T(0)};
     if (mag[i]) {
+      const int seg = G.seg_of_slice[i >> 5];
+      const double* mb = mbar + 3 * seg;
+      const double* hs = hz + 3 * seg;
       T e0[6], d[6], s[6];
       e0_of<T>(mv[0], mv[1], mv[2], P, e0);
 #pragma unroll
@@ -638,9 +766,11 @@ __global__ void __launch_bounds__(kBlock) k_hfield(int64_t n, const T* __restric
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const T far = (T)(hs[a] - (P.Nd[3 * a] * mb[0] + P.Nd[3 * a + 1] * mb[1] +
+                                   P.Nd[3 * a + 2] * mb[2]));
         const T an = -kap * mv[a] * (m2sum - mv[a] * mv[a]);
         const T me = mec * (l100 * mv[a] * S[a][a] + l111 * (mv[b] * S[a][b] + mv[c] * S[a][c]));
-        hv[a] = an + far[a] + me + hd[a * ld + i];
+        hv[a] = an + far + me + hd[a * ld + i];
       }
     }
     if (mode == 0) {
@@ -648,7 +778,7 @@ __global__ void __launch_bounds__(kBlock) k_hfield(int64_t n, const T* __restric
       for (int a = 0; a < 3; ++a) h[a * ld + i] = hv[a];
     } else {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a * ld + i] = (double)mv[a] + coef * (double)hv[a];
+      for (int a = 0; a < 3; ++a) x[a * ld + i] = (T)((double)mv[a] + coef * (double)hv[a]);
     }
   }
 }
@@ -657,11 +787,11 @@ __global__ void __launch_bounds__(kBlock) k_hfield(int64_t n, const T* __restric
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_prep(int64_t n, int64_t ld, const T* __restrict__ m,
                                                     const T* __restrict__ h, double dtau, int c0,
-                                                    int nc, double* __restrict__ x) {
+                                                    int nc, T* __restrict__ x) {
   for (int64_t i = gtid(); i < n; i += gstride())
     for (int k = 0; k < nc; ++k) {
       const int c = c0 + k;
-      x[k * ld + i] = (double)m[c * ld + i] + dtau * (double)h[c * ld + i];
+      x[k * ld + i] = (T)((double)m[c * ld + i] + dtau * (double)h[c * ld + i]);
     }
 }
 
@@ -678,23 +808,22 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_stage(int64_t n, int64_t ld, int stage, int printed,
                                                      const T* __restrict__ m,
                                                      const T* __restrict__ h, double dtau,
-                                                     double* __restrict__ x,
-                                                     T* __restrict__ ms) {
+                                                     T* __restrict__ x, T* __restrict__ ms) {
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const double m1 = m[i], m2 = m[ld + i], m3 = m[2 * ld + i];
     if (!printed) {
       if (stage == 1) {
-        const double s1 = m1 + (x[i] * m3 - x[ld + i] * m2);
+        const double s1 = m1 + ((double)x[i] * m3 - (double)x[ld + i] * m2);
         ms[i] = (T)s1;
-        x[2 * ld + i] = (double)(T)s1 + dtau * (double)h[i];
+        x[2 * ld + i] = (T)((double)(T)s1 + dtau * (double)h[i]);
       } else if (stage == 2) {
         const double s1 = ms[i];
-        const double s2 = m2 + (x[ld + i] * s1 - x[2 * ld + i] * m3);
+        const double s2 = m2 + ((double)x[ld + i] * s1 - (double)x[2 * ld + i] * m3);
         ms[ld + i] = (T)s2;
-        x[i] = (double)(T)s2 + dtau * (double)h[ld + i];
+        x[i] = (T)((double)(T)s2 + dtau * (double)h[ld + i]);
       } else {
         const double s1 = ms[i], s2 = ms[ld + i];
-        ms[2 * ld + i] = (T)(m3 + (x[2 * ld + i] * s2 - x[i] * s1));
+        ms[2 * ld + i] = (T)(m3 + ((double)x[2 * ld + i] * s2 - (double)x[i] * s1));
       }
     } else {
       if (stage == 1) {
@@ -703,41 +832,48 @@ __global__ void __launch_bounds__(kBlock) k_gs_stage(int64_t n, int64_t ld, int 
         const double s2 = m2 + (g3 * m1 - g1 * m3);
         ms[i] = (T)s1;
         ms[ld + i] = (T)s2;
-        x[i] = (double)(T)s1 + dtau * (double)h[i];
-        x[ld + i] = (double)(T)s2 + dtau * (double)h[ld + i];
+        x[i] = (T)((double)(T)s1 + dtau * (double)h[i]);
+        x[ld + i] = (T)((double)(T)s2 + dtau * (double)h[ld + i]);
       } else {
         const double s1 = ms[i], s2 = ms[ld + i];
-        ms[2 * ld + i] = (T)(m3 + (x[i] * s2 - x[ld + i] * s1));
+        ms[2 * ld + i] = (T)(m3 + ((double)x[i] * s2 - (double)x[ld + i] * s1));
       }
     }
   }
 }
 
-// Algorithm B.1 step 4: m = m** / |m**| on Omega_m; <|m_new - m_old|> over magnetic nodes
+// Algorithm B.1 step 4: m = m** / |m**| on Omega_m; <|m_new - m_old|> over each segment's
+// magnetic nodes
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_project(int64_t n, int64_t ld,
-                                                    const double* __restrict__ x,
+__global__ void __launch_bounds__(kBlock) k_project(DSeg G, int64_t ld, const T* __restrict__ x,
                                                     const uint8_t* __restrict__ mag,
                                                     T* __restrict__ m, double* dm_out,
-                                                    double inv_nmag, Red red) {
-  double v[1] = {0.0};
-  for (int64_t i = gtid(); i < n; i += gstride()) {
-    if (!mag[i]) continue;
-    const T a = (T)x[i], b = (T)x[ld + i], c = (T)x[2 * ld + i];
-    const T inv = T(1) / sqrt(a * a + b * b + c * c);
-    const T na = a * inv, nb = b * inv, nc = c * inv;
-    const T da = na - m[i], db = nb - m[ld + i], dc = nc - m[2 * ld + i];
-    v[0] += (double)sqrt(da * da + db * db + dc * dc);
-    m[i] = na;
-    m[ld + i] = nb;
-    m[2 * ld + i] = nc;
+                                                    const double* __restrict__ inv_nmag,
+                                                    Red red) {
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+    const int seg = G.item_seg[item];
+    double v[1] = {0.0};
+    const int64_t r0 = (int64_t)G.item_sl0[item] * 32, r1 = (int64_t)G.item_sl1[item] * 32;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      if (!mag[i]) continue;
+      const T a = x[i], b = x[ld + i], c = x[2 * ld + i];
+      const T inv = T(1) / sqrt(a * a + b * b + c * c);
+      const T na = a * inv, nb = b * inv, nc = c * inv;
+      const T da = na - m[i], db = nb - m[ld + i], dc = nc - m[2 * ld + i];
+      v[0] += (double)sqrt(da * da + db * db + dc * dc);
+      m[i] = na;
+      m[ld + i] = nb;
+      m[2 * ld + i] = nc;
+    }
+    __shared__ double res[1];
+    if (seg_reduce<1>(v, item, seg, G, red, res) && threadIdx.x == 0)
+      dm_out[seg] = res[0] * inv_nmag[seg];
   }
-  __shared__ double res[1];
-  if (grid_reduce<1>(v, red, res) && threadIdx.x == 0) *dm_out = res[0] * inv_nmag;
 }
 
 // ------------------------------------------------------------------------------------------
-// layout changes between the ABI ([n][nc] float64, unique-node order) and internal arrays
+// layout changes between the ABI ([n][nc] float64, unique-node order) and internal arrays;
+// perm[i] < 0 marks a padding row (no node)
 // ------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_import(int64_t n, int nc, const double* __restrict__ src,
@@ -745,7 +881,7 @@ __global__ void k_import(int64_t n, int nc, const double* __restrict__ src,
                          int64_t ns, const uint8_t* __restrict__ mask) {
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const int64_t o = perm[i];
-    const bool z = mask && !mask[i];
+    const bool z = o < 0 || (mask && !mask[i]);
     for (int c = 0; c < nc; ++c) dst[i * ns + c * cs] = z ? T(0) : (T)src[o * nc + c];
   }
 }
@@ -755,6 +891,7 @@ __global__ void k_export(int64_t n, int nc, const T* __restrict__ src, int64_t c
                          const int64_t* __restrict__ perm, double* __restrict__ dst) {
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const int64_t o = perm[i];
+    if (o < 0) continue;
     for (int c = 0; c < nc; ++c) dst[o * nc + c] = (double)src[i * ns + c * cs];
   }
 }
@@ -764,179 +901,314 @@ __global__ void k_convert(int64_t len, const S* __restrict__ s, D* __restrict__ 
   for (int64_t i = gtid(); i < len; i += gstride()) d[i] = (D)s[i];
 }
 
+// linear extrapolation of the previous two solutions: u <- 2 u - u2, u2 <- old u
+template <typename T>
+__global__ void k_extrapolate(int64_t len, T* __restrict__ u, T* __restrict__ u2) {
+  for (int64_t i = gtid(); i < len; i += gstride()) {
+    const T a = u[i], b = u2[i];
+    u2[i] = a;
+    u[i] = T(2) * a - b;
+  }
+}
+
+// t = (a - (2 b - c)) * scale
+template <typename T>
+__global__ void k_scaled_diff(int64_t len, const T* __restrict__ a, const T* __restrict__ b,
+                              const T* __restrict__ c, double scale, float* __restrict__ t) {
+  for (int64_t i = gtid(); i < len; i += gstride())
+    t[i] = (float)(((double)a[i] - (2.0 * (double)b[i] - (double)c[i])) * scale);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-#define GSPM_LAUNCH(L, threads) \
-  (*(L).counter) += 1;          \
-  const int nb = (L).blocks_for(threads)
-
-template <typename T>
-cudaError_t launch_wsum(const Launch& L, int64_t n, int nc, const T* f, int64_t cs, int64_t ns,
-                        const int64_t* perm, const double* w, double* out, const double* add,
-                        Red red) {
-  GSPM_LAUNCH(L, n);
-  k_wsum<T><<<nb, kBlock, 0, L.stream>>>(n, nc, f, cs, ns, perm, w, out, add, red);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, const T* x, T* y) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  if (B == 1)
-    k_spmv1<T><<<nb, kBlock, 0, L.stream>>>(A, val, x, y);
-  else
-    k_spmv9<T><<<nb, kBlock, 0, L.stream>>>(A, val, x, y);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_cg_init(const Launch& L, const DSell& A, const T* val, int B, const double* b,
-                           double* x, double* r, T* p, CGState* st, double rtol, int max_iter,
-                           Red red) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  if (B == 1)
-    k_cg_init<T, 1><<<nb, kBlock, 0, L.stream>>>(A, val, b, x, r, p, st, rtol, max_iter, red);
-  else
-    k_cg_init<T, 9><<<nb, kBlock, 0, L.stream>>>(A, val, b, x, r, p, st, rtol, max_iter, red);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const T* aval, const T* mval,
-                              int nr, int64_t ld, double* x, double* r, T* p, CGState* st,
-                              double rtol, int max_iter, Red red) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  switch (nr) {
-    case 1: k_cg_init_gs<T, 1><<<nb, kBlock, 0, L.stream>>>(A, aval, mval, ld, x, r, p, st, rtol, max_iter, red); break;
-    case 2: k_cg_init_gs<T, 2><<<nb, kBlock, 0, L.stream>>>(A, aval, mval, ld, x, r, p, st, rtol, max_iter, red); break;
-    case 3: k_cg_init_gs<T, 3><<<nb, kBlock, 0, L.stream>>>(A, aval, mval, ld, x, r, p, st, rtol, max_iter, red); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const T* val, int B, int nr,
-                           int64_t ld, const T* p, T* q, CGState* st, Red red) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  if (B == 9) {
-    k_cg_spmv<T, 9, 1><<<nb, kBlock, 0, L.stream>>>(A, val, ld, p, q, st, red);
-  } else {
-    switch (nr) {
-      case 1: k_cg_spmv<T, 1, 1><<<nb, kBlock, 0, L.stream>>>(A, val, ld, p, q, st, red); break;
-      case 2: k_cg_spmv<T, 1, 2><<<nb, kBlock, 0, L.stream>>>(A, val, ld, p, q, st, red); break;
-      case 3: k_cg_spmv<T, 1, 3><<<nb, kBlock, 0, L.stream>>>(A, val, ld, p, q, st, red); break;
-      default: return cudaErrorInvalidValue;
+int grid_for(const Launch& L, int64_t threads, const void* kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> occ;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = occ.find(kernel);
+    if (it == occ.end()) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess ||
+          nb < 1)
+        nb = 1;
+      it = occ.emplace(kernel, nb).first;
     }
+    per_sm = it->second;
+  }
+  int64_t b = (threads + kBlock - 1) / kBlock;
+  const int64_t cap = std::min<int64_t>((int64_t)per_sm * L.sms, L.max_blocks);
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+// grid of an item-loop kernel: one block per item, capped at the resident capacity
+static int item_grid(const Launch& L, const DSeg& G, const void* kernel) {
+  return grid_for(L, (int64_t)G.nitems * kBlock, kernel);
+}
+
+#define GSPM_GRID(L, threads, kern) grid_for((L), (threads), reinterpret_cast<const void*>(kern))
+#define GSPM_IGRID(L, G, kern) item_grid((L), (G), reinterpret_cast<const void*>(kern))
+
+template <typename T>
+cudaError_t launch_wsum(const Launch& L, const DSeg& G, int nc, const T* f, int64_t cs,
+                        int64_t ns, const int64_t* perm, const double* w, double* out,
+                        const double* add, Red red) {
+  (*L.counter) += 1;
+  auto k = k_wsum<T>;
+  k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, nc, f, cs, ns, perm, w, out, add, red);
+  return cudaGetLastError();
+}
+
+template <typename T, int VAR>
+static void spmv_variant(const Launch& L, const DSell& A, const T* val, int B, const T* x, T* y) {
+  const int64_t threads = (VAR == 2 ? 64 : 32) * A.nslices;
+  if (B == 1) {
+    auto k = k_spmv1<T, VAR>;
+    k<<<GSPM_GRID(L, threads, k), kBlock, 0, L.stream>>>(A, val, x, y);
+  } else {
+    auto k = k_spmv9<T, VAR>;
+    k<<<GSPM_GRID(L, threads, k), kBlock, 0, L.stream>>>(A, val, x, y);
+  }
+}
+
+template <typename T>
+cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, const T* x, T* y,
+                        int variant) {
+  (*L.counter) += 1;
+  switch (variant) {
+    case 1: spmv_variant<T, 1>(L, A, val, B, x, y); break;
+    case 2: spmv_variant<T, 2>(L, A, val, B, x, y); break;
+    default: spmv_variant<T, 0>(L, A, val, B, x, y); break;
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_cg_update(const Launch& L, int64_t len, int nr, int64_t ld, double* x,
-                             double* r, const T* p, const T* q, CGState* st, Red red) {
-  GSPM_LAUNCH(L, len);
+cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
+                           const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
+                           int max_iter, Red red) {
+  (*L.counter) += 1;
+  if (B == 1) {
+    auto k = k_cg_init<T, 1>;
+    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, b, x, r, p, st, nactive, rtol,
+                                                    max_iter, red);
+  } else {
+    auto k = k_cg_init<T, 9>;
+    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, b, x, r, p, st, nactive, rtol,
+                                                    max_iter, red);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
+                              const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
+                              int* nactive, double rtol, int max_iter, Red red) {
+  (*L.counter) += 1;
   switch (nr) {
-    case 1: k_cg_update<T, 1><<<nb, kBlock, 0, L.stream>>>(len, ld, x, r, p, q, st, red); break;
-    case 2: k_cg_update<T, 2><<<nb, kBlock, 0, L.stream>>>(len, ld, x, r, p, q, st, red); break;
-    case 3: k_cg_update<T, 3><<<nb, kBlock, 0, L.stream>>>(len, ld, x, r, p, q, st, red); break;
+    case 1: {
+      auto k = k_cg_init_gs<T, 1>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, aval, mval, ld, x, r, p, st, nactive,
+                                                      rtol, max_iter, red);
+      break;
+    }
+    case 2: {
+      auto k = k_cg_init_gs<T, 2>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, aval, mval, ld, x, r, p, st, nactive,
+                                                      rtol, max_iter, red);
+      break;
+    }
+    case 3: {
+      auto k = k_cg_init_gs<T, 3>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, aval, mval, ld, x, r, p, st, nactive,
+                                                      rtol, max_iter, red);
+      break;
+    }
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int VAR>
+static cudaError_t cg_spmv_variant(const Launch& L, const DSell& A, const DSeg& G, const T* val,
+                                   int B, int nr, int64_t ld, const T* p, T* q, CGState* st,
+                                   Red red) {
+  if (B == 9) {
+    auto k = k_cg_spmv<T, 9, 1, VAR>;
+    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+  } else if (nr == 1) {
+    auto k = k_cg_spmv<T, 1, 1, VAR>;
+    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+  } else if (nr == 2) {
+    auto k = k_cg_spmv<T, 1, 2, VAR>;
+    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+  } else if (nr == 3) {
+    auto k = k_cg_spmv<T, 1, 3, VAR>;
+    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
+                           int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
+                           int variant) {
+  (*L.counter) += 1;
+  switch (variant) {
+    case 1: return cg_spmv_variant<T, 1>(L, A, G, val, B, nr, ld, p, q, st, red);
+    case 2: return cg_spmv_variant<T, 2>(L, A, G, val, B, nr, ld, p, q, st, red);
+    default: return cg_spmv_variant<T, 0>(L, A, G, val, B, nr, ld, p, q, st, red);
+  }
+}
+
+template <typename T>
+cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
+                             T* r, const T* p, const T* q, CGState* st, int* nactive, Red red) {
+  (*L.counter) += 1;
+  switch (nr) {
+    case 1: {
+      auto k = k_cg_update<T, 1>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, x, r, p, q, st, nactive, red);
+      break;
+    }
+    case 2: {
+      auto k = k_cg_update<T, 2>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, x, r, p, q, st, nactive, red);
+      break;
+    }
+    case 3: {
+      auto k = k_cg_update<T, 3>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, x, r, p, q, st, nactive, red);
+      break;
+    }
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_cg_pupdate(const Launch& L, int64_t len, int nr, int64_t ld, const double* r,
-                              T* p, const CGState* st) {
-  GSPM_LAUNCH(L, len);
+cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
+                              const T* r, T* p, const CGState* st) {
+  (*L.counter) += 1;
   switch (nr) {
-    case 1: k_cg_pupdate<T, 1><<<nb, kBlock, 0, L.stream>>>(len, ld, r, p, st); break;
-    case 2: k_cg_pupdate<T, 2><<<nb, kBlock, 0, L.stream>>>(len, ld, r, p, st); break;
-    case 3: k_cg_pupdate<T, 3><<<nb, kBlock, 0, L.stream>>>(len, ld, r, p, st); break;
+    case 1: {
+      auto k = k_cg_pupdate<T, 1>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, r, p, st);
+      break;
+    }
+    case 2: {
+      auto k = k_cg_pupdate<T, 2>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, r, p, st);
+      break;
+    }
+    case 3: {
+      auto k = k_cg_pupdate<T, 3>;
+      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, r, p, st);
+      break;
+    }
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_zero(const Launch& L, int64_t len, double* x, const CGState* st) {
-  GSPM_LAUNCH(L, len);
-  k_cg_zero<<<nb, kBlock, 0, L.stream>>>(len, x, st);
+template <typename T>
+cudaError_t launch_cg_zero(const Launch& L, const DSeg& G, int epr, T* x, const CGState* st) {
+  (*L.counter) += 1;
+  auto k = k_cg_zero<T>;
+  k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, x, st);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fdiv(const Launch& L, const DSell& A, const T* Fv, const T* m, int64_t ld,
-                        double* b, int64_t pin) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  k_fdiv<T><<<nb, kBlock, 0, L.stream>>>(A, Fv, m, ld, b, pin);
+cudaError_t launch_fdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Fv, const T* m,
+                        int64_t ld, T* b) {
+  (*L.counter) += 1;
+  auto k = k_fdiv<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Fv, m, ld, b);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const double* U,
+cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U,
                          const double* invML, T* hd, int64_t ld) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  k_fgrad<T><<<nb, kBlock, 0, L.stream>>>(A, Fv, U, invML, hd, ld);
+  (*L.counter) += 1;
+  auto k = k_fgrad<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, Fv, U, invML, hd, ld);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fstrain(const Launch& L, const DSell& A, const T* Fv, const double* u,
-                           const double* invML, const double* Ebar, T* E, int64_t ld) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  k_fstrain<T><<<nb, kBlock, 0, L.stream>>>(A, Fv, u, invML, Ebar, E, ld);
+cudaError_t launch_fstrain(const Launch& L, const DSell& A, const DSeg& G, const T* Fv,
+                           const T* u, const double* invML, const double* Ebar, T* E,
+                           int64_t ld) {
+  (*L.counter) += 1;
+  auto k = k_fstrain<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Fv, u, invML, Ebar, E, ld);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gdiv(const Launch& L, const DSell& A, const T* Gv, const T* sig0, double* b,
-                        int64_t pin) {
-  GSPM_LAUNCH(L, A.nslices * 32);
-  k_gdiv<T><<<nb, kBlock, 0, L.stream>>>(A, Gv, sig0, b, pin);
+cudaError_t launch_gdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Gv,
+                        const T* sig0, T* b) {
+  (*L.counter) += 1;
+  auto k = k_gdiv<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Gv, sig0, b);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_e0(const Launch& L, int64_t n, const T* m, int64_t ld, const uint8_t* mag,
                       const DevParams& P, T* E0, T* sig0) {
-  GSPM_LAUNCH(L, n);
-  k_e0<T><<<nb, kBlock, 0, L.stream>>>(n, m, ld, mag, P, E0, sig0);
+  (*L.counter) += 1;
+  auto k = k_e0<T>;
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, m, ld, mag, P, E0, sig0);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_hfield(const Launch& L, int64_t n, const T* m, const T* hd, const T* E,
-                          int64_t ld, const double* mbar, const uint8_t* mag, const DevParams& P,
-                          int mode, double coef, T* h, double* x) {
-  GSPM_LAUNCH(L, n);
-  k_hfield<T><<<nb, kBlock, 0, L.stream>>>(n, m, hd, E, ld, mbar, mag, P, mode, coef, h, x);
+cudaError_t launch_hfield(const Launch& L, int64_t n, const DSeg& G, const T* m, const T* hd,
+                          const T* E, int64_t ld, const double* mbar, const double* hz,
+                          const uint8_t* mag, const DevParams& P, int mode, double coef, T* h,
+                          T* x) {
+  (*L.counter) += 1;
+  auto k = k_hfield<T>;
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, G, m, hd, E, ld, mbar, hz, mag, P, mode,
+                                                  coef, h, x);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gs_prep(const Launch& L, int64_t n, int64_t ld, const T* m, const T* h,
-                           double dtau, int c0, int nc, double* x) {
-  GSPM_LAUNCH(L, n);
-  k_gs_prep<T><<<nb, kBlock, 0, L.stream>>>(n, ld, m, h, dtau, c0, nc, x);
+                           double dtau, int c0, int nc, T* x) {
+  (*L.counter) += 1;
+  auto k = k_gs_prep<T>;
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, ld, m, h, dtau, c0, nc, x);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gs_stage(const Launch& L, int64_t n, int64_t ld, int stage, int printed,
-                            const T* m, const T* h, double dtau, double* x, T* ms) {
-  GSPM_LAUNCH(L, n);
-  k_gs_stage<T><<<nb, kBlock, 0, L.stream>>>(n, ld, stage, printed, m, h, dtau, x, ms);
+                            const T* m, const T* h, double dtau, T* x, T* ms) {
+  (*L.counter) += 1;
+  auto k = k_gs_stage<T>;
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, ld, stage, printed, m, h, dtau, x, ms);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_project(const Launch& L, int64_t n, int64_t ld, const double* x,
-                           const uint8_t* mag, T* m, double* dm_out, double inv_nmag, Red red) {
-  GSPM_LAUNCH(L, n);
-  k_project<T><<<nb, kBlock, 0, L.stream>>>(n, ld, x, mag, m, dm_out, inv_nmag, red);
+cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* x,
+                           const uint8_t* mag, T* m, double* dm_out, const double* inv_nmag,
+                           Red red) {
+  (*L.counter) += 1;
+  auto k = k_project<T>;
+  k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, ld, x, mag, m, dm_out, inv_nmag, red);
   return cudaGetLastError();
 }
 
@@ -944,70 +1216,96 @@ template <typename T>
 cudaError_t launch_import(const Launch& L, int64_t n, int nc, const double* src,
                           const int64_t* perm, T* dst, int64_t cs, int64_t ns,
                           const uint8_t* mask) {
-  GSPM_LAUNCH(L, n);
-  k_import<T><<<nb, kBlock, 0, L.stream>>>(n, nc, src, perm, dst, cs, ns, mask);
+  (*L.counter) += 1;
+  auto k = k_import<T>;
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, nc, src, perm, dst, cs, ns, mask);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_export(const Launch& L, int64_t n, int nc, const T* src, int64_t cs,
                           int64_t ns, const int64_t* perm, double* dst) {
-  GSPM_LAUNCH(L, n);
-  k_export<T><<<nb, kBlock, 0, L.stream>>>(n, nc, src, cs, ns, perm, dst);
+  (*L.counter) += 1;
+  auto k = k_export<T>;
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, nc, src, cs, ns, perm, dst);
   return cudaGetLastError();
 }
 
 template <typename S, typename D>
 cudaError_t launch_convert(const Launch& L, int64_t len, const S* src, D* dst) {
-  GSPM_LAUNCH(L, len);
-  k_convert<S, D><<<nb, kBlock, 0, L.stream>>>(len, src, dst);
+  (*L.counter) += 1;
+  auto k = k_convert<S, D>;
+  k<<<GSPM_GRID(L, len, k), kBlock, 0, L.stream>>>(len, src, dst);
   return cudaGetLastError();
 }
 
-#define GSPM_INSTANTIATE(T)                                                                      \
-  template cudaError_t launch_wsum<T>(const Launch&, int64_t, int, const T*, int64_t, int64_t,   \
-                                      const int64_t*, const double*, double*, const double*, Red); \
-  template cudaError_t launch_spmv<T>(const Launch&, const DSell&, const T*, int, const T*, T*); \
-  template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const T*, int,             \
-                                         const double*, double*, double*, T*, CGState*, double,  \
-                                         int, Red);                                               \
-  template cudaError_t launch_cg_init_gs<T>(const Launch&, const DSell&, const T*, const T*, int, \
-                                            int64_t, double*, double*, T*, CGState*, double,     \
-                                            int, Red);                                            \
-  template cudaError_t launch_cg_spmv<T>(const Launch&, const DSell&, const T*, int, int,        \
-                                         int64_t, const T*, T*, CGState*, Red);                  \
-  template cudaError_t launch_cg_update<T>(const Launch&, int64_t, int, int64_t, double*,        \
-                                           double*, const T*, const T*, CGState*, Red);          \
-  template cudaError_t launch_cg_pupdate<T>(const Launch&, int64_t, int, int64_t, const double*, \
-                                            T*, const CGState*);                                  \
-  template cudaError_t launch_fdiv<T>(const Launch&, const DSell&, const T*, const T*, int64_t,  \
-                                      double*, int64_t);                                          \
-  template cudaError_t launch_fgrad<T>(const Launch&, const DSell&, const T*, const double*,     \
+template <typename T>
+cudaError_t launch_extrapolate(const Launch& L, int64_t len, T* u, T* u2) {
+  (*L.counter) += 1;
+  auto k = k_extrapolate<T>;
+  k<<<GSPM_GRID(L, len, k), kBlock, 0, L.stream>>>(len, u, u2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T* b, const T* c,
+                               double scale, float* t) {
+  (*L.counter) += 1;
+  auto k = k_scaled_diff<T>;
+  k<<<GSPM_GRID(L, len, k), kBlock, 0, L.stream>>>(len, a, b, c, scale, t);
+  return cudaGetLastError();
+}
+
+#define GSPM_INSTANTIATE(T)                                                                       \
+  template cudaError_t launch_wsum<T>(const Launch&, const DSeg&, int, const T*, int64_t,        \
+                                      int64_t, const int64_t*, const double*, double*,            \
+                                      const double*, Red);                                        \
+  template cudaError_t launch_spmv<T>(const Launch&, const DSell&, const T*, int, const T*, T*,   \
+                                      int);                                                       \
+  template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
+                                         const T*, T*, T*, T*, CGState*, int*, double, int, Red); \
+  template cudaError_t launch_cg_init_gs<T>(const Launch&, const DSell&, const DSeg&, const T*,   \
+                                            const T*, int, int64_t, T*, T*, T*, CGState*, int*,   \
+                                            double, int, Red);                                    \
+  template cudaError_t launch_cg_spmv<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
+                                         int, int64_t, const T*, T*, CGState*, Red, int);         \
+  template cudaError_t launch_cg_update<T>(const Launch&, const DSeg&, int, int, int64_t, T*, T*, \
+                                           const T*, const T*, CGState*, int*, Red);              \
+  template cudaError_t launch_cg_pupdate<T>(const Launch&, const DSeg&, int, int, int64_t,        \
+                                            const T*, T*, const CGState*);                        \
+  template cudaError_t launch_cg_zero<T>(const Launch&, const DSeg&, int, T*, const CGState*);    \
+  template cudaError_t launch_fdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
+                                      const T*, int64_t, T*);                                     \
+  template cudaError_t launch_fgrad<T>(const Launch&, const DSell&, const T*, const T*,           \
                                        const double*, T*, int64_t);                               \
-  template cudaError_t launch_fstrain<T>(const Launch&, const DSell&, const T*, const double*,   \
-                                         const double*, const double*, T*, int64_t);              \
-  template cudaError_t launch_gdiv<T>(const Launch&, const DSell&, const T*, const T*, double*,  \
-                                      int64_t);                                                   \
-  template cudaError_t launch_e0<T>(const Launch&, int64_t, const T*, int64_t, const uint8_t*,   \
+  template cudaError_t launch_fstrain<T>(const Launch&, const DSell&, const DSeg&, const T*,      \
+                                         const T*, const double*, const double*, T*, int64_t);    \
+  template cudaError_t launch_gdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
+                                      const T*, T*);                                              \
+  template cudaError_t launch_e0<T>(const Launch&, int64_t, const T*, int64_t, const uint8_t*,    \
                                     const DevParams&, T*, T*);                                    \
-  template cudaError_t launch_hfield<T>(const Launch&, int64_t, const T*, const T*, const T*,    \
-                                        int64_t, const double*, const uint8_t*,                  \
-                                        const DevParams&, int, double, T*, double*);              \
-  template cudaError_t launch_gs_prep<T>(const Launch&, int64_t, int64_t, const T*, const T*,    \
-                                         double, int, int, double*);                              \
-  template cudaError_t launch_gs_stage<T>(const Launch&, int64_t, int64_t, int, int, const T*,   \
-                                          const T*, double, double*, T*);                         \
-  template cudaError_t launch_project<T>(const Launch&, int64_t, int64_t, const double*,         \
-                                         const uint8_t*, T*, double*, double, Red);               \
-  template cudaError_t launch_import<T>(const Launch&, int64_t, int, const double*,              \
+  template cudaError_t launch_hfield<T>(const Launch&, int64_t, const DSeg&, const T*, const T*,  \
+                                        const T*, int64_t, const double*, const double*,          \
+                                        const uint8_t*, const DevParams&, int, double, T*, T*);   \
+  template cudaError_t launch_gs_prep<T>(const Launch&, int64_t, int64_t, const T*, const T*,     \
+                                         double, int, int, T*);                                   \
+  template cudaError_t launch_gs_stage<T>(const Launch&, int64_t, int64_t, int, int, const T*,    \
+                                          const T*, double, T*, T*);                              \
+  template cudaError_t launch_project<T>(const Launch&, const DSeg&, int64_t, const T*,           \
+                                         const uint8_t*, T*, double*, const double*, Red);        \
+  template cudaError_t launch_import<T>(const Launch&, int64_t, int, const double*,               \
                                         const int64_t*, T*, int64_t, int64_t, const uint8_t*);    \
-  template cudaError_t launch_export<T>(const Launch&, int64_t, int, const T*, int64_t, int64_t, \
-                                        const int64_t*, double*);
+  template cudaError_t launch_export<T>(const Launch&, int64_t, int, const T*, int64_t, int64_t,  \
+                                        const int64_t*, double*);                                 \
+  template cudaError_t launch_extrapolate<T>(const Launch&, int64_t, T*, T*);                     \
+  template cudaError_t launch_scaled_diff<T>(const Launch&, int64_t, const T*, const T*,          \
+                                             const T*, double, float*);
 
 GSPM_INSTANTIATE(double)
 GSPM_INSTANTIATE(float)
 template cudaError_t launch_convert<double, float>(const Launch&, int64_t, const double*, float*);
 template cudaError_t launch_convert<float, double>(const Launch&, int64_t, const float*, double*);
 template cudaError_t launch_convert<double, double>(const Launch&, int64_t, const double*, double*);
+template cudaError_t launch_convert<float, float>(const Launch&, int64_t, const float*, float*);
 
 }  // namespace gspm

@@ -16,11 +16,30 @@ struct DSell {
   int64_t n;
 };
 
-// Scratch for deterministic grid reductions: one partial per block and component, plus the
-// arrival counter of the last-block pattern (reset to 0 by the last block).
+// Scratch for deterministic reductions: one partial per work item and component.
 struct Red {
-  double* partial;     // [max_blocks * kRedComp]
-  unsigned* counter;
+  double* partial;     // [nitems * kRedComp]
+};
+
+// Segments (meshes of a batch) and the work items of the reducing kernels.  Segment s owns the
+// slices [seg_sl0[s], seg_sl0[s] + ...) and the rows [seg_row0[s], seg_row0[s] + seg_nrow[s]);
+// its last slice may end in padding rows.  Items are grouped by segment: items
+// seg_item0[s] .. seg_item0[s] + seg_nitems[s] - 1 cover its slices, item i the slices
+// [item_sl0[i], item_sl1[i]).  counter[s] is the arrival counter of segment s (kept at 0 between
+// kernels by the last arriving item).
+struct DSeg {
+  int nseg;
+  int nitems;
+  const int32_t* seg_of_slice;  // [nslices]
+  const int32_t* item_seg;      // [nitems]
+  const int32_t* item_sl0;      // [nitems]
+  const int32_t* item_sl1;      // [nitems]
+  const int32_t* seg_item0;     // [nseg]
+  const int32_t* seg_nitems;    // [nseg]
+  const int64_t* seg_row0;      // [nseg]
+  const int64_t* seg_nrow;      // [nseg]
+  const int64_t* seg_pin;       // [nseg] pinned row (global internal index)
+  unsigned* counter;            // [nseg]
 };
 constexpr int kRedComp = 16;
 constexpr int kBlock = 256;
@@ -35,17 +54,18 @@ struct CGState {
   int nr, active, max_iter, noconv, zero_x, pad[3];
 };
 
-// Material constants needed on the device (reduced units of App. B).
+// Material constants needed on the device (reduced units of App. B).  The applied field
+// H_ext / m_s is per segment (device array hz[3 * seg + a]).
 struct DevParams {
   double kappa, me_coef, l100, l111, C11, C12, C44;
-  double hz[3];   // H_ext / m_s
   double Nd[9];
   double dtau, alpha;
 };
 
 struct Launch {
   cudaStream_t stream;
-  int max_blocks;        // resident-block cap used for grid-stride kernels
+  int max_blocks;        // upper bound of any grid (sizes the reduction scratch): 8 x SMs
+  int sms;               // multiprocessors of the device
   int64_t* counter;      // kernel launches issued
   int blocks_for(int64_t threads) const {
     int64_t b = (threads + kBlock - 1) / kBlock;
@@ -54,71 +74,83 @@ struct Launch {
   }
 };
 
-// ---- launchers (T = double: plain FP64 path; T = float: mixed path) --------------------------
-template <typename T> struct Types {
-  using V = T;       // matrix values
-  using F = T;       // nodal fields m, h, h_d, E, E0, sigma0
-  using XP = T;      // CG search direction p and q = A p
-  using XR = double; // CG iterate x, residual r
-};
+// Grid for a grid-stride kernel: enough blocks for `threads`, capped at the number of blocks the
+// kernel can keep resident (occupancy x SMs, looked up once per kernel) and at max_blocks, so
+// that every block runs in the first wave.
+int grid_for(const Launch& L, int64_t threads, const void* kernel);
 
+// SpMV schedules chosen by the autotuner: 0 = one thread per row, 1 = one thread per row with
+// five neighbours' loads issued ahead of their FMAs, 2 = two threads per row (alternate
+// neighbours, combined with a shuffle).
+constexpr int kSpmvVariants = 3;
+
+// ---- launchers ----------------------------------------------------------------------------
+// T = double: plain FP64 path.  T = float: mixed path (FP32 matrices, fields and CG vectors;
+// every inner product, norm and volume average accumulated in FP64).
 template <typename T>
-cudaError_t launch_wsum(const Launch& L, int64_t n, int nc, const T* f, int64_t cs, int64_t ns,
-                        const int64_t* perm, const double* w, double* out, const double* add,
-                        Red red);
+cudaError_t launch_wsum(const Launch& L, const DSeg& G, int nc, const T* f, int64_t cs,
+                        int64_t ns, const int64_t* perm, const double* w, double* out,
+                        const double* add, Red red);  // out[seg * nc + c]
 template <typename T>
 cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, const T* x,
-                        T* y);  // B = 1 scalar, B = 9 block (x, y AoS 3)
+                        T* y, int variant = 0);  // B = 1 scalar, B = 9 block (x, y AoS 3)
+// CG pieces.  st and the arrival counters are per segment; nactive counts active segments.
+// epr = elements per row of the vectors (1: scalar, SoA with stride ld; 3: [n][3]).
 template <typename T>
-cudaError_t launch_cg_init(const Launch& L, const DSell& A, const T* val, int B, const double* b,
-                           double* x, double* r, T* p, CGState* st, double rtol, int max_iter,
-                           Red red);
+cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
+                           const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
+                           int max_iter, Red red);
 template <typename T>
-cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const T* aval, const T* mval,
-                              int nr, int64_t ld, double* x, double* r, T* p, CGState* st,
-                              double rtol, int max_iter, Red red);
+cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
+                              const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
+                              int* nactive, double rtol, int max_iter, Red red);
 template <typename T>
-cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const T* val, int B, int nr,
-                           int64_t ld, const T* p, T* q, CGState* st, Red red);
+cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
+                           int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
+                           int variant);
 template <typename T>
-cudaError_t launch_cg_update(const Launch& L, int64_t len, int nr, int64_t ld, double* x,
-                             double* r, const T* p, const T* q, CGState* st, Red red);
+cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
+                             T* r, const T* p, const T* q, CGState* st, int* nactive, Red red);
 template <typename T>
-cudaError_t launch_cg_pupdate(const Launch& L, int64_t len, int nr, int64_t ld, const double* r,
-                              T* p, const CGState* st);
-cudaError_t launch_cg_zero(const Launch& L, int64_t len, double* x, const CGState* st);
+cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
+                              const T* r, T* p, const CGState* st);
+template <typename T>
+cudaError_t launch_cg_zero(const Launch& L, const DSeg& G, int epr, T* x, const CGState* st);
 
 template <typename T>
-cudaError_t launch_fdiv(const Launch& L, const DSell& A, const T* Fv, const T* m, int64_t ld,
-                        double* b, int64_t pin);
+cudaError_t launch_fdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Fv, const T* m,
+                        int64_t ld, T* b);
 template <typename T>
-cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const double* U,
+cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U,
                          const double* invML, T* hd, int64_t ld);
 template <typename T>
-cudaError_t launch_fstrain(const Launch& L, const DSell& A, const T* Fv, const double* u,
-                           const double* invML, const double* Ebar, T* E, int64_t ld);
+cudaError_t launch_fstrain(const Launch& L, const DSell& A, const DSeg& G, const T* Fv,
+                           const T* u, const double* invML, const double* Ebar, T* E,
+                           int64_t ld);
 template <typename T>
-cudaError_t launch_gdiv(const Launch& L, const DSell& A, const T* Gv, const T* sig0, double* b,
-                        int64_t pin);
+cudaError_t launch_gdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Gv,
+                        const T* sig0, T* b);
 template <typename T>
 cudaError_t launch_e0(const Launch& L, int64_t n, const T* m, int64_t ld, const uint8_t* mag,
                       const DevParams& P, T* E0, T* sig0);
-// h(m) = h_anis + H/ms + h_me(m, C(E - E0(m))) + hd - Nd mbar at magnetic nodes, 0 elsewhere.
-// mode 0: write h (SoA 3).  mode 1: write x_c = m_c + coef * h_c (double SoA 3).
+// h(m) = h_anis + H/ms + h_me(m, C(E - E0(m))) + hd - Nd mbar at magnetic nodes, 0 elsewhere
+// (mbar, hz per segment).  mode 0: write h (SoA 3).  mode 1: write x_c = m_c + coef * h_c.
 template <typename T>
-cudaError_t launch_hfield(const Launch& L, int64_t n, const T* m, const T* hd, const T* E,
-                          int64_t ld, const double* mbar, const uint8_t* mag, const DevParams& P,
-                          int mode, double coef, T* h, double* x);
+cudaError_t launch_hfield(const Launch& L, int64_t n, const DSeg& G, const T* m, const T* hd,
+                          const T* E, int64_t ld, const double* mbar, const double* hz,
+                          const uint8_t* mag, const DevParams& P, int mode, double coef, T* h,
+                          T* x);
 // GSPM Gauss-Seidel pieces (Algorithm B.1 step 2); see the driver for the stage layout.
 template <typename T>
 cudaError_t launch_gs_prep(const Launch& L, int64_t n, int64_t ld, const T* m, const T* h,
-                           double dtau, int c0, int nc, double* x);
+                           double dtau, int c0, int nc, T* x);
 template <typename T>
 cudaError_t launch_gs_stage(const Launch& L, int64_t n, int64_t ld, int stage, int printed,
-                            const T* m, const T* h, double dtau, double* x, T* ms);
+                            const T* m, const T* h, double dtau, T* x, T* ms);
 template <typename T>
-cudaError_t launch_project(const Launch& L, int64_t n, int64_t ld, const double* x,
-                           const uint8_t* mag, T* m, double* dm_out, double inv_nmag, Red red);
+cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* x,
+                           const uint8_t* mag, T* m, double* dm_out, const double* inv_nmag,
+                           Red red);  // dm_out[seg]
 
 template <typename T>
 cudaError_t launch_import(const Launch& L, int64_t n, int nc, const double* src,
@@ -129,5 +161,10 @@ cudaError_t launch_export(const Launch& L, int64_t n, int nc, const T* src, int6
                           int64_t ns, const int64_t* perm, double* dst);
 template <typename S, typename D>
 cudaError_t launch_convert(const Launch& L, int64_t len, const S* src, D* dst);
+template <typename T>
+cudaError_t launch_extrapolate(const Launch& L, int64_t len, T* u, T* u2);
+template <typename T>
+cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T* b, const T* c,
+                               double scale, float* t);
 
 }  // namespace gspm

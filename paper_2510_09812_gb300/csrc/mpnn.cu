@@ -1,0 +1,615 @@
+// Learned warm start of the mechanical CG: a three-layer message-passing network over the mesh
+// (hidden width 64) that predicts the displacement correction on top of linear extrapolation.
+//
+// Forward layers run on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation)
+// with the element-message aggregation z_i = sum_j A_ij h_j fused into the tile load: a block
+// owns 128 rows, gathers [h_i, z_i] into shared memory as BF16 and multiplies by the layer's
+// weights held in shared memory.  Training (backward and Adam) runs in FP32 on CUDA cores with
+// deterministic block partials.  The network definition (features, aggregation, loss) is the
+// one documented in include/gspm.h (gspm_mpnn_*).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "mpnn.cuh"
+
+namespace gspm {
+
+namespace {
+
+constexpr int kRows = 128;      // rows per tile (8 warps x 16)
+constexpr int kThreads = 256;
+constexpr int kXs = 2 * kHid + 8;  // padded shared row stride (bf16) of the [h, z] tile
+constexpr int kWs = 2 * kHid + 8;  // padded shared row stride of W^T ([64][128])
+
+__device__ __forceinline__ int64_t tid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t tstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// D = A (16x16, row) * B (16x8, col) + D, BF16 operands, FP32 accumulators
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One warp: rows [r0, r0+16) of X (shared, row stride xs, K columns) times W^T (shared [64][K],
+// row stride ws) -> acc[8][4] (8 n-tiles of 8 columns).  Fragment layout of mma.m16n8k16:
+// lane = 4*g + t; A regs {X[g][2t..], X[g+8][2t..], X[g][2t+8..], X[g+8][2t+8..]};
+// B regs {W^T[n=g][2t..], W^T[g][2t+8..]}; C {row g: cols 2t, 2t+1; row g+8: same}.
+template <int K>
+__device__ __forceinline__ void warp_gemm(const __nv_bfloat16* X, int xs, const __nv_bfloat16* Wt,
+                                          int ws, int r0, float (&acc)[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    const __nv_bfloat16* xr0 = X + (r0 + g) * xs + k0 + 2 * t;
+    const __nv_bfloat16* xr1 = X + (r0 + g + 8) * xs + k0 + 2 * t;
+    a[0] = *reinterpret_cast<const uint32_t*>(xr0);
+    a[1] = *reinterpret_cast<const uint32_t*>(xr1);
+    a[2] = *reinterpret_cast<const uint32_t*>(xr0 + 8);
+    a[3] = *reinterpret_cast<const uint32_t*>(xr1 + 8);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const __nv_bfloat16* wr = Wt + (8 * j + g) * ws + k0 + 2 * t;
+      uint32_t b[2];
+      b[0] = *reinterpret_cast<const uint32_t*>(wr);
+      b[1] = *reinterpret_cast<const uint32_t*>(wr + 8);
+      mma16816(acc[j], a, b);
+    }
+  }
+}
+
+// epilogue: out[row][col] = bf16(relu(acc + bias)) for the warp's 16 rows
+__device__ __forceinline__ void warp_store_relu(const float (&acc)[8][4], const float* bias,
+                                                int64_t row0, int64_t n, __nv_bfloat16* out) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = 8 * j + 2 * t;
+    const float b0 = bias[col], b1 = bias[col + 1];
+    const int64_t ra = row0 + g, rb = row0 + g + 8;
+    if (ra < n)
+      *reinterpret_cast<uint32_t*>(out + ra * kHid + col) =
+          pack2(__float2bfloat16_rn(fmaxf(acc[j][0] + b0, 0.f)),
+                __float2bfloat16_rn(fmaxf(acc[j][1] + b1, 0.f)));
+    if (rb < n)
+      *reinterpret_cast<uint32_t*>(out + rb * kHid + col) =
+          pack2(__float2bfloat16_rn(fmaxf(acc[j][2] + b0, 0.f)),
+                __float2bfloat16_rn(fmaxf(acc[j][3] + b1, 0.f)));
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// features: m (3), E0(m) Voigt / lambda_s (6), u_prev / u_s (3), (u_prev - u_prev2) / u_s (3), 1
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_features(int64_t n, const T* __restrict__ m, int64_t ld,
+                           const uint8_t* __restrict__ mag, const T* __restrict__ up,
+                           const T* __restrict__ up2, double l100, double l111,
+                           double inv_ls, double inv_us, __nv_bfloat16* __restrict__ F) {
+  for (int64_t i = tid(); i < n; i += tstride()) {
+    float f[kFeat];
+    const double m0 = m[i], m1 = m[ld + i], m2 = m[2 * ld + i];
+    f[0] = (float)m0;
+    f[1] = (float)m1;
+    f[2] = (float)m2;
+    if (mag[i]) {
+      const double a = 1.5 * l100 * inv_ls, b = 1.5 * l111 * inv_ls;
+      f[3] = (float)(a * (m0 * m0 - 1.0 / 3.0));
+      f[4] = (float)(a * (m1 * m1 - 1.0 / 3.0));
+      f[5] = (float)(a * (m2 * m2 - 1.0 / 3.0));
+      f[6] = (float)(b * m1 * m2);
+      f[7] = (float)(b * m0 * m2);
+      f[8] = (float)(b * m0 * m1);
+    } else {
+      for (int c = 3; c < 9; ++c) f[c] = 0.f;
+    }
+    for (int c = 0; c < 3; ++c) {
+      const double p = up ? (double)up[3 * i + c] : 0.0, q = up2 ? (double)up2[3 * i + c] : 0.0;
+      f[9 + c] = (float)(p * inv_us);
+      f[12 + c] = (float)((p - q) * inv_us);
+    }
+    f[15] = 1.f;
+    uint32_t* o = reinterpret_cast<uint32_t*>(F + i * kFeat);
+    for (int c = 0; c < kFeat / 2; ++c)
+      o[c] = pack2(__float2bfloat16_rn(f[2 * c]), __float2bfloat16_rn(f[2 * c + 1]));
+  }
+}
+
+// h0 = relu(F W_in + b_in)  (K = 16)
+__global__ void __launch_bounds__(kThreads) k_input(int64_t n, const __nv_bfloat16* __restrict__ F,
+                                                    const __nv_bfloat16* __restrict__ WinT,
+                                                    const float* __restrict__ b_in,
+                                                    __nv_bfloat16* __restrict__ H) {
+  constexpr int fs = kFeat + 8;
+  __shared__ __align__(16) __nv_bfloat16 Xs[kRows * fs];
+  __shared__ __align__(16) __nv_bfloat16 Ws[kHid * fs];
+  __shared__ float bs[kHid];
+  for (int k = threadIdx.x; k < kHid * kFeat; k += blockDim.x)
+    Ws[(k / kFeat) * fs + k % kFeat] = WinT[k];
+  for (int k = threadIdx.x; k < kHid; k += blockDim.x) bs[k] = b_in[k];
+  const int warp = threadIdx.x >> 5;
+  for (int64_t base = (int64_t)blockIdx.x * kRows; base < n; base += (int64_t)gridDim.x * kRows) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < kRows * kFeat; k += blockDim.x) {
+      const int r = k / kFeat, c = k % kFeat;
+      Xs[r * fs + c] = base + r < n ? F[(base + r) * kFeat + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    float acc[8][4];
+    warp_gemm<kFeat>(Xs, fs, Ws, fs, 16 * warp, acc);
+    warp_store_relu(acc, bs, base + 16 * warp, n, H);
+  }
+}
+
+// h_out = relu([h, A h] W + b) with the aggregation gathered into the tile; z optionally saved
+__global__ void __launch_bounds__(kThreads) k_layer(int64_t n, DSell S, const float* __restrict__ Aw,
+                                                    const __nv_bfloat16* __restrict__ Hin,
+                                                    const __nv_bfloat16* __restrict__ WT,
+                                                    const float* __restrict__ bias,
+                                                    __nv_bfloat16* __restrict__ Hout,
+                                                    __nv_bfloat16* __restrict__ Zout) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Ws = Xs + kRows * kXs;
+  float* bs = reinterpret_cast<float*>(Ws + kHid * kWs);
+  for (int k = threadIdx.x; k < kHid * 2 * kHid; k += blockDim.x)
+    Ws[(k / (2 * kHid)) * kWs + k % (2 * kHid)] = WT[k];
+  for (int k = threadIdx.x; k < kHid; k += blockDim.x) bs[k] = bias[k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * kRows; base < n; base += (int64_t)gridDim.x * kRows) {
+    __syncthreads();
+    // each warp fills 16 rows: lane covers features 2*lane, 2*lane+1
+    for (int rr = 0; rr < 16; ++rr) {
+      const int r = 16 * warp + rr;
+      const int64_t i = base + r;
+      float z0 = 0.f, z1 = 0.f;
+      uint32_t hi = 0;
+      if (i < n) {
+        hi = *reinterpret_cast<const uint32_t*>(Hin + i * kHid + 2 * lane);
+        const int64_t s = i >> 5, li = i & 31;
+        const int64_t sb = S.sptr[s];
+        const int len = S.slen[s];
+        for (int k = 0; k < len; ++k) {
+          const int64_t e = sb + (int64_t)k * 32 + li;
+          const int64_t j = S.col[e];
+          const float a = Aw[e];
+          const uint32_t hj = *reinterpret_cast<const uint32_t*>(Hin + j * kHid + 2 * lane);
+          z0 += a * __bfloat162float(__ushort_as_bfloat16((unsigned short)(hj & 0xffffu)));
+          z1 += a * __bfloat162float(__ushort_as_bfloat16((unsigned short)(hj >> 16)));
+        }
+      }
+      const uint32_t zp = pack2(__float2bfloat16_rn(z0), __float2bfloat16_rn(z1));
+      *reinterpret_cast<uint32_t*>(Xs + r * kXs + 2 * lane) = hi;
+      *reinterpret_cast<uint32_t*>(Xs + r * kXs + kHid + 2 * lane) = zp;
+      if (Zout && i < n) *reinterpret_cast<uint32_t*>(Zout + i * kHid + 2 * lane) = zp;
+    }
+    __syncthreads();
+    float acc[8][4];
+    warp_gemm<2 * kHid>(Xs, kXs, Ws, kWs, 16 * warp, acc);
+    warp_store_relu(acc, bs, base + 16 * warp, n, Hout);
+  }
+}
+
+// y = h3 W_out + b_out; mode 0: Y = y (float [n][3]); mode 1: x0 = 2 u_prev - u_prev2 + u_s y
+template <typename T>
+__global__ void k_output(int64_t n, const __nv_bfloat16* __restrict__ H,
+                         const float* __restrict__ Wout, const float* __restrict__ bout, int mode,
+                         float* __restrict__ Y, const T* __restrict__ up,
+                         const T* __restrict__ up2, double us, T* __restrict__ x0) {
+  __shared__ float w[kHid * 3 + 3];
+  for (int k = threadIdx.x; k < kHid * 3; k += blockDim.x) w[k] = Wout[k];
+  if (threadIdx.x < 3) w[kHid * 3 + threadIdx.x] = bout[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = tid(); i < n; i += tstride()) {
+    float y0 = w[kHid * 3], y1 = w[kHid * 3 + 1], y2 = w[kHid * 3 + 2];
+    const uint32_t* hp = reinterpret_cast<const uint32_t*>(H + i * kHid);
+    for (int c = 0; c < kHid / 2; ++c) {
+      const uint32_t v = hp[c];
+      const float a = __bfloat162float(__ushort_as_bfloat16((unsigned short)(v & 0xffffu)));
+      const float b = __bfloat162float(__ushort_as_bfloat16((unsigned short)(v >> 16)));
+      y0 += a * w[3 * (2 * c)] + b * w[3 * (2 * c + 1)];
+      y1 += a * w[3 * (2 * c) + 1] + b * w[3 * (2 * c + 1) + 1];
+      y2 += a * w[3 * (2 * c) + 2] + b * w[3 * (2 * c + 1) + 2];
+    }
+    if (mode == 0) {
+      Y[3 * i] = y0;
+      Y[3 * i + 1] = y1;
+      Y[3 * i + 2] = y2;
+    } else {
+      const float y[3] = {y0, y1, y2};
+      for (int c = 0; c < 3; ++c) {
+        const double p = up ? (double)up[3 * i + c] : 0.0, q = up2 ? (double)up2[3 * i + c] : 0.0;
+        x0[3 * i + c] = (T)(2.0 * p - q + us * (double)y[c]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// training (FP32)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float bf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// dY = 2 (Y - T) / (3n); dH3 = dY W_out^T; block partials of dW_out (h3^T dY), db_out, loss
+__global__ void __launch_bounds__(kThreads) k_out_bwd(int64_t n, const float* __restrict__ Y,
+                                                      const float* __restrict__ T,
+                                                      const __nv_bfloat16* __restrict__ H,
+                                                      const float* __restrict__ Wout,
+                                                      float* __restrict__ dH,
+                                                      float* __restrict__ part) {
+  // part per block: [kHid*3 dW_out][3 db_out][1 loss]
+  __shared__ float acc[kHid * 3 + 4];
+  __shared__ float w[kHid * 3];
+  for (int k = threadIdx.x; k < kHid * 3 + 4; k += blockDim.x) acc[k] = 0.f;
+  for (int k = threadIdx.x; k < kHid * 3; k += blockDim.x) w[k] = Wout[k];
+  __syncthreads();
+  const float scale = 2.f / (3.f * (float)n);
+  // one warp per row: lanes own features 2*lane, 2*lane+1
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float pw[2][3] = {{0, 0, 0}, {0, 0, 0}}, pb[3] = {0, 0, 0}, pl = 0.f;
+  const int64_t nwarps = tstride() >> 5;
+  for (int64_t i = tid() >> 5; i < n; i += nwarps) {
+    float dy[3];
+    for (int c = 0; c < 3; ++c) {
+      const float d = Y[3 * i + c] - T[3 * i + c];
+      dy[c] = scale * d;
+      if (lane == 0) {
+        pb[c] += dy[c];
+        pl += d * d;
+      }
+    }
+    const float h0 = bf(H + i * kHid + 2 * lane), h1 = bf(H + i * kHid + 2 * lane + 1);
+    for (int c = 0; c < 3; ++c) {
+      pw[0][c] += h0 * dy[c];
+      pw[1][c] += h1 * dy[c];
+    }
+    dH[i * kHid + 2 * lane] = dy[0] * w[3 * (2 * lane)] + dy[1] * w[3 * (2 * lane) + 1] +
+                             dy[2] * w[3 * (2 * lane) + 2];
+    dH[i * kHid + 2 * lane + 1] = dy[0] * w[3 * (2 * lane + 1)] +
+                                 dy[1] * w[3 * (2 * lane + 1) + 1] +
+                                 dy[2] * w[3 * (2 * lane + 1) + 2];
+  }
+  // fixed-order block accumulation: warps in turn
+  for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
+    if (warp == wv) {
+      for (int c = 0; c < 3; ++c) {
+        acc[3 * (2 * lane) + c] += pw[0][c];
+        acc[3 * (2 * lane + 1) + c] += pw[1][c];
+      }
+      if (lane == 0) {
+        for (int c = 0; c < 3; ++c) acc[kHid * 3 + c] += pb[c];
+        acc[kHid * 3 + 3] += pl;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < kHid * 3 + 4; k += blockDim.x)
+    part[(int64_t)blockIdx.x * (kHid * 3 + 4) + k] = acc[k];
+}
+
+// For one layer: dA = dH (.) [h > 0]; block partials of dW (X^T dA, X = [h_prev, z]) and db;
+// dXself = dA W^T[:, :64] -> dHprev, dZ = dA W^T[:, 64:]
+__global__ void __launch_bounds__(kThreads) k_layer_bwd(int64_t n, const float* __restrict__ dH,
+                                                        const __nv_bfloat16* __restrict__ Hcur,
+                                                        const __nv_bfloat16* __restrict__ Hprev,
+                                                        const __nv_bfloat16* __restrict__ Z,
+                                                        const float* __restrict__ W,  // [128][64]
+                                                        float* __restrict__ dHprev,
+                                                        float* __restrict__ dZ,
+                                                        float* __restrict__ part) {
+  // part per block: [128*64 dW][64 db]
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* WsT = reinterpret_cast<float*>(smem);          // [64][128]: WsT[c][f] = W[f][c]
+  float* Xr = WsT + 2 * kHid * kHid;                    // [8 warps][128]
+  float* Dr = Xr + 8 * 2 * kHid;                        // [8 warps][64]
+  for (int k = threadIdx.x; k < 2 * kHid * kHid; k += blockDim.x)
+    WsT[(k % kHid) * 2 * kHid + k / kHid] = W[k];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // each thread owns dW entries (f, c) for f in {lane + 32 q}, c in {2 warp .. } ... use a
+  // simple ownership: thread k owns 32 consecutive entries of the flattened [128][64] block
+  float pw[32];
+  for (int q = 0; q < 32; ++q) pw[q] = 0.f;
+  float pb[2] = {0.f, 0.f};
+  const int64_t nwarps = tstride() >> 5;
+  // rows are processed warp-synchronously in rounds so that every warp's row is staged before
+  // the block-wide dW accumulation of that round
+  const int64_t rounds = (n + nwarps - 1) / nwarps;
+  for (int64_t rd = 0; rd < rounds; ++rd) {
+    const int64_t i = rd * nwarps + (tid() >> 5);
+    float* xr = Xr + warp * 2 * kHid;
+    float* dr = Dr + warp * kHid;
+    if (i < n) {
+      for (int c = lane; c < kHid; c += 32) {
+        const float hc = bf(Hcur + i * kHid + c);
+        const float d = hc > 0.f ? dH[i * kHid + c] : 0.f;
+        dr[c] = d;
+        xr[c] = bf(Hprev + i * kHid + c);
+        xr[kHid + c] = bf(Z + i * kHid + c);
+      }
+    } else {
+      for (int c = lane; c < kHid; c += 32) {
+        dr[c] = 0.f;
+        xr[c] = 0.f;
+        xr[kHid + c] = 0.f;
+      }
+    }
+    __syncwarp();
+    if (i < n) {
+      // dX[f] = sum_c dA[c] W[f][c], f = lane + 32 q
+      for (int q = 0; q < 4; ++q) {
+        const int f = lane + 32 * q;
+        float s = 0.f;
+        for (int c = 0; c < kHid; ++c) s += dr[c] * WsT[c * 2 * kHid + f];
+        if (f < kHid)
+          dHprev[i * kHid + f] = s;
+        else
+          dZ[i * kHid + f - kHid] = s;
+      }
+      pb[0] += dr[lane];
+      pb[1] += dr[lane + 32];
+    }
+    __syncthreads();
+    // dW[f][c] += sum over the round's rows of X[f] dA[c]; thread t owns entries 32t .. 32t+31
+    for (int w8 = 0; w8 < 8; ++w8) {
+      const float* xw = Xr + w8 * 2 * kHid;
+      const float* dw = Dr + w8 * kHid;
+      for (int q = 0; q < 32; ++q) {
+        const int k = 32 * threadIdx.x + q;
+        pw[q] += xw[k / kHid] * dw[k % kHid];
+      }
+    }
+    __syncthreads();
+  }
+  float* pp = part + (int64_t)blockIdx.x * (2 * kHid * kHid + kHid);
+  for (int q = 0; q < 32; ++q) pp[32 * threadIdx.x + q] = pw[q];
+  // db: lanes of each warp hold two columns; sum warps in fixed order through shared memory
+  __syncthreads();
+  for (int wv = 0; wv < 8; ++wv) {
+    if (warp == wv) {
+      if (wv == 0) {
+        Dr[lane] = pb[0];
+        Dr[lane + 32] = pb[1];
+      } else {
+        Dr[lane] += pb[0];
+        Dr[lane + 32] += pb[1];
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < kHid; c += blockDim.x) pp[2 * kHid * kHid + c] = Dr[c];
+}
+
+// dH_prev += A^T dZ (SELL with transposed weights), 64-wide, warp per row
+__global__ void k_agg_t(int64_t n, DSell S, const float* __restrict__ At, const float* __restrict__ dZ,
+                        float* __restrict__ dH) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = tstride() >> 5;
+  for (int64_t i = tid() >> 5; i < n; i += nwarps) {
+    const int64_t s = i >> 5, li = i & 31;
+    const int64_t sb = S.sptr[s];
+    const int len = S.slen[s];
+    float a0 = 0.f, a1 = 0.f;
+    for (int k = 0; k < len; ++k) {
+      const int64_t e = sb + (int64_t)k * 32 + li;
+      const int64_t j = S.col[e];
+      const float a = At[e];
+      a0 += a * dZ[j * kHid + lane];
+      a1 += a * dZ[j * kHid + lane + 32];
+    }
+    dH[i * kHid + lane] += a0;
+    dH[i * kHid + lane + 32] += a1;
+  }
+}
+
+// input layer backward: block partials of dW_in (F^T dA0) and db_in
+__global__ void __launch_bounds__(kThreads) k_in_bwd(int64_t n, const float* __restrict__ dH,
+                                                     const __nv_bfloat16* __restrict__ H0,
+                                                     const __nv_bfloat16* __restrict__ F,
+                                                     float* __restrict__ part) {
+  // part per block: [16*64 dW_in][64 db_in]; thread t owns dW entries 4t .. 4t+3
+  float pw[4] = {0, 0, 0, 0};
+  float pb = 0.f;
+  const int t = threadIdx.x;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * t + q;
+      const int f = k / kHid, c = k % kHid;
+      const float d = bf(H0 + i * kHid + c) > 0.f ? dH[i * kHid + c] : 0.f;
+      pw[q] += bf(F + i * kFeat + f) * d;
+    }
+    if (t < kHid) pb += bf(H0 + i * kHid + t) > 0.f ? dH[i * kHid + t] : 0.f;
+  }
+  float* pp = part + (int64_t)blockIdx.x * (kFeat * kHid + kHid);
+  for (int q = 0; q < 4; ++q) pp[4 * t + q] = pw[q];
+  if (t < kHid) pp[kFeat * kHid + t] = pb;
+}
+
+// grad[k] = sum over blocks of part[b][k] (fixed block order)
+__global__ void k_reduce_parts(int nblocks, int count, int stride, const float* __restrict__ part,
+                               float* __restrict__ grad) {
+  for (int64_t k = tid(); k < count; k += tstride()) {
+    float s = 0.f;
+    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * stride + k];
+    grad[k] = s;
+  }
+}
+
+__global__ void k_adam(int64_t count, float* __restrict__ w, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  for (int64_t k = tid(); k < count; k += tstride()) {
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    w[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+  }
+}
+
+// bf16 transposed weight copies for the tensor-core layers: dst[o][i] = src[i][o]
+__global__ void k_transpose_bf16(int rows, int cols, const float* __restrict__ src,
+                                 __nv_bfloat16* __restrict__ dst) {
+  for (int64_t k = tid(); k < (int64_t)rows * cols; k += tstride()) {
+    const int i = (int)(k / cols), o = (int)(k % cols);
+    dst[(int64_t)o * rows + i] = __float2bfloat16_rn(src[k]);
+  }
+}
+
+__global__ void k_loss_sum(int nblocks, const float* __restrict__ part, int width,
+                           float* __restrict__ out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float s = 0.f;
+    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * width + width - 1];
+    *out = s;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------------------------
+static inline int grid_rows(const Launch& L, int64_t n) {
+  int64_t b = (n + kRows - 1) / kRows;
+  const int64_t cap = (int64_t)L.max_blocks;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+size_t mpnn_layer_smem() {
+  return (size_t)kRows * kXs * 2 + (size_t)kHid * kWs * 2 + kHid * 4;
+}
+size_t mpnn_layer_bwd_smem() { return (size_t)(2 * kHid * kHid + 8 * 2 * kHid + 8 * kHid) * 4; }
+
+template <typename T>
+cudaError_t mpnn_features(const Launch& L, int64_t n, const T* m, int64_t ld, const uint8_t* mag,
+                          const T* up, const T* up2, double l100, double l111,
+                          double ls, double us, __nv_bfloat16* F) {
+  (*L.counter) += 1;
+  k_features<T><<<L.blocks_for(n), kBlock, 0, L.stream>>>(n, m, ld, mag, up, up2, l100, l111,
+                                                          1.0 / ls, 1.0 / us, F);
+  return cudaGetLastError();
+}
+template cudaError_t mpnn_features<double>(const Launch&, int64_t, const double*, int64_t,
+                                           const uint8_t*, const double*, const double*, double,
+                                           double, double, double, __nv_bfloat16*);
+template cudaError_t mpnn_features<float>(const Launch&, int64_t, const float*, int64_t,
+                                          const uint8_t*, const float*, const float*, double,
+                                          double, double, double, __nv_bfloat16*);
+
+cudaError_t mpnn_forward(const Launch& L, int64_t n, const DSell& S, const MpnnDev& W,
+                         const __nv_bfloat16* F, __nv_bfloat16* const H[4],
+                         __nv_bfloat16* const Z[3]) {
+  const int g = grid_rows(L, n);
+  (*L.counter) += 1;
+  k_input<<<g, kThreads, 0, L.stream>>>(n, F, W.WinT, W.b_in, H[0]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t sm = mpnn_layer_smem();
+  for (int l = 0; l < kLayers; ++l) {
+    (*L.counter) += 1;
+    k_layer<<<g, kThreads, sm, L.stream>>>(n, S, W.A, H[l], W.WT[l], W.b[l], H[l + 1],
+                                           Z ? Z[l] : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t mpnn_output(const Launch& L, int64_t n, const MpnnDev& W, const __nv_bfloat16* H3,
+                        int mode, float* Y, const T* up, const T* up2, double us, T* x0) {
+  (*L.counter) += 1;
+  k_output<T><<<L.blocks_for(n), kBlock, 0, L.stream>>>(n, H3, W.Wout, W.bout, mode, Y, up, up2,
+                                                      us, x0);
+  return cudaGetLastError();
+}
+
+template cudaError_t mpnn_output<double>(const Launch&, int64_t, const MpnnDev&,
+                                         const __nv_bfloat16*, int, float*, const double*,
+                                         const double*, double, double*);
+template cudaError_t mpnn_output<float>(const Launch&, int64_t, const MpnnDev&,
+                                        const __nv_bfloat16*, int, float*, const float*,
+                                        const float*, double, float*);
+
+cudaError_t mpnn_backward(const Launch& L, int64_t n, const DSell& S, const MpnnDev& W,
+                          const __nv_bfloat16* F, __nv_bfloat16* const H[4],
+                          __nv_bfloat16* const Z[3], const float* Y, const float* T, float* dHa,
+                          float* dHb, float* dZ, float* part, float* grad, float* loss) {
+  // grad layout = parameter layout: W_in, b_in, {W_l, b_l} x 3, W_out, b_out
+  const int gb = grid_rows(L, n);
+  cudaError_t e;
+  const int wout = kHid * 3 + 4;
+  (*L.counter) += 2;
+  k_out_bwd<<<gb, kThreads, 0, L.stream>>>(n, Y, T, H[kLayers], W.Wout, dHa, part);
+  float* g_out = grad + kOffWout;
+  k_reduce_parts<<<1, 256, 0, L.stream>>>(gb, wout - 1, wout, part, g_out);  // W_out, b_out
+  (*L.counter) += 1;
+  k_loss_sum<<<1, 32, 0, L.stream>>>(gb, part, wout, loss);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  float* dH = dHa;
+  float* dHp = dHb;
+  const int wl = 2 * kHid * kHid + kHid;
+  const size_t sm = mpnn_layer_bwd_smem();
+  for (int l = kLayers - 1; l >= 0; --l) {
+    (*L.counter) += 3;
+    k_layer_bwd<<<gb, kThreads, sm, L.stream>>>(n, dH, H[l + 1], H[l], Z[l], W.Wf[l], dHp, dZ,
+                                                part);
+    k_reduce_parts<<<(wl + 255) / 256, 256, 0, L.stream>>>(gb, wl, wl, part, grad + kOffW[l]);
+    k_agg_t<<<L.blocks_for(n * 32), kBlock, 0, L.stream>>>(n, S, W.At, dZ, dHp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    float* t = dH;
+    dH = dHp;
+    dHp = t;
+  }
+  const int wi = kFeat * kHid + kHid;
+  (*L.counter) += 2;
+  k_in_bwd<<<gb, kThreads, 0, L.stream>>>(n, dH, H[0], F, part);
+  k_reduce_parts<<<(wi + 255) / 256, 256, 0, L.stream>>>(gb, wi, wi, part, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t mpnn_adam(const Launch& L, float* w, const float* g, float* m, float* v, float lr,
+                      int t) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  (*L.counter) += 1;
+  k_adam<<<L.blocks_for(kParams), kBlock, 0, L.stream>>>(kParams, w, g, m, v, lr, b1, b2, 1e-8f,
+                                                         c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t mpnn_refresh_bf16(const Launch& L, __nv_bfloat16* WinT, __nv_bfloat16* const WT[3],
+                              const float* params) {
+  (*L.counter) += 1 + kLayers;
+  k_transpose_bf16<<<8, 256, 0, L.stream>>>(kFeat, kHid, params + kOffWin, WinT);
+  for (int l = 0; l < kLayers; ++l)
+    k_transpose_bf16<<<32, 256, 0, L.stream>>>(2 * kHid, kHid, params + kOffW[l], WT[l]);
+  return cudaGetLastError();
+}
+
+cudaError_t mpnn_setup_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_layer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)mpnn_layer_smem());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mpnn_layer_bwd_smem());
+}
+
+}  // namespace gspm

@@ -18,14 +18,22 @@ OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE = range(8)
 HOST, DEVICE = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
 ORDER_NONE, ORDER_RCM = 0, 1
-FLAG_HOST_ONLY, FLAG_ROW2_PRINTED = 1, 2
+FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE = 1, 2, 4
 EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC, \
     EXPORT_LUMPED_MASS = range(6)
-FIELD_M, FIELD_U, FIELD_DISP, FIELD_HD, FIELD_STRAIN, FIELD_H = range(6)
+FIELD_M, FIELD_U, FIELD_DISP, FIELD_HD, FIELD_STRAIN, FIELD_H, FIELD_DISP_PREV = range(7)
+X0_PREV, X0_ZERO, X0_EXTRAPOLATE, X0_LEARNED = range(4)
+MPNN_PARAMS = 26051
+MPNN_KEYS = [("W_in", (16, 64)), ("b_in", (64,)), ("W1", (128, 64)), ("b1", (64,)),
+             ("W2", (128, 64)), ("b2", (64,)), ("W3", (128, 64)), ("b3", (64,)),
+             ("W_out", (64, 3)), ("b_out", (3,))]
 OP_K_MS, OP_A_EPS, OP_A_AEPS, OP_M, OP_K_MECH, OP_DIV, OP_GRAD = range(7)
 KCLASS_NAMES = ["spmv_mech", "spmv_gs", "spmv_ms", "cg_vec", "cg_init", "rowops", "pointwise"]
 KCLASS = {name: k for k, name in enumerate(KCLASS_NAMES)}
-FIELD_NCOMP = {FIELD_M: 3, FIELD_U: 1, FIELD_DISP: 3, FIELD_HD: 3, FIELD_STRAIN: 6, FIELD_H: 3}
+FIELD_NCOMP = {FIELD_M: 3, FIELD_U: 1, FIELD_DISP: 3, FIELD_HD: 3, FIELD_STRAIN: 6, FIELD_H: 3,
+               FIELD_DISP_PREV: 3}
+KCLASS_NAMES.append("learned")
+KCLASS["learned"] = 7
 
 _dp = C.POINTER(C.c_double)
 
@@ -56,7 +64,10 @@ class MeshInfo(C.Structure):
                 ("n_magnetic_nodes", C.c_int64), ("n_magnetic_tets", C.c_int64),
                 ("nnz", C.c_int64), ("sell_entries", C.c_int64), ("volume", C.c_double),
                 ("volume_magnetic", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("n_segments", C.c_int), ("item_slices", C.c_int),
+                ("spmv_schedule_block", C.c_int),
+                ("spmv_schedule_scalar", C.c_int), ("spmv_ms_block", C.c_double * 3),
+                ("spmv_ms_scalar", C.c_double * 3)]
 
 
 class StepStats(C.Structure):
@@ -82,7 +93,7 @@ def _load():
         "gspm_mesh_export": (C.c_int, [vp, C.c_int, vp, C.c_int64]),
         "gspm_set_field": (C.c_int, [vp, C.c_int, vp, C.c_int]),
         "gspm_get_field": (C.c_int, [vp, C.c_int, vp, C.c_int]),
-        "gspm_step": (C.c_int, [vp, C.c_int, _dp, C.POINTER(StepStats)]),
+        "gspm_step": (C.c_int, [vp, C.c_int, _dp, vp]),
         "gspm_solve_elastic": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, vp, C.c_double,
                                          C.POINTER(C.c_int), _dp]),
         "gspm_volume_avg": (C.c_int, [vp, vp, C.c_int, C.c_int, _dp]),
@@ -91,6 +102,19 @@ def _load():
         "gspm_profile_enable": (C.c_int, [vp, C.c_uint]),
         "gspm_profile_read": (C.c_int, [vp, C.c_int, _dp, C.POINTER(C.c_int64)]),
         "gspm_volume_avg_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, vp, vp]),
+        "gspm_set_x0_mode": (C.c_int, [vp, C.c_int]),
+        "gspm_batch_load": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
+                                      C.POINTER(Options), C.POINTER(vp)]),
+        "gspm_batch_segment": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64)]),
+        "gspm_batch_step": (C.c_int, [vp, C.c_int, _dp, vp]),
+        "gspm_mpnn_set_params": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int64]),
+        "gspm_mpnn_get_params": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int64]),
+        "gspm_mpnn_predict": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.c_int]),
+        "gspm_mpnn_dataset_reserve": (C.c_int, [vp, C.c_int]),
+        "gspm_mpnn_dataset_add": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.POINTER(C.c_int)]),
+        "gspm_mpnn_loss_grad": (C.c_int, [vp, C.c_int, _dp, C.POINTER(C.c_float)]),
+        "gspm_mpnn_train": (C.c_int, [vp, C.c_int, C.c_double, C.c_uint64, _dp, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -157,34 +181,47 @@ class Context:
 
     def __init__(self, mesh, material: dict, dt: float, alpha: float, precision: str = "f64",
                  ordering: str = "none", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
-                 max_iter=20000, row2_printed=False, host_only=False, stream=0, wrap_tol=0.0):
-        coords = np.ascontiguousarray(mesh.coords, dtype=np.float64)
-        tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
-        emag = np.ascontiguousarray(mesh.elem_magnetic, dtype=np.uint8)
-        d = MeshDesc()
-        d.n_nodes = coords.shape[0]
-        d.coords = coords.ctypes.data_as(_dp)
-        d.n_tets = tets.shape[0]
-        d.tets = tets.ctypes.data_as(C.POINTER(C.c_int32))
-        d.elem_magnetic = emag.ctypes.data_as(C.POINTER(C.c_uint8))
-        d.box_lo[:] = [float(v) for v in mesh.box_lo]
-        d.box_hi[:] = [float(v) for v in mesh.box_hi]
-        d.wrap_tol = float(wrap_tol)
+                 max_iter=20000, row2_printed=False, host_only=False, stream=0, wrap_tol=0.0,
+                 autotune=True):
+        """One mesh, or a batch when `mesh` is a list (gspm_batch_load)."""
+        meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
+        keep = []
+        descs = (MeshDesc * len(meshes))()
+        for d, me in zip(descs, meshes):
+            coords = np.ascontiguousarray(me.coords, dtype=np.float64)
+            tets = np.ascontiguousarray(me.tets, dtype=np.int32)
+            emag = np.ascontiguousarray(me.elem_magnetic, dtype=np.uint8)
+            keep += [coords, tets, emag]
+            d.n_nodes = coords.shape[0]
+            d.coords = coords.ctypes.data_as(_dp)
+            d.n_tets = tets.shape[0]
+            d.tets = tets.ctypes.data_as(C.POINTER(C.c_int32))
+            d.elem_magnetic = emag.ctypes.data_as(C.POINTER(C.c_uint8))
+            d.box_lo[:] = [float(v) for v in me.box_lo]
+            d.box_hi[:] = [float(v) for v in me.box_hi]
+            d.wrap_tol = float(wrap_tol)
         o = Options()
         o.precision = {"f64": PREC_F64, "mixed": PREC_MIXED}[precision]
         o.ordering = {"none": ORDER_NONE, "rcm": ORDER_RCM}[ordering]
         o.dt, o.alpha = float(dt), float(alpha)
         o.rtol_gs, o.rtol_ms, o.rtol_mech = float(rtol_gs), float(rtol_ms), float(rtol_mech)
         o.max_iter = int(max_iter)
-        o.flags = (FLAG_ROW2_PRINTED if row2_printed else 0) | (FLAG_HOST_ONLY if host_only else 0)
+        o.flags = ((FLAG_ROW2_PRINTED if row2_printed else 0) | (FLAG_HOST_ONLY if host_only else 0)
+                   | (0 if autotune else FLAG_NO_AUTOTUNE))
         o.stream = C.c_void_p(int(stream))
         h = C.c_void_p()
-        _check(lib.gspm_mesh_load(C.byref(d), C.byref(material_struct(material)), C.byref(o),
-                                  C.byref(h)), "gspm_mesh_load")
+        mat = material_struct(material)
+        if isinstance(mesh, (list, tuple)):
+            _check(lib.gspm_batch_load(descs, len(meshes), C.byref(mat), C.byref(o), C.byref(h)),
+                   "gspm_batch_load")
+        else:
+            _check(lib.gspm_mesh_load(descs, C.byref(mat), C.byref(o), C.byref(h)),
+                   "gspm_mesh_load")
         self._h = h
         self.precision = precision
         inf = self.info()
         self.n = inf["n_unique"]
+        self.n_segments = inf["n_segments"]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -206,7 +243,10 @@ class Context:
     def info(self) -> dict:
         i = MeshInfo()
         _check(lib.gspm_mesh_info_get(self._h, C.byref(i)), "gspm_mesh_info_get")
-        return {k: getattr(i, k) for k, _ in MeshInfo._fields_}
+        out = {k: getattr(i, k) for k, _ in MeshInfo._fields_}
+        out["spmv_ms_block"] = list(i.spmv_ms_block)
+        out["spmv_ms_scalar"] = list(i.spmv_ms_scalar)
+        return out
 
     def export(self, what: int) -> np.ndarray:
         inf = self.info()
@@ -235,8 +275,9 @@ class Context:
 
     def step(self, n_steps: int, H, stats: bool = True):
         Hc = (C.c_double * 3)(*[float(v) for v in H])
-        s = StepStats()
-        code = _check(lib.gspm_step(self._h, int(n_steps), Hc, C.byref(s) if stats else None),
+        S = (StepStats * self.n_segments)()
+        s = S[0]
+        code = _check(lib.gspm_step(self._h, int(n_steps), Hc, S if stats else None),
                       "gspm_step", allow=(ENOCONV,))
         if not stats:
             return code
@@ -245,6 +286,32 @@ class Context:
         out["m_bar"] = list(s.m_bar)
         out["status"] = code
         return out
+
+    def batch_step(self, n_steps: int, H_all, stats: bool = True):
+        """gspm_batch_step: one applied field per mesh, H_all [n_meshes][3] (A/m)."""
+        H = np.ascontiguousarray(H_all, dtype=np.float64).reshape(-1)
+        if H.size != 3 * self.n_segments:
+            raise ValueError("need one field per mesh")
+        S = (StepStats * self.n_segments)()
+        code = _check(lib.gspm_batch_step(self._h, int(n_steps), H.ctypes.data_as(_dp),
+                                          S if stats else None), "gspm_batch_step",
+                      allow=(ENOCONV,))
+        if not stats:
+            return code
+        out = []
+        for s in S:
+            d = {k: getattr(s, k) for k, _ in StepStats._fields_}
+            d["it_gs_last"] = list(s.it_gs_last)
+            d["m_bar"] = list(s.m_bar)
+            out.append(d)
+        return out
+
+    def segment(self, seg: int):
+        """(first node, node count) of mesh `seg` in the batch numbering."""
+        off, cnt = C.c_int64(), C.c_int64()
+        _check(lib.gspm_batch_segment(self._h, int(seg), C.byref(off), C.byref(cnt)),
+               "gspm_batch_segment")
+        return off.value, cnt.value
 
     def solve_elastic(self, m, u_out=None, x0_mode=1, x0=None, rtol=0.0):
         pm, where, k1 = _ptr(m, 3 * self.n)
@@ -262,9 +329,10 @@ class Context:
         return u_out, it.value, rel.value, code
 
     def volume_avg(self, field) -> np.ndarray:
+        """Per-mesh volume averages: [ncomp] for one mesh, [n_meshes][ncomp] for a batch."""
         nc = int(np.prod(field.shape[1:])) if len(field.shape) > 1 else 1
         p, where, keep = _ptr(field, self.n * nc)
-        out = np.empty(nc)
+        out = np.empty((self.n_segments, nc)) if self.n_segments > 1 else np.empty(nc)
         _check(lib.gspm_volume_avg(self._h, p, where, nc, out.ctypes.data_as(_dp)),
                "gspm_volume_avg")
         return out
@@ -287,6 +355,64 @@ class Context:
     def launch_count(self) -> int:
         return int(lib.gspm_launch_count(self._h))
 
+    # ---- learned warm start
+    def set_x0_mode(self, mode: int):
+        _check(lib.gspm_set_x0_mode(self._h, int(mode)), "gspm_set_x0_mode")
+
+    def mpnn_set_params(self, params):
+        flat = flatten_params(params) if isinstance(params, dict) else \
+            np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib.gspm_mpnn_set_params(self._h, flat.ctypes.data_as(C.POINTER(C.c_float)),
+                                        flat.size), "gspm_mpnn_set_params")
+
+    def mpnn_get_params(self) -> np.ndarray:
+        out = np.empty(MPNN_PARAMS, dtype=np.float32)
+        _check(lib.gspm_mpnn_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)),
+                                        out.size), "gspm_mpnn_get_params")
+        return out
+
+    def mpnn_predict(self, m, u_prev=None, u_prev2=None, what=0, out=None):
+        pm, where, k1 = _ptr(m, 3 * self.n)
+        pu = _ptr(u_prev, 3 * self.n)[0] if u_prev is not None else None
+        pu2 = _ptr(u_prev2, 3 * self.n)[0] if u_prev2 is not None else None
+        if out is None:
+            if where == DEVICE:
+                import torch
+                out = torch.empty((self.n, 3), dtype=torch.float64, device=m.device)
+            else:
+                out = np.empty((self.n, 3))
+        po, _, k2 = _ptr(out, 3 * self.n)
+        _check(lib.gspm_mpnn_predict(self._h, pm, pu, pu2, po, int(what), where),
+               "gspm_mpnn_predict")
+        return out
+
+    def mpnn_dataset_reserve(self, capacity: int):
+        _check(lib.gspm_mpnn_dataset_reserve(self._h, int(capacity)), "gspm_mpnn_dataset_reserve")
+
+    def mpnn_dataset_add(self, m, u_prev, u_prev2, u_star) -> int:
+        pm, where, k1 = _ptr(m, 3 * self.n)
+        pu = _ptr(u_prev, 3 * self.n)[0] if u_prev is not None else None
+        pu2 = _ptr(u_prev2, 3 * self.n)[0] if u_prev2 is not None else None
+        ps, _, k2 = _ptr(u_star, 3 * self.n)
+        idx = C.c_int()
+        _check(lib.gspm_mpnn_dataset_add(self._h, pm, pu, pu2, ps, where, C.byref(idx)),
+               "gspm_mpnn_dataset_add")
+        return idx.value
+
+    def mpnn_loss_grad(self, pair: int):
+        loss = C.c_double()
+        g = np.empty(MPNN_PARAMS, dtype=np.float32)
+        _check(lib.gspm_mpnn_loss_grad(self._h, int(pair), C.byref(loss),
+                                       g.ctypes.data_as(C.POINTER(C.c_float))),
+               "gspm_mpnn_loss_grad")
+        return loss.value, g
+
+    def mpnn_train(self, iterations: int, lr: float = 1e-3, seed: int = 0):
+        l0, l1 = C.c_double(), C.c_double()
+        _check(lib.gspm_mpnn_train(self._h, int(iterations), float(lr), int(seed), C.byref(l0),
+                                   C.byref(l1)), "gspm_mpnn_train")
+        return l0.value, l1.value
+
     def profile_enable(self, classes=()):
         mask = 0
         for c in classes:
@@ -299,6 +425,21 @@ class Context:
         k = KCLASS[cls] if isinstance(cls, str) else int(cls)
         _check(lib.gspm_profile_read(self._h, k, C.byref(ms), C.byref(cnt)), "gspm_profile_read")
         return ms.value, cnt.value
+
+
+def flatten_params(p: dict) -> np.ndarray:
+    """Oracle-style parameter dict -> flat float32 array in the library's layout."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1)
+                           for k, _ in MPNN_KEYS]).astype(np.float32)
+
+
+def unflatten_params(flat) -> dict:
+    out, o = {}, 0
+    for k, shp in MPNN_KEYS:
+        size = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + size], dtype=np.float64).reshape(shp)
+        o += size
+    return out
 
 
 def volume_avg_noalloc(field, weights, out, stream=0):
