@@ -164,30 +164,64 @@ def cpu_oracle_sample(wall_budget=25.0, steps=None, warmup=1):
 
 def run_batch(gspm, torch, args, barrier):
     """64 independent meshes of log-uniform size 2k-200k nodes, each with its own inclusion and
-    applied field, stepped together (mixed precision) by gspm_batch_step; compared with the
-    same meshes stepped one after another in their own contexts (first 16 meshes)."""
+    applied field, stepped together (mixed precision) by gspm_batch_step with graph replay (and
+    with direct launches from the same state for comparison); compared with the same meshes
+    stepped one after another in their own contexts (first 16 meshes)."""
     from paper_2510_09812_gb300 import synth
-    members = [synth.batch_member(i) for i in range(args.batch_meshes)]
+    from paper_2510_09812_gb300.shard import batch_shard, max_over_ranks, sum_over_ranks
+    ws, rank, _ = _dist()
+    every = [synth.batch_member(i) for i in range(args.batch_meshes)]
+    # N GPUs: each rank steps its own share of the meshes (no data-path collective)
+    mine = batch_shard([c["mesh"].n_unique for c in every], rank, ws)
+    members = [every[i] for i in mine]
     meshes = [c["mesh"] for c in members]
     H = np.array([c["H"] for c in members])
     t0 = time.perf_counter()
     ctx = gspm.Context(meshes, members[0]["material"], members[0]["dt"], members[0]["alpha"],
                        precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
     t_load = time.perf_counter() - t0
-    ctx.set_field(gspm.FIELD_M, np.concatenate([c["m0"] for c in members]))
+    m_all = np.concatenate([c["m0"] for c in members])
+    ctx.set_field(gspm.FIELD_M, m_all)
     info = ctx.info()
     ctx.batch_step(2, H, stats=False)
+    n = info["n_unique"]
+    snap = {f: torch.empty((n, gspm.FIELD_NCOMP[f]) if gspm.FIELD_NCOMP[f] > 1 else (n,),
+                           dtype=torch.float64, device="cuda")
+            for f in (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP)}
+    for f, t in snap.items():
+        ctx.get_field(f, t)
     kb = max(1, min(args.steps, 4))
-    l0 = ctx.launch_count()
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    st = ctx.batch_step(kb, H)
-    ev1.record()
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = ctx.launch_count() - l0
+
+    def timed_batch(graph):
+        # the graph is captured by an untimed step; every pass starts from the same state
+        ctx.set_graph(graph)
+        ctx.batch_step(1, H, stats=False)
+        for f, t in snap.items():
+            ctx.set_field(f, t)
+        l0 = ctx.launch_count()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = ctx.batch_step(kb, H)
+        ev1.record()
+        barrier()
+        return ev0.elapsed_time(ev1), ctx.launch_count() - l0, st
+
+    ms_direct, _, st_direct = timed_batch(False)
+    ms, launches, st = timed_batch(True)
+    same = all(a["it_mech"] == b["it_mech"] for a, b in zip(st, st_direct))
     ctx.close()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ms_direct = max_over_ranks(ms_direct, dev)
+    ms = max_over_ranks(ms, dev)
+    nodes_all = sum_over_ranks(info["n_unique"], dev)
+    nmag_all = sum_over_ranks(info["n_magnetic_nodes"], dev)
+    if ws > 1:
+        return {"meshes": len(every), "meshes_per_rank": len(members), "nodes": int(nodes_all),
+                "steps": kb, "ms_per_batch_step": ms / kb,
+                "batch_steps_per_s": kb / (ms / 1000.0),
+                "node_updates_per_s": nmag_all * kb / (ms / 1000.0), "graph_replay": True,
+                "ms_per_batch_step_direct": ms_direct / kb, "scaling": "weak"}
     # the same first 16 meshes, one context each, stepped one after another
     k16 = min(16, len(members))
     seq_ctx = []
@@ -215,14 +249,42 @@ def run_batch(gspm, torch, args, barrier):
     for x in seq_ctx:
         x.close()
     bctx.close()
-    return {"meshes": len(members), "nodes": info["n_unique"],
+    return {"meshes": len(members), "nodes": int(nodes_all),
             "min_nodes": min(m.n_unique for m in meshes), "max_nodes": max(m.n_unique for m in meshes),
             "steps": kb, "ms_per_batch_step": ms / kb, "batch_steps_per_s": kb / (ms / 1000.0),
-            "node_updates_per_s": info["n_magnetic_nodes"] * kb / (ms / 1000.0),
+            "node_updates_per_s": nmag_all * kb / (ms / 1000.0),
+            "graph_replay": True, "ms_per_batch_step_direct": ms_direct / kb,
+            "graph_and_direct_same_iterations": same,
             "gpu_launches_per_batch_step": launches / kb, "load_s": round(t_load, 1),
             "item_slices": info["item_slices"],
             "first16_batched_vs_sequential_ms": [round(1000 * t_bat, 1), round(1000 * t_seq, 1)],
             "mech_it_per_mesh_last_step": [s_["it_mech_last"] for s_ in st]}
+
+
+def run_small(gspm, torch, barrier, steps=200):
+    """The 1024-node Fe box (16x16x4 cubes): kernels of a few microseconds, so the host's
+    launches and synchronisations dominate; direct launches against graph replay, same state."""
+    from paper_2510_09812_gb300 import synth
+    cfg = synth.fe_box_17x17x5()
+    out = {"workload": cfg["name"], "steps": steps}
+    for graph in (False, True):
+        ctx = gspm.Context(cfg["mesh"], cfg["material"], cfg["dt"], cfg["alpha"],
+                           precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
+                           graph=graph)
+        ctx.set_field(gspm.FIELD_M, cfg["m0"])
+        ctx.step(3, cfg["H"], stats=False)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = ctx.step(steps, cfg["H"])
+        ev1.record()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        key = "graph" if graph else "direct"
+        out[key] = {"steps_per_s": steps / (ms / 1000.0), "ms_per_step": ms / steps,
+                    "cg_iterations_per_step": (st["it_ms"] + st["it_mech"] + st["it_gs"]) / steps}
+        ctx.close()
+    return out
 
 
 def _dist():
@@ -278,14 +340,17 @@ def run_ours(args):
         weights = np.load(WEIGHTS)
     x0_names = {"prev": gspm.X0_PREV, "zero": gspm.X0_ZERO, "extrapolate": gspm.X0_EXTRAPOLATE,
                 "learned": gspm.X0_LEARNED}
-    x0 = args.x0 if args.x0 != "auto" else ("learned" if weights is not None else "extrapolate")
+    # default: the previous solution, the best measured guess for the singular-form CG (the
+    # extrapolation 2u_n - u_{n-1} needs more iterations there)
+    x0 = args.x0 if args.x0 != "auto" else ("learned" if weights is not None else "prev")
     if x0 == "learned" and weights is None:
         raise SystemExit(f"--x0 learned needs trained weights at {WEIGHTS}")
 
-    def make(prec, mode="prev"):
+    def make(prec, mode="prev", pinned=False):
         t0 = time.perf_counter()
         ctx = gspm.Context(mesh, cfg["material"], cfg["dt"], cfg["alpha"], precision=prec,
-                           ordering=args.ordering, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
+                           ordering=args.ordering, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
+                           pinned_cg=pinned)
         ctx.set_field(gspm.FIELD_M, cfg["m0"])
         if weights is not None:
             ctx.mpnn_set_params(weights)
@@ -313,7 +378,7 @@ def run_ours(args):
         return ms, st_tot, launches, prof, clk.summary()
 
     precision = args.precision
-    ctx, t_load = make(precision, x0)
+    ctx, t_load = make(precision, x0, pinned=args.pinned_cg)
     info = ctx.info()
     n = info["n_unique"]
     for _ in range(args.warmup):
@@ -322,7 +387,7 @@ def run_ours(args):
     # region, the kernel breakdown and the end-to-end pass do identical work
     snap = {f: torch.empty((n, gspm.FIELD_NCOMP[f]) if gspm.FIELD_NCOMP[f] > 1 else (n,),
                            dtype=torch.float64, device="cuda")
-            for f in (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP)}
+            for f in (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP, gspm.FIELD_DISP_PREV)}
     for f, t in snap.items():
         ctx.get_field(f, t)
 
@@ -332,12 +397,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     ms, st, launches, prof, clocks = timed_steps(ctx, args.steps)
-    t_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    from paper_2510_09812_gb300.shard import max_over_ranks
+    t_max = max_over_ranks(ms, torch.device("cuda", local))
     value = ws * args.steps / (t_max / 1000.0)
 
     # roofline of the dominant kernel: 3x3-block SELL SpMV of the mechanical CG
@@ -377,7 +438,7 @@ def run_ours(args):
     # mechanical-CG initial guesses compared over the same steps from the same state
     x0_cmp = {}
     if not args.skip_x0:
-        modes = ["prev", "extrapolate"] + (["learned"] if weights is not None else [])
+        modes = ["prev", "extrapolate", "zero"] + (["learned"] if weights is not None else [])
         kx = max(1, min(args.steps, 3))
         for mode in modes:
             restore()
@@ -386,17 +447,49 @@ def run_ours(args):
             x0_cmp[mode] = {"it_mech_per_step": st_x["it_mech"] / kx,
                             "ms_per_step": round(ms_x / kx, 2)}
         ctx.set_x0_mode(x0_names[x0])
+
+    # graph replay of the same steps from the same state (no per-kernel events inside a graph,
+    # so the roofline above comes from the direct pass)
+    graph = None
+    if not args.skip_graph:
+        restore()
+        ctx.set_graph(True)
+        ctx.step(1, H, stats=False)  # capture
+        restore()
+        ms_g, st_g, l_g, _, _ = timed_steps(ctx, args.steps, ())
+        graph = {"value": ws * args.steps / (ms_g / 1000.0), "unit": "steps/s",
+                 "ms_per_step": ms_g / args.steps, "gpu_launches": l_g,
+                 "same_iterations_as_direct": st_g == st}
+        ctx.set_graph(False)
     ctx.close()
+
+    small = None
+    if not args.skip_graph and ws == 1:
+        small = run_small(gspm, torch, barrier)
 
     # batched uneven meshes (64 meshes, 2k-200k nodes) in one context
     batched = None
     if not args.skip_batch:
         batched = run_batch(gspm, torch, args, barrier)
 
-    # plain FP64 GPU form on the same GPU (the comparison the metric names)
+    # the pinned systems of Sec. 2.5 in the headline precision, same steps from the same start
+    pinned_cmp = None
+    if not args.skip_plain:
+        ctxp, _ = make(precision, x0, pinned=True)
+        for _ in range(args.warmup):
+            ctxp.step(1, H)
+        kp = max(1, min(args.steps, 3))
+        ms_p, st_p, _, _, _ = timed_steps(ctxp, kp, ())
+        pinned_cmp = {"steps": kp, "ms_per_step": round(ms_p / kp, 2),
+                      "it_mech_per_step": st_p["it_mech"] / kp,
+                      "it_ms_per_step": st_p["it_ms"] / kp}
+        ctxp.close()
+
+    # plain FP64 GPU form on the same GPU (the comparison the metric names): the paper's
+    # formulation (pinned systems, FP64 throughout, previous solution as initial guess)
     plain = None
     if precision != "f64" and not args.skip_plain:
-        ctx64, t_load64 = make("f64")
+        ctx64, t_load64 = make("f64", pinned=True)
         for _ in range(args.warmup):
             ctx64.step(1, H)
         k64 = max(1, args.steps // 2)
@@ -435,7 +528,12 @@ def run_ours(args):
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_per_iter,
                      "launches_timed": n_spmv, "iterations_timed": st["it_mech"]},
         "breakdown_ms_per_step": breakdown,
+        "cg_form": "pinned (Sec. 2.5)" if args.pinned_cg else
+                   "consistent singular system, shifted to the pin",
+        "pinned_form_same_start": pinned_cmp,
         "plain_f64": plain,
+        "graph_replay": graph,
+        "small_mesh_direct_vs_graph": small,
         "batched": batched,
         "x0": x0,
         "x0_comparison": x0_cmp,
@@ -457,6 +555,9 @@ def main():
     ap.add_argument("--ordering", default="none", choices=["none", "rcm"])
     ap.add_argument("--cells", default=None, help="smaller mesh of the same recipe, e.g. 64,64,16")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-graph", action="store_true")
+    ap.add_argument("--pinned-cg", action="store_true",
+                    help="solve the pinned systems of Sec. 2.5 instead of the singular form")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-x0", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")

@@ -65,6 +65,26 @@ extern "C" {
 #define GSPM_FLAG_ROW2_PRINTED 2u     /* Algorithm B.1 second row exactly as printed (m^n_1,
                                          g^n_1) instead of the Gauss-Seidel sweep (m*_1, g*_1)  */
 #define GSPM_FLAG_NO_AUTOTUNE 4u      /* skip the SpMV schedule autotuner (schedule 0)          */
+#define GSPM_FLAG_GRAPH 8u            /* gspm_step / gspm_batch_step replay one captured CUDA
+                                         graph per step (see gspm_set_graph)                    */
+#define GSPM_FLAG_RESOLVE_AT_MSTAR 32u /* Algorithm B.1 step 3: solve the magnetostatic and
+                                         mechanical equilibria again at m* (x0 = the step-n
+                                         solutions) so that h[m*] is the whole effective field
+                                         of m*.  Default: h~_d and E held from step n.  With
+                                         the flag, the state's U and u after a step are the
+                                         solutions at m*, it_ms / it_mech count both solves of
+                                         a step and *_last report the solves at m*          */
+#define GSPM_FLAG_PINNED_CG 16u       /* solve K^ms U = b and K^mech u = b as the pinned systems of
+                                         Sec. 2.5 (node 0's rows and columns replaced by the
+                                         identity, its right-hand side zeroed).  Default: the
+                                         equivalent consistent singular systems on the periodic
+                                         mesh (b minus its mean per component, CG on the
+                                         unpinned K, then the constant that makes the pinned
+                                         node zero subtracted): the same solution in exact
+                                         arithmetic, with far fewer CG iterations, since
+                                         pinning one node of a periodic body leaves an
+                                         eigenvalue of order 1/n.  Stopping test of either form:
+                                         ||r|| < rtol ||b||, with its own r and b               */
 
 /* ---- inputs ----------------------------------------------------------------------------- */
 typedef struct gspm_mesh_desc {
@@ -89,6 +109,12 @@ typedef struct gspm_material {
   double gamma0;      /* mu0 * gyromagnetic ratio, m/(A s); <= 0 selects 2.2127615e5            */
   double mu0;         /* H/m; <= 0 selects 1.25663706212e-6                                     */
   double l_d;         /* model length scale (m) = unit of the mesh coordinates; <= 0 -> 1e-9   */
+  double R[9];        /* App. D rotated crystal: v_mesh = R v_crystal (row-major; the rows are
+                         the crystal directions of the mesh axes, e.g. <111>, <-110>, <11-2>).
+                         All zero = identity (mesh axes = cube axes).  Must be a proper rotation
+                         to 1e-12, else GSPM_EINVAL.  C, E0(m), the anisotropy and the
+                         magnetoelastic field are then evaluated as Algorithm D.1 states;
+                         H_ext, N_d, sigma_ext and all fields at the ABI are in the mesh axes  */
 } gspm_material;
 
 typedef struct gspm_options {
@@ -115,7 +141,7 @@ typedef struct gspm_mesh_info {
   double dtau;             /* gamma0 m_s dt                                                    */
   int64_t device_bytes;    /* device memory held by the context                               */
   int n_segments;          /* meshes in the context (1 unless loaded with gspm_batch_load)     */
-  int item_slices;         /* slices per work item of the reducing kernels                    */
+  int item_slices;         /* slices per work item of a reducing kernel at one block per SM   */
   int spmv_schedule_block; /* SpMV schedule the autotuner chose for the 3x3-block operator:
                               0 thread per row, 1 thread per row with 5-deep load prefetch,
                               2 two threads per row                                             */
@@ -228,9 +254,11 @@ GSPM_API int gspm_get_field(struct gspm_ctx* ctx, int field, double* data, int w
 
 /* Advance n_steps GSPM steps in place under the applied field H_ext (A/m, host array of 3).
  * One step (App. B, Algorithm B.1, with Sec. 2.1-2.4):
- *   m_bar (Sec. 2.4) -> b^ms = F^ms m (Eq. RHS_b) -> CG on pinned K^ms, x0 = previous U
+ *   m_bar (Sec. 2.4) -> b^ms = F^ms m (Eq. RHS_b) -> CG for K^ms U = b^ms with U = 0 at the
+ *   pinned node (GSPM_FLAG_PINNED_CG says how), x0 = previous U
  *   -> h~_d = -grad U (F^ms / lumped mass) -> E0(m) (Table A.1), E_bar = <E0> + C^-1 sigma_ext
- *   -> b^mech = F^mech E0 -> CG on pinned K^mech, x0 = previous u -> E = E_bar + sym grad u
+ *   -> b^mech = F^mech E0 -> CG for K^mech u = b^mech, u = 0 at the pinned node, x0 = previous
+ *   u -> E = E_bar + sym grad u
  *   -> h(m^n) = h_anis + H/m_s + h_me + h~_d - N_d m_bar
  *   -> Gauss-Seidel stages with (M + eps K) g = M f (x0 = f), giving m*
  *   -> h(m*) (local terms and far field at m*, h~_d and E held) -> (M + alpha eps K) m** = M f
@@ -307,6 +335,21 @@ GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights,
  * Parameter layout (float32, GSPM_MPNN_PARAMS values): W_in [16][64], b_in [64],
  * {W_l [128][64], b_l [64]} for l = 1..3, W_out [64][3], b_out [3]; all row-major [in][out]. */
 #define GSPM_MPNN_PARAMS 26051
+
+/* Graph replay of the time step (on != 0) or direct launches (0, the default unless the context
+ * was loaded with GSPM_FLAG_GRAPH).  The paper has no counterpart: it is how the step is issued,
+ * not what it computes; results are bitwise those of direct launches.  In graph mode the first
+ * gspm_step / gspm_batch_step (and the first after a change of initial-guess mode) captures one
+ * step into a CUDA graph on private streams; each CG loop is a conditional WHILE node whose
+ * body (SpMV with p.q, update with r.r, p-update) repeats until the device-side count of
+ * unconverged meshes reaches zero, with max_iter + 2 iterations as a hard limit.  A call of n
+ * steps is then n graph launches on the context's stream and one synchronisation at the end,
+ * with no host round trip inside a step.  The graph holds the context's buffers and stream
+ * ordering only, so it stays valid across gspm_set_field calls.  While kernel-class profiling is
+ * enabled (gspm_profile_enable) steps run directly.  Capture does not allocate device memory
+ * beyond a few counters made at the first capture.  Errors: GSPM_ESTATE for host-only contexts,
+ * GSPM_ECUDA if capture or instantiation fails (the step is then not run). */
+GSPM_API int gspm_set_graph(struct gspm_ctx* ctx, int on);
 
 /* Select the mechanical CG's initial guess for gspm_step (GSPM_X0_*); GSPM_X0_LEARNED needs
  * parameters (GSPM_ESTATE otherwise). */

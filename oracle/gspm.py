@@ -28,7 +28,15 @@ import numpy as np
 
 from . import fem
 from .material import (Reduced, compliance_apply, contract, h_anisotropy, h_magnetoelastic,
-                       spontaneous_strain)
+                       spontaneous_strain, tensor_to_voigt, voigt_to_tensor)
+
+
+def voigt_to_tensor_field(v):
+    """[..., 6] Voigt (tensor shear) -> [..., 3, 3]."""
+    v = np.asarray(v, dtype=np.float64)
+    return np.stack([np.stack([v[..., 0], v[..., 5], v[..., 4]], -1),
+                     np.stack([v[..., 5], v[..., 1], v[..., 3]], -1),
+                     np.stack([v[..., 4], v[..., 3], v[..., 2]], -1)], -2)
 from .mesh import WrappedMesh
 from .solvers import cg
 
@@ -38,12 +46,13 @@ class System:
 
     def __init__(self, wm: WrappedMesh, material: dict, dt: float, alpha: float,
                  rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7, max_iter=20000,
-                 row2_printed=False):
+                 row2_printed=False, resolve_at_mstar=False):
         self.wm = wm
         self.red = red = Reduced(material, dt, alpha)
         self.rtol = dict(gs=rtol_gs, ms=rtol_ms, mech=rtol_mech)
         self.max_iter = max_iter
         self.row2_printed = row2_printed
+        self.resolve_at_mstar = resolve_at_mstar
         n = wm.n
         # Omega_c operators (Eqs. LHS, RHS_F), node 0 pinned (Sec. 2.5)
         self.K_ms_raw = fem.stiffness(wm)
@@ -65,7 +74,7 @@ class System:
         self.A_eps = (M_m + red.eps * K_m)[idx][:, idx].tocsr()
         self.A_aeps = (M_m + red.alpha * red.eps * K_m)[idx][:, idx].tocsr()
         self.E_ext = compliance_apply(material["C11"], material["C12"], material["C44"],
-                                      red.sigma_ext)
+                                      red.sigma_ext, red.D)
         self.n = n
 
     # ---------------------------------------------------------------- pieces of the step
@@ -89,7 +98,15 @@ class System:
         return -fem.nodal_gradient(self.F, self.ML, U)
 
     def e0_nodal(self, m):
-        E0 = spontaneous_strain(m, self.red.l100, self.red.l111)
+        """Table A.1 at the nodes; rotated crystal (Algorithm D.1 step 1):
+        E0_111 = M E0_100(m_100) with m_100 = R^-1 m_111."""
+        red = self.red
+        if red.rotated:
+            m100 = m @ red.R            # rows: R^T m
+            E0 = voigt_to_tensor_field(tensor_to_voigt(
+                spontaneous_strain(m100, red.l100, red.l111)) @ red.M.T)
+        else:
+            E0 = spontaneous_strain(m, red.l100, red.l111)
         E0[~self.mag] = 0.0
         return E0
 
@@ -117,8 +134,15 @@ class System:
         """h(m) = h_anis + H_ext / m_s + h_me + h~_d - N_d m_bar (App. B), zero where there is
         no magnetisation."""
         red = self.red
-        h = (h_anisotropy(m, red.kappa) + np.asarray(H, float)[None] / red.Ms
-             + h_magnetoelastic(m, sigma, red) + hd_local - (red.Nd @ m_bar)[None])
+        if red.rotated:
+            # Algorithm D.1 step 4: the crystal terms at m_100 = R^-1 m with the stress in the
+            # crystal axes (sigma_100 = M^-1 sigma_111), then h_111 = R h_100
+            m100 = m @ red.R
+            s100 = voigt_to_tensor_field(np.linalg.solve(red.M, tensor_to_voigt(sigma).T).T)
+            h_cr = (h_anisotropy(m100, red.kappa) + h_magnetoelastic(m100, s100, red)) @ red.R.T
+        else:
+            h_cr = h_anisotropy(m, red.kappa) + h_magnetoelastic(m, sigma, red)
+        h = (h_cr + np.asarray(H, float)[None] / red.Ms + hd_local - (red.Nd @ m_bar)[None])
         h[~self.mag] = 0.0
         return h
 
@@ -175,9 +199,18 @@ class System:
         ms3 = m3 + (gs1 * ms2 - gs2 * ms1)
         m_star = np.stack([ms1, ms2, ms3], axis=1)
         m_star[~self.mag] = 0.0
-        # Step 3: damped solve with h re-evaluated at m*
+        # Step 3: damped solve with h re-evaluated at m*.  Default: local terms and far field at
+        # m*, h~_d and E held from step n.  resolve_at_mstar: the magnetostatic and mechanical
+        # equilibria are solved again at m* (x0 = the step-n solutions), so h[m*] is the whole
+        # effective field of m*; U and u returned are then the solutions at m*.
         mbar_star = self.volume_average(m_star)
-        sigma_star = contract(red.C, E - self.e0_nodal(m_star))
+        if self.resolve_at_mstar:
+            U, _, _ = self.solve_ms(m_star, U)
+            hd = self.demag_local(U)
+            el_star = self.solve_elastic(m_star, u)
+            u, E, sigma_star = el_star["u"], el_star["E"], el_star["sigma"]
+        else:
+            sigma_star = contract(red.C, E - self.e0_nodal(m_star))
         h_star = self.h_field(m_star, mbar_star, hd, sigma_star, H)
         f = m_star + red.alpha * red.dtau * h_star
         m_ss = np.zeros_like(m)
@@ -207,7 +240,7 @@ class System:
         m = np.asarray(m, float)
         e_ex = mat["A"] / red.l_d ** 2 * sum(m[:, c] @ (self.K_m @ m[:, c]) for c in range(3)) / V
         ML_m = np.asarray(self.M_m_full.sum(axis=1)).ravel()
-        m2 = m ** 2
+        m2 = (m @ red.R) ** 2 if red.rotated else m ** 2   # cube-axis components
         e_an = mat["K1"] * (ML_m @ (m2[:, 0] * m2[:, 1] + m2[:, 1] * m2[:, 2]
                                     + m2[:, 2] * m2[:, 0])) / V
         el_E0 = self.e0_nodal(m)

@@ -26,7 +26,17 @@ class Reduced:
         self.dtau = self.gamma0 * self.Ms * dt
         self.alpha = alpha
         self.eps = self.A_star * self.dtau                          # (1 - eps Lap), Algorithm B.1
-        self.C = cubic_stiffness(mat["C11"], mat["C12"], mat["C44"])
+        # App. D: crystal axes rotated against the mesh axes by R (v_mesh = R v_crystal);
+        # absent or identity = the mesh axes are the cube axes
+        R = np.asarray(mat.get("R", np.eye(3)), dtype=np.float64).reshape(3, 3)
+        self.R = R
+        self.rotated = not np.array_equal(R, np.eye(3))
+        self.M = bond_matrix(R)
+        self.D100 = voigt_stiffness(mat["C11"], mat["C12"], mat["C44"])
+        # stiffness in the mesh axes: C_111 = M C_100 M^T (Algorithm D.1, first line)
+        self.D = self.M @ self.D100 @ self.M.T if self.rotated else self.D100
+        self.C = (stiffness_from_voigt(self.D) if self.rotated
+                  else cubic_stiffness(mat["C11"], mat["C12"], mat["C44"]))
         self.Nd = np.asarray(mat["Nd"], dtype=np.float64).reshape(3, 3)
         self.sigma_ext = voigt_to_tensor(np.asarray(mat.get("sigma_ext", [0.0] * 6), float))
         self.l100 = mat["lambda100"]
@@ -46,6 +56,58 @@ def cubic_stiffness(C11, C12, C44) -> np.ndarray:
                 C[i, j, i, j] = C44
                 C[i, j, j, i] = C44
     return C
+
+
+def rotation_111() -> np.ndarray:
+    """App. D: mesh axes along <111>, <-110>, <11-2> of the crystal (rows of R)."""
+    return np.array([[1 / np.sqrt(3), 1 / np.sqrt(3), 1 / np.sqrt(3)],
+                     [-1 / np.sqrt(2), 1 / np.sqrt(2), 0.0],
+                     [-1 / np.sqrt(6), -1 / np.sqrt(6), 2 / np.sqrt(6)]])
+
+
+# Voigt index pairs in the order (11, 22, 33, 23, 13, 12)
+_VP = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def bond_matrix(R: np.ndarray) -> np.ndarray:
+    """App. D's 6 x 6 matrix M of a rotation R: E_111 = M E_100 for strain vectors with tensor
+    shear components (and for stress vectors), C_111 = M C_100 M^T for the Voigt stiffness of
+    engineering strain.  Entry (I, J), I = (i, j), J = (k, l): R_ik R_jl for k = l, and
+    R_ik R_jl + R_il R_jk for k != l (the symmetric pair counted once)."""
+    M = np.zeros((6, 6))
+    for I, (i, j) in enumerate(_VP):
+        for J, (k, l) in enumerate(_VP):
+            M[I, J] = R[i, k] * R[j, l] + (R[i, l] * R[j, k] if k != l else 0.0)
+    return M
+
+
+def voigt_stiffness(C11, C12, C44) -> np.ndarray:
+    """Cubic stiffness as the 6 x 6 matrix of sigma_v = D eps_v with engineering shear
+    eps_v = (E11, E22, E33, 2E23, 2E13, 2E12)."""
+    D = np.zeros((6, 6))
+    D[:3, :3] = C12
+    np.fill_diagonal(D[:3, :3], C11)
+    D[3, 3] = D[4, 4] = D[5, 5] = C44
+    return D
+
+
+def stiffness_from_voigt(D: np.ndarray) -> np.ndarray:
+    """C_ijkl = D[v(ij), v(kl)] for the engineering-shear Voigt matrix D (minor symmetric)."""
+    v = np.zeros((3, 3), dtype=int)
+    for I, (i, j) in enumerate(_VP):
+        v[i, j] = v[j, i] = I
+    C = np.zeros((3, 3, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    C[i, j, k, l] = D[v[i, j], v[k, l]]
+    return C
+
+
+def tensor_to_voigt(E: np.ndarray) -> np.ndarray:
+    """Symmetric [..., 3, 3] -> [..., 6] in the order (11, 22, 33, 23, 13, 12), tensor shear."""
+    return np.stack([E[..., i, j] for i, j in _VP], axis=-1)
 
 
 def voigt_to_tensor(v) -> np.ndarray:
@@ -122,13 +184,13 @@ def ellipsoid_demag_factors(a: float, b: float, c: float) -> np.ndarray:
                      p * carlson_rd(a * a, b * b, c * c)])
 
 
-def compliance_apply(C11: float, C12: float, C44: float, sigma: np.ndarray) -> np.ndarray:
-    """E = C^-1 sigma for the cubic stiffness: solve the Voigt system with engineering shear
-    (sigma_v = D eps_v, eps_v = (E11, E22, E33, 2E23, 2E13, 2E12)) and return the tensor E."""
-    D = np.zeros((6, 6))
-    D[:3, :3] = C12
-    np.fill_diagonal(D[:3, :3], C11)
-    D[3, 3] = D[4, 4] = D[5, 5] = C44
+def compliance_apply(C11: float, C12: float, C44: float, sigma: np.ndarray,
+                     D: np.ndarray | None = None) -> np.ndarray:
+    """E = C^-1 sigma: solve the Voigt system with engineering shear (sigma_v = D eps_v,
+    eps_v = (E11, E22, E33, 2E23, 2E13, 2E12)) and return the tensor E.  D defaults to the cubic
+    stiffness in its cube axes."""
+    if D is None:
+        D = voigt_stiffness(C11, C12, C44)
     s = np.asarray(sigma, dtype=np.float64)
     sv = np.array([s[0, 0], s[1, 1], s[2, 2], s[1, 2], s[0, 2], s[0, 1]])
     ev = np.linalg.solve(D, sv)

@@ -93,6 +93,7 @@ class EngineBase {
   virtual int profile_enable(unsigned mask) = 0;
   virtual int profile_read(int cls, double* ms, int64_t* launches) = 0;
   virtual int set_x0_mode(int mode) = 0;
+  virtual int set_graph(int on) = 0;
   virtual int mpnn_params(float* out, const float* in, int64_t count) = 0;
   virtual int mpnn_predict(const double* m, const double* up, const double* up2, double* out,
                            int what, int where) = 0;
@@ -125,6 +126,10 @@ class Engine final : public EngineBase {
     L_.sms = std::max(1, sms);
   }
   ~Engine() override {
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (cap_stream_) cudaStreamDestroy(cap_stream_);
+    if (body_stream_) cudaStreamDestroy(body_stream_);
+    if (host_graph_) cudaFreeHost(host_graph_);
     if (host_state_) cudaFreeHost(host_state_);
     if (host_active_) cudaFreeHost(host_active_);
     if (host_scal_) cudaFreeHost(host_scal_);
@@ -188,6 +193,16 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&tin_, 3 * ld));
     ST(mem_.alloc(&tout_, 3 * ld));
     ST(mem_.alloc(&cg_, (int64_t)kSolveSlots * nseg_));
+    ST(mem_.alloc(&proj_, 6 * (int64_t)nseg_));
+    ST(mem_.alloc(&pinsave_, 3 * (int64_t)nseg_));
+    ST(mem_.alloc(&wmean_, n));
+    {
+      std::vector<double> wm(n, 0.0);
+      for (int sg = 0; sg < nseg_; ++sg)
+        for (int64_t i = 0; i < hb_.seg_nrow[sg]; ++i)
+          wm[hb_.seg_row0[sg] + i] = 1.0 / (double)hb_.seg_nrow[sg];
+      CK(cudaMemcpy(wmean_, wm.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
     ST(mem_.alloc(&nactive_, kSolveSlots));
     ST(mem_.alloc(&scal_, (int64_t)kScalPerSeg * nseg_ + 8));
     CK(cudaMemset(scal_, 0, ((int64_t)kScalPerSeg * nseg_ + 8) * sizeof(double)));
@@ -220,6 +235,9 @@ class Engine final : public EngineBase {
     for (int k = 0; k < kSolveSlots; ++k) pred_[k] = 8;
     CK(cudaDeviceSynchronize());
     if (!(opt_.flags & GSPM_FLAG_NO_AUTOTUNE)) ST(autotune());
+    graph_on_ = (opt_.flags & GSPM_FLAG_GRAPH) != 0;
+    pinned_ = (opt_.flags & GSPM_FLAG_PINNED_CG) ? 1 : 0;
+    resolve_ = (opt_.flags & GSPM_FLAG_RESOLVE_AT_MSTAR) != 0;
     return GSPM_OK;
   }
 
@@ -295,81 +313,52 @@ class Engine final : public EngineBase {
   }
 
   // ---------------------------------------------------------------- one GSPM step
+  // Per-step solve records of the direct (non-graph) path: per segment, for K^ms, K^mech and
+  // each Gauss-Seidel right-hand side in sweep order.
+  struct StepInfo {
+    std::vector<SolveInfo> ims, imech, ig[8];
+    std::vector<SolveInfo> ims2, imech2;  // the solves at m* (GSPM_FLAG_RESOLVE_AT_MSTAR)
+    int ngs = 0;
+  };
+
   // H: applied field (A/m), three values per segment when per_segment, else one for all.
   // st: per-segment statistics (nseg entries) or NULL.
   int step(int n_steps, const double* H, bool per_segment, gspm_step_stats* st) override {
     DevParams D = dev_params();
-    std::vector<gspm_step_stats> acc(nseg_);
-    for (auto& a : acc) memset(&a, 0, sizeof(a));
-    const int64_t n = n_, ld = ld_;
     const int printed = (opt_.flags & GSPM_FLAG_ROW2_PRINTED) ? 1 : 0;
     for (int s = 0; s < nseg_; ++s)
       for (int a = 0; a < 3; ++a)
         host_scal_[3 * s + a] = (per_segment ? H[3 * s + a] : H[a]) / P_.Ms;
     CK(cudaMemcpyAsync(hz(), host_scal_, 3 * nseg_ * sizeof(double), cudaMemcpyHostToDevice,
                        L_.stream));
-    std::vector<SolveInfo> ims, imech, ig[8];
+    if (graph_on_ && prof_mask_ == 0) return step_graph(n_steps, D, printed, st);
+    std::vector<gspm_step_stats> acc(nseg_);
+    for (auto& a : acc) memset(&a, 0, sizeof(a));
+    StepInfo si;
     for (int stp = 0; stp < n_steps; ++stp) {
-      // a1 volume average of m (Sec. 2.4)
-      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, m_, ld, 1, nullptr, w_, mbar(), nullptr, red_));
-      // a2 b^ms / m_s = F^ms m (Eq. RHS_b), a3 CG on pinned K^ms, x0 = previous U
-      TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, SG_, F_, m_, ld, b_));
-      ST(solve_general(kSlotMs, Kms_, 1, b_, U_, opt_.rtol_ms, &ims));
-      // a4 local demagnetising field h~_d = -grad U
-      TK(GSPM_KCLASS_ROWOPS, launch_fgrad<T>(L_, A_, F_, U_, invML_, hd_, ld));
-      // a5 E0(m), sigma0 = C E0, E_bar = <E0> + C^-1 sigma_ext
-      TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, m_, ld, mag_, D, E0_, sig0_));
-      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
-      // a6 b^mech = F^mech E0, a7 CG on pinned K^mech, x0 per the initial-guess mode
-      TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_));
-      ST(mech_initial_guess(m_, x0_mode_));
-      ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, opt_.rtol_mech, &imech));
-      // a8 strain E = E_bar + sym grad u
-      TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
-      // a9 h(m^n)
-      TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, m_, hd_, E_, ld, mbar(), hz(), mag_, D, 0, 0.0, h_, nullptr));
-      // a10 Gauss-Seidel stages (Algorithm B.1 steps 1-2), (M + eps K) g = M f, x0 = f
-      int ngs = 0;
-      if (!printed) {
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_prep<T>(L_, n, ld, m_, h_, P_.dtau, 1, 2, x_));
-        ST(solve_gs(kSlotGs0, Aeps_, 0, 2, &ig[0]));
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 1, 0, m_, h_, P_.dtau, x_, ms_));
-        ST(solve_gs(kSlotGs1, Aeps_, 2, 1, &ig[2]));
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 2, 0, m_, h_, P_.dtau, x_, ms_));
-        ST(solve_gs(kSlotGs2, Aeps_, 0, 1, &ig[3]));
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 3, 0, m_, h_, P_.dtau, x_, ms_));
-        ngs = 4;
-      } else {
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_prep<T>(L_, n, ld, m_, h_, P_.dtau, 0, 3, x_));
-        ST(solve_gs(kSlotGs0, Aeps_, 0, 3, &ig[0]));
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 1, 1, m_, h_, P_.dtau, x_, ms_));
-        ST(solve_gs(kSlotGs1, Aeps_, 0, 2, &ig[3]));
-        TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 3, 1, m_, h_, P_.dtau, x_, ms_));
-        ngs = 5;
-      }
-      // a11 h(m*) with h~_d and E held, far field from m_bar*; f = m* + alpha dtau h*
-      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, ms_, ld, 1, nullptr, w_, mbar_s(), nullptr, red_));
-      TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, ms_, hd_, E_, ld, mbar_s(), hz(), mag_, D, 1, P_.alpha * P_.dtau, nullptr, x_));
-      // a12 (M + alpha eps K) m** = M f, three right-hand sides
-      ST(solve_gs(kSlotGsD, Aaeps_, 0, 3, &ig[ngs]));
-      ngs += 3;
-      // a13 projection and <|dm|>
-      TK(GSPM_KCLASS_POINTWISE, launch_project<T>(L_, SG_, ld, x_, mag_, m_, dmv(), inv_nmag(), red_));
+      ST(step_once(D, printed, &si));
       for (int sg = 0; sg < nseg_; ++sg) {
         gspm_step_stats& a = acc[sg];
         a.steps += 1;
-        a.it_ms += ims[sg].iters;
-        a.it_mech += imech[sg].iters;
-        a.it_ms_last = ims[sg].iters;
-        a.it_mech_last = imech[sg].iters;
-        a.res_ms_last = ims[sg].relres;
-        a.res_mech_last = imech[sg].relres;
-        a.noconv += ims[sg].noconv + imech[sg].noconv;
+        a.it_ms += si.ims[sg].iters;
+        a.it_mech += si.imech[sg].iters;
+        a.noconv += si.ims[sg].noconv + si.imech[sg].noconv;
+        const SolveInfo& lms = resolve_ ? si.ims2[sg] : si.ims[sg];
+        const SolveInfo& lme = resolve_ ? si.imech2[sg] : si.imech[sg];
+        if (resolve_) {
+          a.it_ms += lms.iters;
+          a.it_mech += lme.iters;
+          a.noconv += lms.noconv + lme.noconv;
+        }
+        a.it_ms_last = lms.iters;
+        a.it_mech_last = lme.iters;
+        a.res_ms_last = lms.relres;
+        a.res_mech_last = lme.relres;
         for (int k = 0; k < 8; ++k) {
-          a.it_gs_last[k] = k < ngs ? ig[k][sg].iters : 0;
-          if (k < ngs) {
-            a.it_gs += ig[k][sg].iters;
-            a.noconv += ig[k][sg].noconv;
+          a.it_gs_last[k] = k < si.ngs ? si.ig[k][sg].iters : 0;
+          if (k < si.ngs) {
+            a.it_gs += si.ig[k][sg].iters;
+            a.noconv += si.ig[k][sg].noconv;
           }
         }
       }
@@ -385,6 +374,246 @@ class Engine final : public EngineBase {
         acc[sg].dm_last = host_scal_[12 * nseg_ + sg];
         st[sg] = acc[sg];
       }
+    }
+    CK(cudaGetLastError());
+    return noconv ? GSPM_ENOCONV : GSPM_OK;
+  }
+
+  // The kernel sequence of one GSPM step (Algorithm B.1 with the field and equilibrium solves
+  // of Sec. 2).  While a graph is being captured the CG loops become WHILE nodes and `si` is
+  // left alone.
+  int step_once(const DevParams& D, int printed, StepInfo* si) {
+    const int64_t n = n_, ld = ld_;
+    // a1 volume average of m (Sec. 2.4)
+    TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, m_, ld, 1, nullptr, w_, mbar(), nullptr, red_));
+    // a2 b^ms / m_s = F^ms m (Eq. RHS_b), a3 CG on pinned K^ms, x0 = previous U
+    TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, SG_, F_, m_, ld, b_, pinned_));
+    ST(solve_general(kSlotMs, Kms_, 1, b_, U_, opt_.rtol_ms, &si->ims));
+    // a4 local demagnetising field h~_d = -grad U
+    TK(GSPM_KCLASS_ROWOPS, launch_fgrad<T>(L_, A_, F_, U_, invML_, hd_, ld));
+    // a5 E0(m), sigma0 = C E0, E_bar = <E0> + C^-1 sigma_ext
+    TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, m_, ld, mag_, D, E0_, sig0_));
+    TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
+    // a6 b^mech = F^mech E0, a7 CG on pinned K^mech, x0 per the initial-guess mode
+    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
+    ST(mech_initial_guess(m_, x0_mode_));
+    ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, opt_.rtol_mech, &si->imech));
+    // a8 strain E = E_bar + sym grad u
+    TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
+    // a9 h(m^n)
+    TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, m_, hd_, E_, ld, mbar(), hz(), mag_, D, 0, 0.0, h_, nullptr));
+    // a10 Gauss-Seidel stages (Algorithm B.1 steps 1-2), (M + eps K) g = M f, x0 = f
+    std::vector<SolveInfo>* ig = si->ig;
+    int ngs = 0;
+    if (!printed) {
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_prep<T>(L_, n, ld, m_, h_, P_.dtau, 1, 2, x_));
+      ST(solve_gs(kSlotGs0, Aeps_, 0, 2, &ig[0]));
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 1, 0, m_, h_, P_.dtau, x_, ms_));
+      ST(solve_gs(kSlotGs1, Aeps_, 2, 1, &ig[2]));
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 2, 0, m_, h_, P_.dtau, x_, ms_));
+      ST(solve_gs(kSlotGs2, Aeps_, 0, 1, &ig[3]));
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 3, 0, m_, h_, P_.dtau, x_, ms_));
+      ngs = 4;
+    } else {
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_prep<T>(L_, n, ld, m_, h_, P_.dtau, 0, 3, x_));
+      ST(solve_gs(kSlotGs0, Aeps_, 0, 3, &ig[0]));
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 1, 1, m_, h_, P_.dtau, x_, ms_));
+      ST(solve_gs(kSlotGs1, Aeps_, 0, 2, &ig[3]));
+      TK(GSPM_KCLASS_POINTWISE, launch_gs_stage<T>(L_, n, ld, 3, 1, m_, h_, P_.dtau, x_, ms_));
+      ngs = 5;
+    }
+    // a11 h(m*) with h~_d and E held, far field from m_bar*; f = m* + alpha dtau h*
+    TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, ms_, ld, 1, nullptr, w_, mbar_s(), nullptr, red_));
+    if (resolve_) {
+      // variant: the magnetostatic and mechanical equilibria solved again at m* (x0 = the
+      // step-n solutions), so h[m*] is the whole effective field of m*
+      TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, SG_, F_, ms_, ld, b_, pinned_));
+      ST(solve_general(kSlotMs, Kms_, 1, b_, U_, opt_.rtol_ms, &si->ims2));
+      TK(GSPM_KCLASS_ROWOPS, launch_fgrad<T>(L_, A_, F_, U_, invML_, hd_, ld));
+      TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, ms_, ld, mag_, D, E0_, sig0_));
+      TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
+      TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
+      ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, opt_.rtol_mech, &si->imech2));
+      TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
+    }
+    TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, ms_, hd_, E_, ld, mbar_s(), hz(), mag_, D, 1, P_.alpha * P_.dtau, nullptr, x_));
+    // a12 (M + alpha eps K) m** = M f, three right-hand sides
+    ST(solve_gs(kSlotGsD, Aaeps_, 0, 3, &ig[ngs]));
+    ngs += 3;
+    // a13 projection and <|dm|>
+    TK(GSPM_KCLASS_POINTWISE, launch_project<T>(L_, SG_, ld, x_, mag_, m_, dmv(), inv_nmag(), red_));
+    si->ngs = ngs;
+    return GSPM_OK;
+  }
+
+  // ---------------------------------------------------------------- CUDA-graph replay
+  // One step is captured once (per initial-guess mode) into a graph whose CG loops are WHILE
+  // nodes: the body (SpMV, update, p-update) repeats until the device-side count of active
+  // segments reaches zero, with the iteration limit max_iter + 2 as a backstop.  A call of
+  // n steps is n graph launches and one synchronisation at the end; statistics come from device
+  // accumulators and the CG status blocks.
+  int set_graph(int on) override {
+    graph_on_ = on != 0;
+    return GSPM_OK;
+  }
+
+  int graph_alloc() {
+    if (loop_cnt_) return GSPM_OK;
+    ST(mem_.alloc(&loop_cnt_, kSolveSlots));
+    ST(mem_.alloc(&loop_total_, 1));
+    ST(mem_.alloc(&gstats_, 4 * (int64_t)nseg_));
+    CK(cudaMemset(loop_cnt_, 0, kSolveSlots * sizeof(int)));
+    CK(cudaMemset(loop_total_, 0, sizeof(unsigned long long)));
+    const size_t hb = 4 * (size_t)nseg_ * sizeof(long long) + sizeof(unsigned long long) +
+                      (size_t)kSolveSlots * nseg_ * sizeof(CGState);
+    CK(cudaMallocHost(&host_graph_, hb));
+    CK(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&body_stream_, cudaStreamNonBlocking));
+    return GSPM_OK;
+  }
+
+  int build_graph(const DevParams& D, int printed) {
+    ST(graph_alloc());
+    if (gexec_) {
+      CK(cudaGraphExecDestroy(gexec_));
+      gexec_ = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    const cudaStream_t outer = L_.stream;
+    const int64_t c0 = *L_.counter;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap_stream_, g, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+    int rc = GSPM_OK;
+    if (e == cudaSuccess) {
+      L_.stream = cap_stream_;
+      capturing_ = true;
+      graph_body_ = 0;
+      StepInfo si;
+      rc = step_once(D, printed, &si);
+      capturing_ = false;
+      L_.stream = outer;
+      cudaGraph_t out = nullptr;
+      e = cudaStreamEndCapture(cap_stream_, &out);
+    }
+    const int64_t captured = *L_.counter - c0;
+    *L_.counter = c0;  // nothing has run yet
+    if (rc == GSPM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gexec_, g, 0);
+    cudaGraphDestroy(g);
+    ST(rc);
+    if (e != cudaSuccess) {
+      gexec_ = nullptr;
+      set_error("graph capture of the step failed: %s", cudaGetErrorString(e));
+      return GSPM_ECUDA;
+    }
+    graph_static_ = captured - graph_body_;
+    gexec_x0_ = x0_mode_;
+    return GSPM_OK;
+  }
+
+  // A CG loop as a WHILE node of the graph being captured on L_.stream.
+  template <class Iter>
+  int cg_graph_loop(int slot, Iter iter, int kind) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(L_.stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    const LoopCtl lc{h, nactive_ + slot, loop_cnt_ + slot, opt_.max_iter + 2, loop_total_};
+    CK(launch_loop_start(L_, lc));
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(L_.stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(L_.stream, &node, nullptr, 1,
+                                           cudaStreamSetCaptureDependencies));
+    const cudaStream_t outer = L_.stream;
+    CK(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    L_.stream = body_stream_;
+    loop_ = lc;
+    const int64_t c0 = *L_.counter;
+    const int rc = iter();
+    graph_body_ += *L_.counter - c0;
+    loop_ = LoopCtl{};
+    L_.stream = outer;
+    cudaGraph_t done = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(body_stream_, &done);
+    ST(rc);
+    CK(e);
+    CK(launch_solve_stats(L_, cg_ + (int64_t)slot * nseg_, nseg_, kind, gstats_));
+    return GSPM_OK;
+  }
+
+  static SolveInfo info_of(const CGState& c, int k) {
+    SolveInfo s;
+    for (int j = 0; j < c.nr; ++j) {
+      if (k >= 0 && j != k) continue;
+      s.iters = std::max(s.iters, c.r[j].iters);
+      const double bb = c.r[j].bb;
+      s.relres = std::max(s.relres, bb > 0 ? std::sqrt(c.r[j].rr / bb) : 0.0);
+    }
+    s.noconv = c.noconv;
+    return s;
+  }
+
+  int step_graph(int n_steps, const DevParams& D, int printed, gspm_step_stats* st) {
+    if (!gexec_ || gexec_x0_ != x0_mode_) ST(build_graph(D, printed));
+    CK(cudaMemsetAsync(gstats_, 0, 4 * (size_t)nseg_ * sizeof(long long), L_.stream));
+    for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(gexec_, L_.stream));
+    *L_.counter += graph_static_ * n_steps;
+    long long* hst = reinterpret_cast<long long*>(host_graph_);
+    unsigned long long* hloops = reinterpret_cast<unsigned long long*>(hst + 4 * nseg_);
+    CGState* hcg = reinterpret_cast<CGState*>(hloops + 1);
+    CK(cudaMemcpyAsync(hst, gstats_, 4 * (size_t)nseg_ * sizeof(long long),
+                       cudaMemcpyDeviceToHost, L_.stream));
+    CK(cudaMemcpyAsync(hloops, loop_total_, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       L_.stream));
+    CK(cudaMemcpyAsync(hcg, cg_, (size_t)kSolveSlots * nseg_ * sizeof(CGState),
+                       cudaMemcpyDeviceToHost, L_.stream));
+    CK(cudaMemcpyAsync(host_scal_, scal_, 13 * nseg_ * sizeof(double), cudaMemcpyDeviceToHost,
+                       L_.stream));
+    CK(cudaStreamSynchronize(L_.stream));
+    // loop bodies: SpMV, update and p-update per iteration
+    *L_.counter += 3 * (int64_t)(*hloops - loops_seen_);
+    loops_seen_ = *hloops;
+    // Gauss-Seidel solves in sweep order: (slot, right-hand side)
+    static const int kGsOrder[2][8][2] = {
+        {{kSlotGs0, 0}, {kSlotGs0, 1}, {kSlotGs1, 0}, {kSlotGs2, 0}, {kSlotGsD, 0},
+         {kSlotGsD, 1}, {kSlotGsD, 2}, {-1, 0}},
+        {{kSlotGs0, 0}, {kSlotGs0, 1}, {kSlotGs0, 2}, {kSlotGs1, 0}, {kSlotGs1, 1},
+         {kSlotGsD, 0}, {kSlotGsD, 1}, {kSlotGsD, 2}}};
+    int noconv = 0;
+    for (int sg = 0; sg < nseg_; ++sg) {
+      noconv += (int)hst[4 * sg + 3];
+      if (!st) continue;
+      gspm_step_stats a;
+      memset(&a, 0, sizeof(a));
+      a.steps = n_steps;
+      a.it_ms = hst[4 * sg + 0];
+      a.it_mech = hst[4 * sg + 1];
+      a.it_gs = hst[4 * sg + 2];
+      a.noconv = (int)hst[4 * sg + 3];
+      const SolveInfo ms = info_of(hcg[kSlotMs * nseg_ + sg], -1);
+      const SolveInfo me = info_of(hcg[kSlotMech * nseg_ + sg], -1);
+      a.it_ms_last = ms.iters;
+      a.it_mech_last = me.iters;
+      a.res_ms_last = ms.relres;
+      a.res_mech_last = me.relres;
+      for (int k = 0; k < 8; ++k) {
+        const int slot = kGsOrder[printed][k][0];
+        a.it_gs_last[k] =
+            slot < 0 ? 0 : info_of(hcg[slot * nseg_ + sg], kGsOrder[printed][k][1]).iters;
+      }
+      for (int c = 0; c < 3; ++c) a.m_bar[c] = host_scal_[3 * sg + c];
+      a.dm_last = host_scal_[12 * nseg_ + sg];
+      st[sg] = a;
     }
     CK(cudaGetLastError());
     return noconv ? GSPM_ENOCONV : GSPM_OK;
@@ -419,7 +648,7 @@ class Engine final : public EngineBase {
     }
     TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, ms_, ld, mag_, D, E0_, sig0_));
     TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
-    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_));
+    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
     std::vector<SolveInfo> info;
     ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, rtol > 0 ? rtol : opt_.rtol_mech, &info));
     TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
@@ -465,18 +694,22 @@ class Engine final : public EngineBase {
         const T* val = op == GSPM_OP_K_MS ? Kms_ : op == GSPM_OP_A_EPS ? Aeps_
                      : op == GSPM_OP_A_AEPS ? Aaeps_ : M_;
         ST(import_field(x, where, 1, tin_, 1, 1, nullptr));
+        if (op == GSPM_OP_K_MS) ST(pin_hide(1));
         CK(launch_spmv<T>(L_, A_, val, 1, tin_, tout_, var_scalar_));
+        if (op == GSPM_OP_K_MS) ST(pin_restore(1));
         ST(export_field(tout_, 1, 1, 1, y, where));
         break;
       }
       case GSPM_OP_K_MECH:
         ST(import_field(x, where, 3, tin_, 1, 3, nullptr));
+        ST(pin_hide(3));
         CK(launch_spmv<T>(L_, A_, Kmech_, 9, tin_, tout_, var_block_));
+        ST(pin_restore(3));
         ST(export_field(tout_, 1, 3, 3, y, where));
         break;
       case GSPM_OP_DIV:
         ST(import_field(x, where, 3, tin_, ld, 1, nullptr));
-        CK(launch_fdiv<T>(L_, A_, SG_, F_, tin_, ld, b_));
+        CK(launch_fdiv<T>(L_, A_, SG_, F_, tin_, ld, b_, 1));
         ST(export_field(b_, 1, 1, 1, y, where));
         break;
       case GSPM_OP_GRAD:
@@ -489,6 +722,26 @@ class Engine final : public EngineBase {
         return GSPM_EINVAL;
     }
     if (where == GSPM_HOST) CK(cudaStreamSynchronize(L_.stream));
+    return GSPM_OK;
+  }
+
+  // The stored K^ms and K^mech are the unpinned periodic operators.  The pinned operator of
+  // Sec. 2.5 (pinned rows and columns replaced by the identity) is y = K (x with x_pin = 0),
+  // then y_pin = x_pin: pin_hide keeps each segment's x_pin aside in tin_ and zeroes it,
+  // pin_restore writes it into tout_.
+  int pin_hide(int epr) {
+    for (int sg = 0; sg < nseg_; ++sg) {
+      T* xp = tin_ + epr * hb_.seg_pin[sg];
+      CK(cudaMemcpyAsync(pinsave_ + 3 * sg, xp, epr * sizeof(T), cudaMemcpyDeviceToDevice,
+                         L_.stream));
+      CK(cudaMemsetAsync(xp, 0, epr * sizeof(T), L_.stream));
+    }
+    return GSPM_OK;
+  }
+  int pin_restore(int epr) {
+    for (int sg = 0; sg < nseg_; ++sg)
+      CK(cudaMemcpyAsync(tout_ + epr * hb_.seg_pin[sg], pinsave_ + 3 * sg, epr * sizeof(T),
+                         cudaMemcpyDeviceToDevice, L_.stream));
     return GSPM_OK;
   }
 
@@ -723,6 +976,8 @@ class Engine final : public EngineBase {
     for (int k = 0; k < 9; ++k) D.Nd[k] = P_.Nd[k];
     D.dtau = P_.dtau;
     D.alpha = P_.alpha;
+    for (int k = 0; k < 9; ++k) D.R[k] = P_.R[k];
+    D.rotated = P_.rotated;
     return D;
   }
 
@@ -806,15 +1061,30 @@ class Engine final : public EngineBase {
     int* na = nactive_ + slot;
     const int epr = B == 9 ? 3 : 1;
     const int64_t len = epr * n_;
+    double* bmean = proj_;
+    double* xpin = proj_ + 3 * nseg_;
     CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_));
+    // x0 moved to zero at the pinned node: the pinned system (Sec. 2.5) needs it, and for the
+    // singular system it removes any large constant from x0, whose product with K would only
+    // add rounding noise to the residual
+    TK(GSPM_KCLASS_CG_INIT, launch_pin_shift<T>(L_, A_, SG_, epr, x, xpin));
+    if (!pinned_) {
+      // the consistent singular system: b minus its per-segment mean of each component
+      TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, b, 1, epr, nullptr, wmean_, bmean, nullptr, red_));
+    }
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_, pinned_ ? nullptr : bmean, pinned_));
     auto iter = [&]() -> int {
-      TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_));
+      TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_, pinned_));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, epr, 1, len, x, r_, p_, q_, st, na, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, epr, 1, len, r_, p_, st));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, epr, 1, len, r_, p_, st, loop_));
       return GSPM_OK;
     };
-    ST(cg_loop(slot, iter, info));
+    if (capturing_)
+      ST(cg_graph_loop(slot, iter, B == 9 ? 1 : 0));
+    else
+      ST(cg_loop(slot, iter, info));
+    // singular system: move the solution to the pinned one (zero at the pinned node)
+    if (!pinned_) TK(GSPM_KCLASS_CG_INIT, launch_pin_shift<T>(L_, A_, SG_, epr, x, xpin));
     TK(GSPM_KCLASS_CG_INIT, launch_cg_zero<T>(L_, SG_, epr, x, st));
     return GSPM_OK;
   }
@@ -828,11 +1098,12 @@ class Engine final : public EngineBase {
     CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
     TK(GSPM_KCLASS_CG_INIT, launch_cg_init_gs<T>(L_, A_, SG_, aval, M_, nr, ld_, x, r_, p_, st, na, opt_.rtol_gs, opt_.max_iter, red_));
     auto iter = [&]() -> int {
-      TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, SG_, aval, 1, nr, ld_, p_, q_, st, red_, var_scalar_));
+      TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, SG_, aval, 1, nr, ld_, p_, q_, st, red_, var_scalar_, 0));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, 1, nr, ld_, x, r_, p_, q_, st, na, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st, loop_));
       return GSPM_OK;
     };
+    if (capturing_) return cg_graph_loop(slot, iter, 2);
     std::vector<SolveInfo> tot;
     ST(cg_loop(slot, iter, &tot));
     for (int k = 0; k < nr; ++k) {
@@ -859,50 +1130,67 @@ class Engine final : public EngineBase {
   double* avg() const { return scal_ + 17 * nseg_; }
   double* eext() const { return scal_ + 26 * nseg_; }
 
-  // segment tables and the work items of the reducing kernels
+  // Segment tables and the work items of the reducing kernels.  List k - 1 serves kernels that
+  // keep k blocks resident per SM: about k x SMs items, each segment getting a share
+  // proportional to its slices (at least one item, at most one per slice), its slices split
+  // evenly, so every block of the single resident wave reduces one item.
   int init_segments() {
     const int S = nseg_;
-    // items of about `item_slices_` slices: enough items for ~4 per resident block slot
-    const int64_t resident = (int64_t)L_.sms * 6;
-    int64_t u = nslices_ / std::max<int64_t>(1, 4 * resident);
-    item_slices_ = (int)std::max<int64_t>(1, std::min<int64_t>(64, u));
-    std::vector<int32_t> iseg, isl0, isl1, sitem0(S), snit(S);
-    for (int sg = 0; sg < S; ++sg) {
-      sitem0[sg] = (int32_t)iseg.size();
-      const int64_t a = hb_.seg_sl0[sg], b = a + hb_.seg_nsl[sg];
-      for (int64_t x = a; x < b; x += item_slices_) {
-        iseg.push_back(sg);
-        isl0.push_back((int32_t)x);
-        isl1.push_back((int32_t)std::min<int64_t>(b, x + item_slices_));
-      }
-      snit[sg] = (int32_t)iseg.size() - sitem0[sg];
-    }
-    nitems_ = (int)iseg.size();
-    int32_t *d_sos, *d_iseg, *d_isl0, *d_isl1, *d_si0, *d_sni;
+    int32_t *d_sos, *d_si0, *d_sni;
     int64_t *d_r0, *d_nr, *d_pin;
     unsigned* d_cnt;
     ST(mem_.alloc(&d_sos, nslices_));
-    ST(mem_.alloc(&d_iseg, nitems_));
-    ST(mem_.alloc(&d_isl0, nitems_));
-    ST(mem_.alloc(&d_isl1, nitems_));
-    ST(mem_.alloc(&d_si0, S));
-    ST(mem_.alloc(&d_sni, S));
     ST(mem_.alloc(&d_r0, S));
     ST(mem_.alloc(&d_nr, S));
     ST(mem_.alloc(&d_pin, S));
     ST(mem_.alloc(&d_cnt, S));
     CK(cudaMemcpy(d_sos, hb_.seg_of_slice.data(), nslices_ * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_iseg, iseg.data(), nitems_ * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_isl0, isl0.data(), nitems_ * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_isl1, isl1.data(), nitems_ * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_si0, sitem0.data(), S * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_sni, snit.data(), S * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_r0, hb_.seg_row0.data(), S * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_nr, hb_.seg_nrow.data(), S * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_pin, hb_.seg_pin.data(), S * 8, cudaMemcpyHostToDevice));
     CK(cudaMemset(d_cnt, 0, S * sizeof(unsigned)));
-    SG_ = DSeg{S, nitems_, d_sos, d_iseg, d_isl0, d_isl1, d_si0, d_sni, d_r0, d_nr, d_pin, d_cnt};
-    ST(mem_.alloc(&red_.partial, (int64_t)nitems_ * kRedComp));
+    DSeg g{};
+    g.nseg = S;
+    g.seg_of_slice = d_sos;
+    g.seg_row0 = d_r0;
+    g.seg_nrow = d_nr;
+    g.seg_pin = d_pin;
+    g.counter = d_cnt;
+    int max_items = 0;
+    for (int k = 1; k <= kItemLists; ++k) {
+      const double target = (double)k * L_.sms;
+      std::vector<int32_t> iseg, isl0, isl1, sitem0(S), snit(S);
+      for (int sg = 0; sg < S; ++sg) {
+        const int64_t a = hb_.seg_sl0[sg], nsl = hb_.seg_nsl[sg];
+        int64_t ni = std::llround(target * (double)nsl / (double)nslices_);
+        ni = std::max<int64_t>(1, std::min<int64_t>(nsl, ni));
+        sitem0[sg] = (int32_t)iseg.size();
+        for (int64_t i = 0; i < ni; ++i) {
+          iseg.push_back(sg);
+          isl0.push_back((int32_t)(a + i * nsl / ni));
+          isl1.push_back((int32_t)(a + (i + 1) * nsl / ni));
+        }
+        snit[sg] = (int32_t)ni;
+      }
+      const int ni = (int)iseg.size();
+      int32_t *d_iseg, *d_isl0, *d_isl1;
+      ST(mem_.alloc(&d_iseg, ni));
+      ST(mem_.alloc(&d_isl0, ni));
+      ST(mem_.alloc(&d_isl1, ni));
+      ST(mem_.alloc(&d_si0, S));
+      ST(mem_.alloc(&d_sni, S));
+      CK(cudaMemcpy(d_iseg, iseg.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_isl0, isl0.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_isl1, isl1.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_si0, sitem0.data(), S * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_sni, snit.data(), S * 4, cudaMemcpyHostToDevice));
+      g.list[k - 1] = ItemList{ni, d_iseg, d_isl0, d_isl1, d_si0, d_sni};
+      max_items = std::max(max_items, ni);
+      if (k == 1) item_slices_ = (int)((nslices_ + ni - 1) / ni);
+    }
+    SG_ = g;
+    nitems_ = max_items;
+    ST(mem_.alloc(&red_.partial, (int64_t)max_items * kRedComp));
     return GSPM_OK;
   }
 
@@ -1084,6 +1372,25 @@ class Engine final : public EngineBase {
   int var_block_ = 0, var_scalar_ = 0;
   float tune_ms_block_[kSpmvVariants] = {}, tune_ms_scalar_[kSpmvVariants] = {};
   int seen_[kSolveSlots] = {};
+  // K^ms / K^mech solves: pinned system (flag) or the consistent singular one (default)
+  int pinned_ = 0;
+  bool resolve_ = false;     // equilibria solved again at m* (Algorithm B.1 step 3 variant)
+  double* wmean_ = nullptr;  // [n] 1 / (rows of the row's segment), 0 on padding rows
+  double* proj_ = nullptr;   // [6 nseg] per-segment means of b, then pinned values of x
+  T* pinsave_ = nullptr;     // [3 nseg]
+  // CUDA-graph replay state
+  bool graph_on_ = false, capturing_ = false;
+  cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr;
+  cudaGraphExec_t gexec_ = nullptr;
+  int gexec_x0_ = -1;
+  int64_t graph_static_ = 0;  // launches per replay outside the loop bodies
+  int64_t graph_body_ = 0;    // launches captured inside loop bodies (once each)
+  LoopCtl loop_{};            // loop control of the body being captured (zero otherwise)
+  int* loop_cnt_ = nullptr;
+  unsigned long long* loop_total_ = nullptr;
+  unsigned long long loops_seen_ = 0;
+  long long* gstats_ = nullptr;  // [nseg][4]: it_ms, it_mech, it_gs, noconv
+  void* host_graph_ = nullptr;   // pinned: gstats, loop total, CG status blocks
 };
 
 }  // namespace gspm
@@ -1315,6 +1622,11 @@ int gspm_apply(gspm_ctx* ctx, int op, const double* x, double* y, int where) {
 }
 
 int64_t gspm_launch_count(const gspm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gspm_set_graph(gspm_ctx* ctx, int on) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->set_graph(on);
+}
 
 int gspm_set_x0_mode(gspm_ctx* ctx, int mode) {
   NEED_ENGINE(ctx);

@@ -34,21 +34,90 @@ int make_params(const gspm_material* m, const gspm_options* o, Params* p) {
   p->l100 = m->lambda100; p->l111 = m->lambda111;
   p->me_coef = 3.0 / p->scale;
   for (int i = 0; i < 9; ++i) p->Nd[i] = m->Nd[i];
-  // E_ext = C^-1 sigma_ext for the cubic stiffness (closed-form inverse of the normal block;
-  // tensor shear strain = sigma / (2 C44))
+  // App. D rotation (all zero = identity); must be a proper rotation
+  bool zero = true;
+  for (int i = 0; i < 9; ++i) zero = zero && m->R[i] == 0.0;
+  for (int i = 0; i < 9; ++i) p->R[i] = zero ? (i % 4 == 0 ? 1.0 : 0.0) : m->R[i];
+  {
+    double err = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double d = 0.0;
+        for (int k = 0; k < 3; ++k) d += p->R[3 * i + k] * p->R[3 * j + k];
+        err = std::max(err, std::fabs(d - (i == j ? 1.0 : 0.0)));
+      }
+    const double* R = p->R;
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (err > 1e-12 || std::fabs(det - 1.0) > 1e-12) {
+      set_error("material: R is not a proper rotation (R R^T = I, det R = 1 to 1e-12)");
+      return GSPM_EINVAL;
+    }
+  }
+  p->rotated = 0;
+  for (int i = 0; i < 9; ++i) p->rotated |= p->R[i] != (i % 4 == 0 ? 1.0 : 0.0);
+  // stiffness tensor in the mesh axes: C'_ijkl = R_ia R_jb R_kc R_ld C_abcd (cubic C in the
+  // crystal axes)
+  double Cc[81];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+          double v = 0.0;
+          if (a == b && c == d) v = a == c ? m->C11 : m->C12;
+          else if ((a == c && b == d) || (a == d && b == c)) v = m->C44;
+          Cc[((a * 3 + b) * 3 + c) * 3 + d] = v;
+        }
+  for (int i = 0; i < 81; ++i) {
+    const int ii = i / 27, jj = (i / 9) % 3, kk = (i / 3) % 3, ll = i % 3;
+    double v = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d)
+            v += p->R[3 * ii + a] * p->R[3 * jj + b] * p->R[3 * kk + c] * p->R[3 * ll + d] *
+                 Cc[((a * 3 + b) * 3 + c) * 3 + d];
+    p->Cm[i] = v;
+  }
+  // E_ext = C^-1 sigma_ext: rotate sigma_ext into the crystal axes (R^T s R), apply the cubic
+  // compliance (closed-form inverse of the normal block; tensor shear strain = sigma / (2 C44)),
+  // rotate back (R e R^T)
   const double d = (m->C11 - m->C12) * (m->C11 + 2.0 * m->C12);
   if (!(d != 0.0) || !(m->C44 != 0.0)) {
     set_error("material: singular elastic stiffness");
     return GSPM_EINVAL;
   }
   const double S11 = (m->C11 + m->C12) / d, S12 = -m->C12 / d;
-  const double* s = m->sigma_ext;
-  p->E_ext[0] = S11 * s[0] + S12 * (s[1] + s[2]);
-  p->E_ext[1] = S11 * s[1] + S12 * (s[0] + s[2]);
-  p->E_ext[2] = S11 * s[2] + S12 * (s[0] + s[1]);
-  p->E_ext[3] = s[3] / (2.0 * m->C44);
-  p->E_ext[4] = s[4] / (2.0 * m->C44);
-  p->E_ext[5] = s[5] / (2.0 * m->C44);
+  const double* sv = m->sigma_ext;
+  const double sm[3][3] = {{sv[0], sv[5], sv[4]}, {sv[5], sv[1], sv[3]}, {sv[4], sv[3], sv[2]}};
+  double sc[3][3], ec[3][3], em[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) v += p->R[3 * a + i] * sm[a][b] * p->R[3 * b + j];
+      sc[i][j] = v;
+    }
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    ec[i][i] = S11 * sc[i][i] + S12 * (sc[j][j] + sc[k][k]);
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (i != j) ec[i][j] = sc[i][j] / (2.0 * m->C44);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) v += p->R[3 * i + a] * ec[a][b] * p->R[3 * j + b];
+      em[i][j] = v;
+    }
+  p->E_ext[0] = em[0][0];
+  p->E_ext[1] = em[1][1];
+  p->E_ext[2] = em[2][2];
+  p->E_ext[3] = em[1][2];
+  p->E_ext[4] = em[0][2];
+  p->E_ext[5] = em[0][1];
   return GSPM_OK;
 }
 
@@ -357,7 +426,6 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
       for (int k = 0; k < 4; ++k) nti[fill[hm.tets_u[4 * e + k]]++] = e;
   }
   const double C11 = p.C11, C12 = p.C12, C44 = p.C44, eps = p.eps, aeps = p.alpha * p.eps;
-  const int64_t pin = ops->pin;
 #pragma omp parallel
   {
     std::vector<double> kms, km, mm, f, g, k9, bb;
@@ -395,12 +463,21 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
             f[3 * pos + a] += -(V / 4.0) * gl[a];   // -int phi_i d_a phi_j
             g[3 * pos + a] += (V / 4.0) * gk[a];    //  int phi_j d_a phi_i
           }
-          // cubic C: K_ab = d_ab [(C11 - C44) gk_a gl_a + C44 gk.gl] + (1 - d_ab)[C12 gk_a gl_b
-          //                + C44 gk_b gl_a]  (= sum_cd gk_c C_acbd gl_d)
+          // K_ab = sum_cd gk_c C_acbd gl_d; in the cube axes
+          // K_ab = d_ab [(C11 - C44) gk_a gl_a + C44 gk.gl] + (1 - d_ab)[C12 gk_a gl_b
+          //        + C44 gk_b gl_a]
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
-              const double v = a == b ? (C11 - C44) * gk[a] * gl[a] + C44 * dot
-                                      : C12 * gk[a] * gl[b] + C44 * gk[b] * gl[a];
+              double v;
+              if (p.rotated) {
+                v = 0.0;
+                for (int c = 0; c < 3; ++c)
+                  for (int dd = 0; dd < 3; ++dd)
+                    v += gk[c] * p.Cm[((a * 3 + c) * 3 + b) * 3 + dd] * gl[dd];
+              } else {
+                v = a == b ? (C11 - C44) * gk[a] * gl[a] + C44 * dot
+                           : C12 * gk[a] * gl[b] + C44 * gk[b] * gl[a];
+              }
               k9[9 * pos + 3 * a + b] += V * v;
             }
         }
@@ -409,9 +486,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
       for (int pos = 0; pos < len; ++pos) {
         const int64_t ent = s.sptr[sl] + (int64_t)pos * kSell + lane;
         const int64_t vb = ent - lane;  // value base for B-valued matrices
-        const bool pinned = (i == pin) || (rc[pos] == pin);
-        const bool diag = rc[pos] == i;
-        ops->Kms[ent] = pinned ? (diag ? 1.0 : 0.0) : kms[pos];
+        ops->Kms[ent] = kms[pos];
         ops->M[ent] = mm[pos];
         ops->Aeps[ent] = mm[pos] + eps * km[pos];
         ops->Aaeps[ent] = mm[pos] + aeps * km[pos];
@@ -419,9 +494,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
           ops->F[vb * 3 + a * kSell + lane] = f[3 * pos + a];
           ops->G[vb * 3 + a * kSell + lane] = g[3 * pos + a];
         }
-        for (int b = 0; b < 9; ++b)
-          ops->Kmech[vb * 9 + b * kSell + lane] =
-              pinned ? ((diag && (b == 0 || b == 4 || b == 8)) ? 1.0 : 0.0) : k9[9 * pos + b];
+        for (int b = 0; b < 9; ++b) ops->Kmech[vb * 9 + b * kSell + lane] = k9[9 * pos + b];
       }
       for (int pos = 0; pos < len; ++pos)
         ops->Agg[s.sptr[sl] + (int64_t)pos * kSell + lane] = bb[pos] / (4.0 * ml);

@@ -27,6 +27,11 @@ struct Params {
   double me_coef;   // 3 / (mu0 Ms^2)
   double Nd[9];
   double E_ext[6];  // C^-1 sigma_ext, Voigt order, tensor shear components
+  // App. D: v_mesh = R v_crystal; rotated = R is not the identity.  Cm = the stiffness tensor
+  // C_ijkl in the mesh axes (index (((i*3 + j)*3 + k)*3 + l)), used for K^mech when rotated.
+  double R[9];
+  int rotated;
+  double Cm[81];
 };
 int make_params(const gspm_material* mat, const gspm_options* opt, Params* p);
 

@@ -38,7 +38,7 @@ __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * block
 // thread of that block).
 template <int NC>
 __device__ __forceinline__ bool seg_reduce(double (&v)[NC], int item, int seg, const DSeg& G,
-                                           const Red& red, double* res) {
+                                           const ItemList& IL, const Red& red, double* res) {
   __shared__ double sm[NC][32];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -58,12 +58,12 @@ __device__ __forceinline__ bool seg_reduce(double (&v)[NC], int item, int seg, c
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(G.counter + seg, 1u);
-    am_last = (t == (unsigned)G.seg_nitems[seg] - 1u);
+    am_last = (t == (unsigned)IL.seg_nitems[seg] - 1u);
   }
   __syncthreads();
   if (!am_last) return false;
   __threadfence();
-  const int i0 = G.seg_item0[seg], ni = G.seg_nitems[seg];
+  const int i0 = IL.seg_item0[seg], ni = IL.seg_nitems[seg];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     double acc = 0.0;
@@ -199,17 +199,17 @@ __device__ __forceinline__ bool unit_combine(Acc (&acc)[N], int lane) {
 // nodal weights M_L,i / V(segment)
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_wsum(DSeg G, int nc, const T* __restrict__ f,
+__global__ void __launch_bounds__(kBlock) k_wsum(DSeg G, ItemList IL, int nc, const T* __restrict__ f,
                                                  int64_t cs, int64_t ns,
                                                  const int64_t* __restrict__ perm,
                                                  const double* __restrict__ w, double* out,
                                                  const double* add, Red red) {
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     double v[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) v[c] = 0.0;
-    const int64_t r0 = (int64_t)G.item_sl0[item] * 32, r1 = (int64_t)G.item_sl1[item] * 32;
+    const int64_t r0 = (int64_t)IL.sl0[item] * 32, r1 = (int64_t)IL.sl1[item] * 32;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       if (!row_valid(G, seg, i)) continue;
       const double wi = w[i];
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) k_wsum(DSeg G, int nc, const T* __rest
         if (c < nc) v[c] += wi * (double)f[src * ns + c * cs];
     }
     __shared__ double res[9];
-    if (seg_reduce<9>(v, item, seg, G, red, res) && threadIdx.x == 0)
+    if (seg_reduce<9>(v, item, seg, G, IL, red, res) && threadIdx.x == 0)
       for (int c = 0; c < nc; ++c) out[seg * nc + c] = res[c] + (add ? add[c] : 0.0);
   }
 }
@@ -294,19 +294,30 @@ __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, cons
   if (any) atomicAdd(nactive, 1);
 }
 
-// r = b - A x, p = r (scalar B = 1 or 3x3 block B = 9), one right-hand side
+// r = b' - A x, p = r (scalar B = 1 or 3x3 block B = 9), one right-hand side, where
+//   bmean != NULL: b' = b - bmean[seg] per component (the consistent singular system's
+//                  right-hand side: b projected off the constants),
+//   pinned:        b' = b with r = 0 at the segment's pinned row (the pinned system; x and b
+//                  are 0 there).
 template <typename T, int B>
-__global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, const T* __restrict__ val,
+__global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL, const T* __restrict__ val,
                                                     const T* __restrict__ b,
                                                     const T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ p,
                                                     CGState* st, int* nactive, double rtol,
-                                                    int max_iter, Red red) {
+                                                    int max_iter, Red red,
+                                                    const double* __restrict__ bmean,
+                                                    int pinned) {
+  constexpr int NC = B == 9 ? 3 : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
+    const int64_t pin = pinned ? G.seg_pin[seg] : -1;
+    double bm[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) bm[a] = bmean ? bmean[NC * seg + a] : 0.0;
     double v[2] = {0.0, 0.0};  // rr, bb
-    for (int64_t s = G.item_sl0[item] + warp; s < G.item_sl1[item]; s += kBlock / 32) {
+    for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
       const int64_t row = s * 32 + lane;
       const bool ok = row_valid(G, seg, row);
       if (B == 1) {
@@ -314,11 +325,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, const T* __
         const int skip[1] = {0};
         sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, acc);
         if (ok) {
-          const T rv = (T)((double)b[row] - acc[0]);
+          const double bv = (double)b[row] - bm[0];
+          const T rv = row == pin ? T(0) : (T)(bv - acc[0]);
           r[row] = rv;
           p[row] = rv;
           v[0] += (double)rv * (double)rv;
-          v[1] += (double)b[row] * (double)b[row];
+          v[1] += bv * bv;
         }
       } else {
         double acc[3];
@@ -326,17 +338,18 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, const T* __
         if (ok) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            const T rv = (T)((double)b[3 * row + a] - acc[a]);
+            const double bv = (double)b[3 * row + a] - bm[a];
+            const T rv = row == pin ? T(0) : (T)(bv - acc[a]);
             r[3 * row + a] = rv;
             p[3 * row + a] = rv;
             v[0] += (double)rv * (double)rv;
-            v[1] += (double)b[3 * row + a] * (double)b[3 * row + a];
+            v[1] += bv * bv;
           }
         }
       }
     }
     __shared__ double res[2];
-    if (seg_reduce<2>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+    if (seg_reduce<2>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       const double bb[1] = {res[1]}, rr[1] = {res[0]};
       cg_start(st + seg, nactive, 1, bb, rr, rtol, max_iter, 1);
     }
@@ -345,7 +358,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, const T* __
 
 // GSPM systems (M + c eps K) g = M f with x0 = f already in x: b = M x, r = b - A x, p = r
 template <typename T, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G,
+__global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G, ItemList IL,
                                                        const T* __restrict__ aval,
                                                        const T* __restrict__ mval, int64_t ld,
                                                        const T* __restrict__ x,
@@ -354,12 +367,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G,
                                                        int max_iter, Red red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int skip[NR] = {};
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     double v[2 * NR];
 #pragma unroll
     for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
-    for (int64_t s = G.item_sl0[item] + warp; s < G.item_sl1[item]; s += kBlock / 32) {
+    for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
       double ax[NR], mx[NR];
       sell_scalar_row<T, T, double, NR>(A, aval, s, lane, x, ld, skip, ax);
       sell_scalar_row<T, T, double, NR>(A, mval, s, lane, x, ld, skip, mx);
@@ -376,7 +389,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G,
       }
     }
     __shared__ double res[2 * NR];
-    if (seg_reduce<2 * NR>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+    if (seg_reduce<2 * NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       double bb[NR], rr[NR];
       for (int k = 0; k < NR; ++k) {
         rr[k] = res[2 * k];
@@ -387,24 +400,27 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G,
   }
 }
 
-// q = A p with the p.q dot fused; the segment's last item forms alpha = rr / p.q
+// q = A p with the p.q dot fused; the segment's last item forms alpha = rr / p.q.
+// pinned: q = 0 at the segment's pinned row (the pinned operator; p is 0 there).
 template <typename T, int B, int NR, int VAR>
-__global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, const T* __restrict__ val,
+__global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, ItemList IL, const T* __restrict__ val,
                                                     int64_t ld, const T* __restrict__ p,
-                                                    T* __restrict__ q, CGState* st, Red red) {
+                                                    T* __restrict__ q, CGState* st, Red red,
+                                                    int pinned) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     CGState* sg = st + seg;
     if (!sg->active) continue;
+    const int64_t pin = pinned ? G.seg_pin[seg] : -1;
     int skip[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) skip[k] = sg->r[k].done;
     double v[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) v[k] = 0.0;
-    const int64_t u0 = (int64_t)G.item_sl0[item] * units_per_slice<VAR>();
-    const int64_t u1 = (int64_t)G.item_sl1[item] * units_per_slice<VAR>();
+    const int64_t u0 = (int64_t)IL.sl0[item] * units_per_slice<VAR>();
+    const int64_t u1 = (int64_t)IL.sl1[item] * units_per_slice<VAR>();
     for (int64_t u = u0 + warp; u < u1; u += kBlock / 32) {
       int64_t s;
       int sl, k0, ks;
@@ -413,6 +429,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, const T* __
       if (B == 1) {
         T acc[NR];
         sell_scalar_row<T, T, T, NR>(A, val, s, sl, p, ld, skip, acc, k0, ks);
+        if (row == pin) {
+#pragma unroll
+          for (int k = 0; k < NR; ++k) acc[k] = T(0);
+        }
         if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
 #pragma unroll
           for (int k = 0; k < NR; ++k)
@@ -424,6 +444,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, const T* __
       } else {
         T acc[3];
         sell_block_row<T, T, T, VAR>(A, val, s, sl, p, acc, k0, ks);
+        if (row == pin) acc[0] = acc[1] = acc[2] = T(0);
         if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
@@ -434,7 +455,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, const T* __
       }
     }
     __shared__ double res[NR];
-    if (seg_reduce<NR>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+    if (seg_reduce<NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       for (int k = 0; k < NR; ++k) {
         CGRhs& c = sg->r[k];
         if (c.done) continue;
@@ -450,16 +471,43 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, const T* __
   }
 }
 
+// 16-byte packs of vector elements for the CG vector kernels
+template <typename T> struct Pack16;
+template <> struct Pack16<float> { using V = float4; static constexpr int W = 4; };
+template <> struct Pack16<double> { using V = double2; static constexpr int W = 2; };
+
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&v)[Pack16<T>::W]) {
+  *reinterpret_cast<typename Pack16<T>::V*>(v) = *reinterpret_cast<const typename Pack16<T>::V*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&v)[Pack16<T>::W]) {
+  *reinterpret_cast<typename Pack16<T>::V*>(p) = *reinterpret_cast<const typename Pack16<T>::V*>(v);
+}
+
+// Element range [e0, e1) of an item in a vector of epr elements per row, clipped to the
+// segment's rows.  e0 is a multiple of 32 * epr, so 16-byte aligned when the vector is.
+__device__ __forceinline__ void item_elems(const DSeg& G, const ItemList& IL, int item, int seg,
+                                           int epr, int64_t& e0, int64_t& e1) {
+  e0 = (int64_t)IL.sl0[item] * 32 * epr;
+  const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
+  const int64_t rhi = (int64_t)IL.sl1[item] * 32;
+  e1 = (rhi < rend ? rhi : rend) * epr;
+}
+
 // x += alpha p, r -= alpha q, r.r fused; the segment's last item forms beta and decides
 // convergence.  Vectors hold epr elements per row (1: scalar SoA with stride ld; 3: [n][3]).
-template <typename T, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, int epr, int64_t ld,
+// VEC: all vectors 16-byte aligned (and ld a multiple of the pack width), so the item's range
+// moves in 16-byte packs with a scalar tail.
+template <typename T, int NR, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int epr, int64_t ld,
                                                       T* __restrict__ x, T* __restrict__ r,
                                                       const T* __restrict__ p,
                                                       const T* __restrict__ q, CGState* st,
                                                       int* nactive, Red red) {
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+  constexpr int W = Pack16<T>::W;
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     CGState* sg = st + seg;
     if (!sg->active) continue;
     int skip[NR];
@@ -472,11 +520,36 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, int epr, int64_t l
     double v[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) v[k] = 0.0;
-    const int64_t e0 = (int64_t)G.item_sl0[item] * 32 * epr;
-    const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
-    const int64_t rhi = (int64_t)G.item_sl1[item] * 32;
-    const int64_t e1 = (rhi < rend ? rhi : rend) * epr;
-    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+    int64_t e0, e1;
+    item_elems(G, IL, item, seg, epr, e0, e1);
+    int64_t etail = e0;
+    if (VEC) {
+      const int64_t np = (e1 - e0) / W;
+      for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+          if (!skip[k]) {
+            const int64_t o = k * ld + e0 + t * W;
+            T xv[W], rv[W], pv[W], qv[W];
+            ld16(x + o, xv);
+            ld16(r + o, rv);
+            ld16(p + o, pv);
+            ld16(q + o, qv);
+            T rr = T(0);  // the pack's r.r in T, one FP64 add per pack
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+              xv[c] += al[k] * pv[c];
+              rv[c] -= al[k] * qv[c];
+              rr += rv[c] * rv[c];
+            }
+            v[k] += (double)rr;
+            st16(x + o, xv);
+            st16(r + o, rv);
+          }
+      }
+      etail = e0 + np * W;
+    }
+    for (int64_t i = etail + threadIdx.x; i < e1; i += blockDim.x) {
 #pragma unroll
       for (int k = 0; k < NR; ++k)
         if (!skip[k]) {
@@ -488,7 +561,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, int epr, int64_t l
         }
     }
     __shared__ double res[NR];
-    if (seg_reduce<NR>(v, item, seg, G, red, res) && threadIdx.x == 0) {
+    if (seg_reduce<NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       int any = 0;
       for (int k = 0; k < NR; ++k) {
         CGRhs& c = sg->r[k];
@@ -510,12 +583,23 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, int epr, int64_t l
   }
 }
 
-template <typename T, int NR>
-__global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, int epr, int64_t ld,
+// p = r + beta p
+// In a graph loop, block 0 also decides whether the loop runs again (nactive is final: the
+// update kernel before this one has finished).
+template <typename T, int NR, bool VEC>
+__global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int epr, int64_t ld,
                                                        const T* __restrict__ r,
-                                                       T* __restrict__ p, const CGState* st) {
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+                                                       T* __restrict__ p, const CGState* st,
+                                                       LoopCtl lc) {
+  constexpr int W = Pack16<T>::W;
+  if (lc.count && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int c = *lc.count + 1;
+    *lc.count = c;
+    *lc.total += 1ull;
+    cudaGraphSetConditional(lc.handle, (__ldcg(lc.nactive) > 0 && c < lc.limit) ? 1u : 0u);
+  }
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     const CGState* sg = st + seg;
     if (!sg->active) continue;
     int skip[NR];
@@ -525,11 +609,27 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, int epr, int64_t 
       skip[k] = sg->r[k].done;
       be[k] = (T)sg->r[k].beta;
     }
-    const int64_t e0 = (int64_t)G.item_sl0[item] * 32 * epr;
-    const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
-    const int64_t rhi = (int64_t)G.item_sl1[item] * 32;
-    const int64_t e1 = (rhi < rend ? rhi : rend) * epr;
-    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+    int64_t e0, e1;
+    item_elems(G, IL, item, seg, epr, e0, e1);
+    int64_t etail = e0;
+    if (VEC) {
+      const int64_t np = (e1 - e0) / W;
+      for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+          if (!skip[k]) {
+            const int64_t o = k * ld + e0 + t * W;
+            T rv[W], pv[W];
+            ld16(r + o, rv);
+            ld16(p + o, pv);
+#pragma unroll
+            for (int c = 0; c < W; ++c) pv[c] = rv[c] + be[k] * pv[c];
+            st16(p + o, pv);
+          }
+      }
+      etail = e0 + np * W;
+    }
+    for (int64_t i = etail + threadIdx.x; i < e1; i += blockDim.x) {
 #pragma unroll
       for (int k = 0; k < NR; ++k)
         if (!skip[k]) {
@@ -540,14 +640,56 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, int epr, int64_t 
   }
 }
 
+// x(i, c) -= x(pin, c) over each segment's rows (element (i, c) at x[i * epr + c]): the
+// singular system's solution moved to the pinned system's (zero at the pinned node).  xp holds
+// the segment's pinned values, read by k_pin_gather first.
+template <typename T>
+__global__ void k_pin_gather(DSeg G, int epr, const T* __restrict__ x, double* __restrict__ xp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.nseg * epr;
+       i += gridDim.x * blockDim.x) {
+    const int seg = i / epr, c = i % epr;
+    xp[i] = (double)x[G.seg_pin[seg] * epr + c];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pin_shift(DSell A, DSeg G, int epr, T* __restrict__ x,
+                                                      const double* __restrict__ xp) {
+  const int64_t len = (int64_t)A.nslices * 32 * epr;
+  for (int64_t e = gtid(); e < len; e += gstride()) {
+    const int64_t row = e / epr;
+    const int seg = G.seg_of_slice[row >> 5];
+    if (!row_valid(G, seg, row)) continue;
+    x[e] = (T)((double)x[e] - xp[seg * epr + (int)(e - row * epr)]);
+  }
+}
+
+__global__ void k_loop_start(LoopCtl lc) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *lc.count = 0;
+    cudaGraphSetConditional(lc.handle, __ldcg(lc.nactive) > 0 ? 1u : 0u);
+  }
+}
+
+__global__ void k_solve_stats(const CGState* st, int nseg, int kind, long long* acc) {
+  for (int sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x) {
+    const CGState& c = st[sg];
+    int it = 0;
+    for (int k = 0; k < c.nr; ++k)
+      it = kind == 2 ? it + c.r[k].iters : (c.r[k].iters > it ? c.r[k].iters : it);
+    acc[4 * sg + kind] += it;
+    acc[4 * sg + 3] += c.noconv;
+  }
+}
+
 // x = 0 for segments whose right-hand side vanished
 template <typename T>
-__global__ void k_cg_zero(DSeg G, int epr, T* x, const CGState* st) {
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+__global__ void k_cg_zero(DSeg G, ItemList IL, int epr, T* x, const CGState* st) {
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     if (!st[seg].zero_x) continue;
-    const int64_t e0 = (int64_t)G.item_sl0[item] * 32 * epr;
-    const int64_t e1 = (int64_t)G.item_sl1[item] * 32 * epr;
+    const int64_t e0 = (int64_t)IL.sl0[item] * 32 * epr;
+    const int64_t e1 = (int64_t)IL.sl1[item] * 32 * epr;
     for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) x[i] = T(0);
   }
 }
@@ -555,11 +697,12 @@ __global__ void k_cg_zero(DSeg G, int epr, T* x, const CGState* st) {
 // ------------------------------------------------------------------------------------------
 // F^ms / G operators (Sec. 2.3): right-hand sides and derivatives as row gathers
 // ------------------------------------------------------------------------------------------
-// b_i = sum_j F_{ij,a} m_{j,a}  (Eq. RHS_b divided by m_s); the segment's pinned entry is 0
+// b_i = sum_j F_{ij,a} m_{j,a}  (Eq. RHS_b divided by m_s); pin_zero: the segment's pinned
+// entry is 0 (right-hand side of the pinned system)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, DSeg G, const T* __restrict__ Fv,
                                                  const T* __restrict__ m, int64_t ld,
-                                                 T* __restrict__ b) {
+                                                 T* __restrict__ b, int pin_zero) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
@@ -576,7 +719,7 @@ __global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, DSeg G, const T* __res
              __ldcs(fp + 64) * __ldg(m + 2 * ld + j);
     }
     const int64_t row = s * 32 + lane;
-    if (row < A.n) b[row] = row == G.seg_pin[G.seg_of_slice[s]] ? T(0) : acc;
+    if (row < A.n) b[row] = pin_zero && row == G.seg_pin[G.seg_of_slice[s]] ? T(0) : acc;
   }
 }
 
@@ -654,12 +797,12 @@ __global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, DSeg G, const T* __
   }
 }
 
-// b^mech_(i,a) = sum_j sum_c G_{ij,c} sigma0_{j,ac}, sigma0 = C E0 (nodal, [n][6] Voigt);
-// the segment's pinned node's entries are 0  (= F^mech E0 of Eq. RHS_b for a uniform C)
+// b^mech_(i,a) = sum_j sum_c G_{ij,c} sigma0_{j,ac}, sigma0 = C E0 (nodal, [n][6] Voigt)
+// (= F^mech E0 of Eq. RHS_b for a uniform C); pin_zero: the segment's pinned node's entries are 0
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, DSeg G, const T* __restrict__ Gv,
                                                  const T* __restrict__ sig0,
-                                                 T* __restrict__ b) {
+                                                 T* __restrict__ b, int pin_zero) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   for (int64_t s = gtid() >> 5; s < A.nslices; s += nw) {
@@ -682,7 +825,7 @@ __global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, DSeg G, const T* __res
     }
     const int64_t row = s * 32 + lane;
     if (row < A.n) {
-      const bool pz = row == G.seg_pin[G.seg_of_slice[s]];
+      const bool pz = pin_zero && row == G.seg_pin[G.seg_of_slice[s]];
       b[3 * row] = pz ? T(0) : b0;
       b[3 * row + 1] = pz ? T(0) : b1;
       b[3 * row + 2] = pz ? T(0) : b2;
@@ -717,6 +860,50 @@ __device__ __forceinline__ void stress_of(const T (&e)[6], const DevParams& P, T
   s[5] = T(2) * C44 * e[5];
 }
 
+// App. D rotations: v_mesh = R v_crystal; symmetric tensors in Voigt order (tensor shear)
+// A_mesh = R A_crystal R^T.  to_mesh = 0 applies the inverse (R^T v, R^T A R).
+template <typename T>
+__device__ __forceinline__ void rot_vec(const DevParams& P, bool to_mesh, const T (&v)[3],
+                                        T (&o)[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc += (T)(to_mesh ? P.R[3 * i + k] : P.R[3 * k + i]) * v[k];
+    o[i] = acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void rot_sym(const DevParams& P, bool to_mesh, const T (&v)[6],
+                                        T (&o)[6]) {
+  const T A[3][3] = {{v[0], v[5], v[4]}, {v[5], v[1], v[3]}, {v[4], v[3], v[2]}};
+  T Q[3][3], B[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Q[i][k] = (T)(to_mesh ? P.R[3 * i + k] : P.R[3 * k + i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc += Q[i][a] * A[a][b] * Q[j][b];
+      B[i][j] = acc;
+    }
+  o[0] = B[0][0];
+  o[1] = B[1][1];
+  o[2] = B[2][2];
+  o[3] = B[1][2];
+  o[4] = B[0][2];
+  o[5] = B[0][1];
+}
+
+// E0(m) and sigma0 = C E0 in the mesh axes; rotated crystal (Algorithm D.1 step 1): both
+// evaluated in the crystal axes at R^T m and rotated to the mesh axes
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_e0(int64_t n, const T* __restrict__ m, int64_t ld,
                                                const uint8_t* __restrict__ mag, DevParams P,
@@ -724,8 +911,18 @@ __global__ void __launch_bounds__(kBlock) k_e0(int64_t n, const T* __restrict__ 
   for (int64_t i = gtid(); i < n; i += gstride()) {
     T e[6] = {}, s[6] = {};
     if (mag[i]) {
-      e0_of<T>(m[i], m[ld + i], m[2 * ld + i], P, e);
-      stress_of<T>(e, P, s);
+      if (P.rotated) {
+        const T mm[3] = {m[i], m[ld + i], m[2 * ld + i]};
+        T mc[3], ec[6], sc[6];
+        rot_vec<T>(P, false, mm, mc);
+        e0_of<T>(mc[0], mc[1], mc[2], P, ec);
+        stress_of<T>(ec, P, sc);
+        rot_sym<T>(P, true, ec, e);
+        rot_sym<T>(P, true, sc, s);
+      } else {
+        e0_of<T>(m[i], m[ld + i], m[2 * ld + i], P, e);
+        stress_of<T>(e, P, s);
+      }
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -755,22 +952,47 @@ __global__ void __launch_bounds__(kBlock) k_hfield(int64_t n, DSeg G, const T* _
       const int seg = G.seg_of_slice[i >> 5];
       const double* mb = mbar + 3 * seg;
       const double* hs = hz + 3 * seg;
-      T e0[6], d[6], s[6];
-      e0_of<T>(mv[0], mv[1], mv[2], P, e0);
+      // crystal terms (anisotropy, magnetoelastic) in the crystal axes: m_c = R^T m and
+      // E_c = R^T E R when rotated (Algorithm D.1 step 4), rotated back with R at the end
+      T mc[3], Ec[6];
+      if (P.rotated) {
+        const T Em[6] = {E[i], E[ld + i], E[2 * ld + i], E[3 * ld + i], E[4 * ld + i],
+                         E[5 * ld + i]};
+        rot_vec<T>(P, false, mv, mc);
+        rot_sym<T>(P, false, Em, Ec);
+      } else {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) d[c] = E[c * ld + i] - e0[c];
+        for (int a = 0; a < 3; ++a) mc[a] = mv[a];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Ec[c] = E[c * ld + i];
+      }
+      T e0[6], d[6], s[6];
+      e0_of<T>(mc[0], mc[1], mc[2], P, e0);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) d[c] = Ec[c] - e0[c];
       stress_of<T>(d, P, s);
       // full symmetric stress lookup: (0,0)->0 (1,1)->1 (2,2)->2 (1,2)->3 (0,2)->4 (0,1)->5
       const T S[3][3] = {{s[0], s[5], s[4]}, {s[5], s[1], s[3]}, {s[4], s[3], s[2]}};
-      const T m2sum = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+      const T m2sum = mc[0] * mc[0] + mc[1] * mc[1] + mc[2] * mc[2];
+      T hc[3], hm[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const T an = -kap * mc[a] * (m2sum - mc[a] * mc[a]);
+        const T me = mec * (l100 * mc[a] * S[a][a] + l111 * (mc[b] * S[a][b] + mc[c] * S[a][c]));
+        hc[a] = an + me;
+      }
+      if (P.rotated) {
+        rot_vec<T>(P, true, hc, hm);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) hm[a] = hc[a];
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
         const T far = (T)(hs[a] - (P.Nd[3 * a] * mb[0] + P.Nd[3 * a + 1] * mb[1] +
                                    P.Nd[3 * a + 2] * mb[2]));
-        const T an = -kap * mv[a] * (m2sum - mv[a] * mv[a]);
-        const T me = mec * (l100 * mv[a] * S[a][a] + l111 * (mv[b] * S[a][b] + mv[c] * S[a][c]));
-        hv[a] = an + far + me + hd[a * ld + i];
+        hv[a] = hm[a] + far + hd[a * ld + i];
       }
     }
     if (mode == 0) {
@@ -845,15 +1067,15 @@ __global__ void __launch_bounds__(kBlock) k_gs_stage(int64_t n, int64_t ld, int 
 // Algorithm B.1 step 4: m = m** / |m**| on Omega_m; <|m_new - m_old|> over each segment's
 // magnetic nodes
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_project(DSeg G, int64_t ld, const T* __restrict__ x,
+__global__ void __launch_bounds__(kBlock) k_project(DSeg G, ItemList IL, int64_t ld, const T* __restrict__ x,
                                                     const uint8_t* __restrict__ mag,
                                                     T* __restrict__ m, double* dm_out,
                                                     const double* __restrict__ inv_nmag,
                                                     Red red) {
-  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
-    const int seg = G.item_seg[item];
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
     double v[1] = {0.0};
-    const int64_t r0 = (int64_t)G.item_sl0[item] * 32, r1 = (int64_t)G.item_sl1[item] * 32;
+    const int64_t r0 = (int64_t)IL.sl0[item] * 32, r1 = (int64_t)IL.sl1[item] * 32;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       if (!mag[i]) continue;
       const T a = x[i], b = x[ld + i], c = x[2 * ld + i];
@@ -866,7 +1088,7 @@ __global__ void __launch_bounds__(kBlock) k_project(DSeg G, int64_t ld, const T*
       m[2 * ld + i] = nc;
     }
     __shared__ double res[1];
-    if (seg_reduce<1>(v, item, seg, G, red, res) && threadIdx.x == 0)
+    if (seg_reduce<1>(v, item, seg, G, IL, red, res) && threadIdx.x == 0)
       dm_out[seg] = res[0] * inv_nmag[seg];
   }
 }
@@ -924,31 +1146,39 @@ __global__ void k_scaled_diff(int64_t len, const T* __restrict__ a, const T* __r
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-int grid_for(const Launch& L, int64_t threads, const void* kernel) {
+int resident_per_sm(const void* kernel) {
   static std::mutex mu;
   static std::unordered_map<const void*, int> occ;
-  int per_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = occ.find(kernel);
-    if (it == occ.end()) {
-      int nb = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess ||
-          nb < 1)
-        nb = 1;
-      it = occ.emplace(kernel, nb).first;
-    }
-    per_sm = it->second;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = occ.find(kernel);
+  if (it == occ.end()) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    it = occ.emplace(kernel, nb).first;
   }
+  return it->second;
+}
+
+int grid_for(const Launch& L, int64_t threads, const void* kernel) {
+  const int per_sm = resident_per_sm(kernel);
   int64_t b = (threads + kBlock - 1) / kBlock;
   const int64_t cap = std::min<int64_t>((int64_t)per_sm * L.sms, L.max_blocks);
   if (b > cap) b = cap;
   return b < 1 ? 1 : (int)b;
 }
 
-// grid of an item-loop kernel: one block per item, capped at the resident capacity
-static int item_grid(const Launch& L, const DSeg& G, const void* kernel) {
-  return grid_for(L, (int64_t)G.nitems * kBlock, kernel);
+// Grid and item list of a reducing kernel: the list made for the kernel's residency, one block
+// per item (capped at the resident capacity and the launch limit).
+struct ItemGrid {
+  int grid;
+  ItemList list;
+};
+static ItemGrid item_grid(const Launch& L, const DSeg& G, const void* kernel) {
+  const int per_sm = resident_per_sm(kernel);
+  const ItemList& il = G.list[(per_sm < kItemLists ? per_sm : kItemLists) - 1];
+  return ItemGrid{grid_for(L, (int64_t)il.nitems * kBlock, kernel), il};
 }
 
 #define GSPM_GRID(L, threads, kern) grid_for((L), (threads), reinterpret_cast<const void*>(kern))
@@ -960,7 +1190,8 @@ cudaError_t launch_wsum(const Launch& L, const DSeg& G, int nc, const T* f, int6
                         const double* add, Red red) {
   (*L.counter) += 1;
   auto k = k_wsum<T>;
-  k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, nc, f, cs, ns, perm, w, out, add, red);
+  const ItemGrid ig = GSPM_IGRID(L, G, k);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, nc, f, cs, ns, perm, w, out, add, red);
   return cudaGetLastError();
 }
 
@@ -991,16 +1222,18 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
-                           int max_iter, Red red) {
+                           int max_iter, Red red, const double* bmean, int pinned) {
   (*L.counter) += 1;
   if (B == 1) {
     auto k = k_cg_init<T, 1>;
-    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, b, x, r, p, st, nactive, rtol,
-                                                    max_iter, red);
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, r, p, st, nactive, rtol,
+                                        max_iter, red, bmean, pinned);
   } else {
     auto k = k_cg_init<T, 9>;
-    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, b, x, r, p, st, nactive, rtol,
-                                                    max_iter, red);
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, r, p, st, nactive, rtol,
+                                        max_iter, red, bmean, pinned);
   }
   return cudaGetLastError();
 }
@@ -1013,19 +1246,22 @@ cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, co
   switch (nr) {
     case 1: {
       auto k = k_cg_init_gs<T, 1>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, aval, mval, ld, x, r, p, st, nactive,
+      const ItemGrid ig = GSPM_IGRID(L, G, k);
+      k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, aval, mval, ld, x, r, p, st, nactive,
                                                       rtol, max_iter, red);
       break;
     }
     case 2: {
       auto k = k_cg_init_gs<T, 2>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, aval, mval, ld, x, r, p, st, nactive,
+      const ItemGrid ig = GSPM_IGRID(L, G, k);
+      k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, aval, mval, ld, x, r, p, st, nactive,
                                                       rtol, max_iter, red);
       break;
     }
     case 3: {
       auto k = k_cg_init_gs<T, 3>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, aval, mval, ld, x, r, p, st, nactive,
+      const ItemGrid ig = GSPM_IGRID(L, G, k);
+      k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, aval, mval, ld, x, r, p, st, nactive,
                                                       rtol, max_iter, red);
       break;
     }
@@ -1037,19 +1273,23 @@ cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, co
 template <typename T, int VAR>
 static cudaError_t cg_spmv_variant(const Launch& L, const DSell& A, const DSeg& G, const T* val,
                                    int B, int nr, int64_t ld, const T* p, T* q, CGState* st,
-                                   Red red) {
+                                   Red red, int pinned) {
   if (B == 9) {
     auto k = k_cg_spmv<T, 9, 1, VAR>;
-    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 1) {
     auto k = k_cg_spmv<T, 1, 1, VAR>;
-    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 2) {
     auto k = k_cg_spmv<T, 1, 2, VAR>;
-    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 3) {
     auto k = k_cg_spmv<T, 1, 3, VAR>;
-    k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(A, G, val, ld, p, q, st, red);
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1059,35 +1299,63 @@ static cudaError_t cg_spmv_variant(const Launch& L, const DSell& A, const DSeg& 
 template <typename T>
 cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
-                           int variant) {
+                           int variant, int pinned) {
   (*L.counter) += 1;
   switch (variant) {
-    case 1: return cg_spmv_variant<T, 1>(L, A, G, val, B, nr, ld, p, q, st, red);
-    case 2: return cg_spmv_variant<T, 2>(L, A, G, val, B, nr, ld, p, q, st, red);
-    default: return cg_spmv_variant<T, 0>(L, A, G, val, B, nr, ld, p, q, st, red);
+    case 1: return cg_spmv_variant<T, 1>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
+    case 2: return cg_spmv_variant<T, 2>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
+    default: return cg_spmv_variant<T, 0>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
   }
+}
+
+static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+template <typename T, int NR, bool VEC>
+static void cg_update_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, T* x, T* r,
+                         const T* p, const T* q, CGState* st, int* nactive, Red red) {
+  auto k = k_cg_update<T, NR, VEC>;
+  const ItemGrid ig = GSPM_IGRID(L, G, k);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, x, r, p, q, st, nactive, red);
+}
+
+template <typename T, bool VEC>
+static cudaError_t cg_update_vec(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
+                                 T* x, T* r, const T* p, const T* q, CGState* st, int* nactive,
+                                 Red red) {
+  switch (nr) {
+    case 1: cg_update_nr<T, 1, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red); break;
+    case 2: cg_update_nr<T, 2, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red); break;
+    case 3: cg_update_nr<T, 3, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
                              T* r, const T* p, const T* q, CGState* st, int* nactive, Red red) {
   (*L.counter) += 1;
+  const bool vec = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) &&
+                   (nr == 1 || ld % Pack16<T>::W == 0);
+  return vec ? cg_update_vec<T, true>(L, G, epr, nr, ld, x, r, p, q, st, nactive, red)
+             : cg_update_vec<T, false>(L, G, epr, nr, ld, x, r, p, q, st, nactive, red);
+}
+
+template <typename T, int NR, bool VEC>
+static void cg_pupdate_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, const T* r, T* p,
+                          const CGState* st, const LoopCtl& lc) {
+  auto k = k_cg_pupdate<T, NR, VEC>;
+  const ItemGrid ig = GSPM_IGRID(L, G, k);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, r, p, st, lc);
+}
+
+template <typename T, bool VEC>
+static cudaError_t cg_pupdate_vec(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
+                                  const T* r, T* p, const CGState* st, const LoopCtl& lc) {
   switch (nr) {
-    case 1: {
-      auto k = k_cg_update<T, 1>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, x, r, p, q, st, nactive, red);
-      break;
-    }
-    case 2: {
-      auto k = k_cg_update<T, 2>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, x, r, p, q, st, nactive, red);
-      break;
-    }
-    case 3: {
-      auto k = k_cg_update<T, 3>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, x, r, p, q, st, nactive, red);
-      break;
-    }
+    case 1: cg_pupdate_nr<T, 1, VEC>(L, G, epr, ld, r, p, st, lc); break;
+    case 2: cg_pupdate_nr<T, 2, VEC>(L, G, epr, ld, r, p, st, lc); break;
+    case 3: cg_pupdate_nr<T, 3, VEC>(L, G, epr, ld, r, p, st, lc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1095,26 +1363,33 @@ cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, in
 
 template <typename T>
 cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
-                              const T* r, T* p, const CGState* st) {
+                              const T* r, T* p, const CGState* st, const LoopCtl& lc) {
   (*L.counter) += 1;
-  switch (nr) {
-    case 1: {
-      auto k = k_cg_pupdate<T, 1>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, r, p, st);
-      break;
-    }
-    case 2: {
-      auto k = k_cg_pupdate<T, 2>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, r, p, st);
-      break;
-    }
-    case 3: {
-      auto k = k_cg_pupdate<T, 3>;
-      k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, ld, r, p, st);
-      break;
-    }
-    default: return cudaErrorInvalidValue;
-  }
+  const bool vec = aligned16(r) && aligned16(p) && (nr == 1 || ld % Pack16<T>::W == 0);
+  return vec ? cg_pupdate_vec<T, true>(L, G, epr, nr, ld, r, p, st, lc)
+             : cg_pupdate_vec<T, false>(L, G, epr, nr, ld, r, p, st, lc);
+}
+
+cudaError_t launch_loop_start(const Launch& L, const LoopCtl& lc) {
+  (*L.counter) += 1;
+  k_loop_start<<<1, 32, 0, L.stream>>>(lc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_stats(const Launch& L, const CGState* st, int nseg, int kind,
+                               long long* acc) {
+  (*L.counter) += 1;
+  k_solve_stats<<<(nseg + 127) / 128, 128, 0, L.stream>>>(st, nseg, kind, acc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pin_shift(const Launch& L, const DSell& A, const DSeg& G, int epr, T* x,
+                             double* xp) {
+  (*L.counter) += 2;
+  k_pin_gather<T><<<(G.nseg * epr + 127) / 128, 128, 0, L.stream>>>(G, epr, x, xp);
+  auto k = k_pin_shift<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32 * epr, k), kBlock, 0, L.stream>>>(A, G, epr, x, xp);
   return cudaGetLastError();
 }
 
@@ -1122,16 +1397,17 @@ template <typename T>
 cudaError_t launch_cg_zero(const Launch& L, const DSeg& G, int epr, T* x, const CGState* st) {
   (*L.counter) += 1;
   auto k = k_cg_zero<T>;
-  k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, epr, x, st);
+  const ItemGrid ig = GSPM_IGRID(L, G, k);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, x, st);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Fv, const T* m,
-                        int64_t ld, T* b) {
+                        int64_t ld, T* b, int pin_zero) {
   (*L.counter) += 1;
   auto k = k_fdiv<T>;
-  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Fv, m, ld, b);
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Fv, m, ld, b, pin_zero);
   return cudaGetLastError();
 }
 
@@ -1156,10 +1432,10 @@ cudaError_t launch_fstrain(const Launch& L, const DSell& A, const DSeg& G, const
 
 template <typename T>
 cudaError_t launch_gdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Gv,
-                        const T* sig0, T* b) {
+                        const T* sig0, T* b, int pin_zero) {
   (*L.counter) += 1;
   auto k = k_gdiv<T>;
-  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Gv, sig0, b);
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Gv, sig0, b, pin_zero);
   return cudaGetLastError();
 }
 
@@ -1208,7 +1484,8 @@ cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* 
                            Red red) {
   (*L.counter) += 1;
   auto k = k_project<T>;
-  k<<<GSPM_IGRID(L, G, k), kBlock, 0, L.stream>>>(G, ld, x, mag, m, dm_out, inv_nmag, red);
+  const ItemGrid ig = GSPM_IGRID(L, G, k);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, ld, x, mag, m, dm_out, inv_nmag, red);
   return cudaGetLastError();
 }
 
@@ -1263,25 +1540,28 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
   template cudaError_t launch_spmv<T>(const Launch&, const DSell&, const T*, int, const T*, T*,   \
                                       int);                                                       \
   template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
-                                         const T*, T*, T*, T*, CGState*, int*, double, int, Red); \
+                                         const T*, T*, T*, T*, CGState*, int*, double, int, Red,  \
+                                         const double*, int);                                     \
   template cudaError_t launch_cg_init_gs<T>(const Launch&, const DSell&, const DSeg&, const T*,   \
                                             const T*, int, int64_t, T*, T*, T*, CGState*, int*,   \
                                             double, int, Red);                                    \
   template cudaError_t launch_cg_spmv<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
-                                         int, int64_t, const T*, T*, CGState*, Red, int);         \
+                                         int, int64_t, const T*, T*, CGState*, Red, int, int);    \
   template cudaError_t launch_cg_update<T>(const Launch&, const DSeg&, int, int, int64_t, T*, T*, \
                                            const T*, const T*, CGState*, int*, Red);              \
   template cudaError_t launch_cg_pupdate<T>(const Launch&, const DSeg&, int, int, int64_t,        \
-                                            const T*, T*, const CGState*);                        \
+                                            const T*, T*, const CGState*, const LoopCtl&);        \
   template cudaError_t launch_cg_zero<T>(const Launch&, const DSeg&, int, T*, const CGState*);    \
   template cudaError_t launch_fdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
-                                      const T*, int64_t, T*);                                     \
+                                      const T*, int64_t, T*, int);                                \
   template cudaError_t launch_fgrad<T>(const Launch&, const DSell&, const T*, const T*,           \
                                        const double*, T*, int64_t);                               \
   template cudaError_t launch_fstrain<T>(const Launch&, const DSell&, const DSeg&, const T*,      \
                                          const T*, const double*, const double*, T*, int64_t);    \
   template cudaError_t launch_gdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
-                                      const T*, T*);                                              \
+                                      const T*, T*, int);                                         \
+  template cudaError_t launch_pin_shift<T>(const Launch&, const DSell&, const DSeg&, int, T*,     \
+                                           double*);                                              \
   template cudaError_t launch_e0<T>(const Launch&, int64_t, const T*, int64_t, const uint8_t*,    \
                                     const DevParams&, T*, T*);                                    \
   template cudaError_t launch_hfield<T>(const Launch&, int64_t, const DSeg&, const T*, const T*,  \

@@ -18,28 +18,34 @@ struct DSell {
 
 // Scratch for deterministic reductions: one partial per work item and component.
 struct Red {
-  double* partial;     // [nitems * kRedComp]
+  double* partial;     // [max items of any list * kRedComp]
 };
 
-// Segments (meshes of a batch) and the work items of the reducing kernels.  Segment s owns the
-// slices [seg_sl0[s], seg_sl0[s] + ...) and the rows [seg_row0[s], seg_row0[s] + seg_nrow[s]);
-// its last slice may end in padding rows.  Items are grouped by segment: items
-// seg_item0[s] .. seg_item0[s] + seg_nitems[s] - 1 cover its slices, item i the slices
-// [item_sl0[i], item_sl1[i]).  counter[s] is the arrival counter of segment s (kept at 0 between
-// kernels by the last arriving item).
+// Work items of the reducing kernels: item i covers the slices [sl0[i], sl1[i]) of segment
+// seg[i]; items are grouped by segment (segment s owns items seg_item0[s] .. + seg_nitems[s]).
+struct ItemList {
+  int nitems;
+  const int32_t* seg;        // [nitems]
+  const int32_t* sl0;        // [nitems]
+  const int32_t* sl1;        // [nitems]
+  const int32_t* seg_item0;  // [nseg]
+  const int32_t* seg_nitems; // [nseg]
+};
+constexpr int kItemLists = 8;  // one list per residency 1..8 blocks per SM
+
+// Segments (meshes of a batch).  Segment s owns the rows [seg_row0[s], seg_row0[s] +
+// seg_nrow[s]) (its last slice may end in padding rows).  A reducing kernel that keeps k blocks
+// resident per SM uses list[k - 1], which holds about k x SMs items (at least one per segment,
+// otherwise proportional to the segment's slices), so every block of its single wave reduces
+// one item.  counter[s] is the arrival counter of segment s, 0 between kernels.
 struct DSeg {
   int nseg;
-  int nitems;
   const int32_t* seg_of_slice;  // [nslices]
-  const int32_t* item_seg;      // [nitems]
-  const int32_t* item_sl0;      // [nitems]
-  const int32_t* item_sl1;      // [nitems]
-  const int32_t* seg_item0;     // [nseg]
-  const int32_t* seg_nitems;    // [nseg]
   const int64_t* seg_row0;      // [nseg]
   const int64_t* seg_nrow;      // [nseg]
   const int64_t* seg_pin;       // [nseg] pinned row (global internal index)
   unsigned* counter;            // [nseg]
+  ItemList list[kItemLists];
 };
 constexpr int kRedComp = 16;
 constexpr int kBlock = 256;
@@ -60,6 +66,20 @@ struct DevParams {
   double kappa, me_coef, l100, l111, C11, C12, C44;
   double Nd[9];
   double dtau, alpha;
+  double R[9];   // App. D: v_mesh = R v_crystal (C11, C12, C44, lambda, K1 in crystal axes)
+  int rotated;   // R is not the identity
+};
+
+// Device-side loop control of a CG loop replayed as a CUDA-graph WHILE node.  After each
+// iteration one thread sets the node's condition to (active segments > 0 and iterations < limit),
+// so the loop ends when every segment has converged (or stopped at max_iter) and never runs more
+// than `limit` times.  count == NULL: not in a graph (launched directly).
+struct LoopCtl {
+  cudaGraphConditionalHandle handle;
+  const int* nactive;
+  int* count;                 // iterations of the current loop
+  int limit;
+  unsigned long long* total;  // iterations of all loops (launch accounting)
 };
 
 struct Launch {
@@ -96,10 +116,12 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
                         T* y, int variant = 0);  // B = 1 scalar, B = 9 block (x, y AoS 3)
 // CG pieces.  st and the arrival counters are per segment; nactive counts active segments.
 // epr = elements per row of the vectors (1: scalar, SoA with stride ld; 3: [n][3]).
+// bmean != NULL: solve the consistent singular system with b projected off the constants
+// (bmean = per-segment mean of each component); pinned: the pinned system (Sec. 2.5).
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
-                           int max_iter, Red red);
+                           int max_iter, Red red, const double* bmean, int pinned);
 template <typename T>
 cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
                               const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
@@ -107,19 +129,29 @@ cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, co
 template <typename T>
 cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
-                           int variant);
+                           int variant, int pinned);
+// x(i, c) -= x(pin of i's segment, c) for x[i * epr + c]; xp: nseg * epr doubles of scratch
+template <typename T>
+cudaError_t launch_pin_shift(const Launch& L, const DSell& A, const DSeg& G, int epr, T* x,
+                             double* xp);
 template <typename T>
 cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
                              T* r, const T* p, const T* q, CGState* st, int* nactive, Red red);
 template <typename T>
 cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
-                              const T* r, T* p, const CGState* st);
+                              const T* r, T* p, const CGState* st, const LoopCtl& lc);
+// Graph loops: reset the iteration count and set the WHILE condition to (nactive > 0).
+cudaError_t launch_loop_start(const Launch& L, const LoopCtl& lc);
+// Add one solve's iterations (kind 0 K^ms, 1 K^mech: the largest over right-hand sides;
+// 2 GS: their sum) and non-converged count to acc[4 * seg + kind] and acc[4 * seg + 3].
+cudaError_t launch_solve_stats(const Launch& L, const CGState* st, int nseg, int kind,
+                               long long* acc);
 template <typename T>
 cudaError_t launch_cg_zero(const Launch& L, const DSeg& G, int epr, T* x, const CGState* st);
 
 template <typename T>
 cudaError_t launch_fdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Fv, const T* m,
-                        int64_t ld, T* b);
+                        int64_t ld, T* b, int pin_zero);
 template <typename T>
 cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U,
                          const double* invML, T* hd, int64_t ld);
@@ -129,7 +161,7 @@ cudaError_t launch_fstrain(const Launch& L, const DSell& A, const DSeg& G, const
                            int64_t ld);
 template <typename T>
 cudaError_t launch_gdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Gv,
-                        const T* sig0, T* b);
+                        const T* sig0, T* b, int pin_zero);
 template <typename T>
 cudaError_t launch_e0(const Launch& L, int64_t n, const T* m, int64_t ld, const uint8_t* mag,
                       const DevParams& P, T* E0, T* sig0);

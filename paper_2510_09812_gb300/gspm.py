@@ -18,7 +18,8 @@ OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE = range(8)
 HOST, DEVICE = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
 ORDER_NONE, ORDER_RCM = 0, 1
-FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE = 1, 2, 4
+FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE, FLAG_GRAPH, FLAG_PINNED_CG = 1, 2, 4, 8, 16
+FLAG_RESOLVE_AT_MSTAR = 32
 EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC, \
     EXPORT_LUMPED_MASS = range(6)
 FIELD_M, FIELD_U, FIELD_DISP, FIELD_HD, FIELD_STRAIN, FIELD_H, FIELD_DISP_PREV = range(7)
@@ -49,7 +50,7 @@ class Material(C.Structure):
                 ("lambda100", C.c_double), ("lambda111", C.c_double), ("C11", C.c_double),
                 ("C12", C.c_double), ("C44", C.c_double), ("Nd", C.c_double * 9),
                 ("sigma_ext", C.c_double * 6), ("gamma0", C.c_double), ("mu0", C.c_double),
-                ("l_d", C.c_double)]
+                ("l_d", C.c_double), ("R", C.c_double * 9)]
 
 
 class Options(C.Structure):
@@ -103,6 +104,7 @@ def _load():
         "gspm_profile_read": (C.c_int, [vp, C.c_int, _dp, C.POINTER(C.c_int64)]),
         "gspm_volume_avg_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, vp, vp]),
         "gspm_set_x0_mode": (C.c_int, [vp, C.c_int]),
+        "gspm_set_graph": (C.c_int, [vp, C.c_int]),
         "gspm_batch_load": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
                                       C.POINTER(Options), C.POINTER(vp)]),
         "gspm_batch_segment": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int64),
@@ -173,6 +175,7 @@ def material_struct(mat: dict) -> Material:
     m.gamma0 = float(mat.get("gamma0", 0.0))
     m.mu0 = float(mat.get("mu0", 0.0))
     m.l_d = float(mat.get("l_d", 0.0))
+    m.R[:] = [float(v) for v in np.asarray(mat.get("R", np.zeros(9)), dtype=np.float64).reshape(-1)]
     return m
 
 
@@ -182,7 +185,7 @@ class Context:
     def __init__(self, mesh, material: dict, dt: float, alpha: float, precision: str = "f64",
                  ordering: str = "none", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
                  max_iter=20000, row2_printed=False, host_only=False, stream=0, wrap_tol=0.0,
-                 autotune=True):
+                 autotune=True, graph=False, pinned_cg=False, resolve_at_mstar=False):
         """One mesh, or a batch when `mesh` is a list (gspm_batch_load)."""
         meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
@@ -207,7 +210,9 @@ class Context:
         o.rtol_gs, o.rtol_ms, o.rtol_mech = float(rtol_gs), float(rtol_ms), float(rtol_mech)
         o.max_iter = int(max_iter)
         o.flags = ((FLAG_ROW2_PRINTED if row2_printed else 0) | (FLAG_HOST_ONLY if host_only else 0)
-                   | (0 if autotune else FLAG_NO_AUTOTUNE))
+                   | (0 if autotune else FLAG_NO_AUTOTUNE) | (FLAG_GRAPH if graph else 0)
+                   | (FLAG_PINNED_CG if pinned_cg else 0)
+                   | (FLAG_RESOLVE_AT_MSTAR if resolve_at_mstar else 0))
         o.stream = C.c_void_p(int(stream))
         h = C.c_void_p()
         mat = material_struct(material)
@@ -356,6 +361,10 @@ class Context:
         return int(lib.gspm_launch_count(self._h))
 
     # ---- learned warm start
+    def set_graph(self, on: bool):
+        """Replay each step as one captured CUDA graph (``gspm_set_graph``)."""
+        _check(lib.gspm_set_graph(self._h, int(bool(on))), "gspm_set_graph")
+
     def set_x0_mode(self, mode: int):
         _check(lib.gspm_set_x0_mode(self._h, int(mode)), "gspm_set_x0_mode")
 

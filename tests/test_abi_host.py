@@ -102,3 +102,17 @@ def test_invalid_meshes_are_rejected(gspm_lib):
     with pytest.raises(gspm_lib.GSPMError) as e:
         gspm_lib.Context(mesh, mat, -1.0, 0.5, host_only=True)       # dt <= 0
     assert e.value.code == gspm_lib.EINVAL
+
+
+def test_rotation_must_be_proper(gspm_lib):
+    mesh = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    for R in (np.diag([1.0, 1.0, -1.0]), np.diag([1.0, 2.0, 1.0])):   # reflection, not orthogonal
+        mat = synth.fe_like_material()
+        mat["R"] = R.reshape(-1).tolist()
+        with pytest.raises(gspm_lib.GSPMError) as e:
+            gspm_lib.Context(mesh, mat, 1e-12, 0.5, host_only=True)
+        assert e.value.code == gspm_lib.EINVAL and "rotation" in str(e.value)
+    mat = synth.fe_like_material()
+    c, s_ = np.cos(0.3), np.sin(0.3)
+    mat["R"] = [c, -s_, 0.0, s_, c, 0.0, 0.0, 0.0, 1.0]
+    gspm_lib.Context(mesh, mat, 1e-12, 0.5, host_only=True).close()

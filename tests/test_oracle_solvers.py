@@ -58,3 +58,33 @@ def test_gs_solve_fourier_mode_closed_form():
     for c, A in [(1.0, s.A_eps), (0.5, s.A_aeps)]:
         g, it, rel = s.gs_solve(A, f, 1e-14)
         assert np.allclose(g, lM / (lM + c * s.red.eps * lK) * f, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("which", ["ms", "mech"])
+def test_pinned_solution_solves_the_unpinned_periodic_system(c0_system, which):
+    """Sec. 2.5 pins node 0 so that K becomes SPD.  The CUDA path instead solves the consistent
+    singular system K x = b (b with zero sum per component, as every divergence-form right-hand
+    side on the periodic mesh has) and subtracts the constant that makes node 0 zero.  Both give
+    the pinned system's solution: checked here with a dense direct solve of the pinned system,
+    which must satisfy every row of the unpinned one (node 0's included), and with the oracle's
+    CG on the singular system after the shift."""
+    s = c0_system
+    m = synth.random_unit_m(s.n, 21)
+    m[~s.mag] = 0.0
+    if which == "ms":
+        K_raw, K_pin, d = s.K_ms_raw, s.K_ms, 1
+        b = sum(s.F[a] @ m[:, a] for a in range(3))
+    else:
+        K_raw, K_pin, d = s.K_mech_raw, s.K_mech, 3
+        b = s.F_mech @ s.e0_nodal(m).reshape(-1)
+    # divergence form: zero sum per component up to rounding
+    assert np.abs(b.reshape(-1, d).sum(0)).max() < 1e-12 * np.abs(b).sum()
+    bp = b.copy()
+    bp[:d] = 0.0
+    xp = np.linalg.solve(K_pin.toarray(), bp)
+    assert np.all(xp[:d] == 0.0)
+    assert np.abs(K_raw @ xp - b).max() < 1e-10 * np.abs(b).max()
+    bs = (b.reshape(-1, d) - b.reshape(-1, d).mean(0)).reshape(-1)
+    xs, it, rel = cg(K_raw, bs, np.zeros_like(bs), 1e-13, 20000)
+    xs = (xs.reshape(-1, d) - xs.reshape(-1, d)[0]).reshape(-1)
+    assert np.abs(xs - xp).max() < 1e-9 * np.abs(xp).max()
