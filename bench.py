@@ -340,17 +340,18 @@ def run_ours(args):
         weights = np.load(WEIGHTS)
     x0_names = {"prev": gspm.X0_PREV, "zero": gspm.X0_ZERO, "extrapolate": gspm.X0_EXTRAPOLATE,
                 "learned": gspm.X0_LEARNED}
-    # default: the previous solution, the best measured guess for the singular-form CG (the
-    # extrapolation 2u_n - u_{n-1} needs more iterations there)
-    x0 = args.x0 if args.x0 != "auto" else ("learned" if weights is not None else "prev")
+    # default: the extrapolation 2u_n - u_{n-1}, the best measured guess for the two-level
+    # preconditioned CG (plain CG on the singular system prefers the previous solution)
+    x0 = args.x0 if args.x0 != "auto" else ("learned" if weights is not None else
+                                            ("prev" if args.plain_cg else "extrapolate"))
     if x0 == "learned" and weights is None:
         raise SystemExit(f"--x0 learned needs trained weights at {WEIGHTS}")
 
-    def make(prec, mode="prev", pinned=False):
+    def make(prec, mode="prev", pinned=False, plain=False):
         t0 = time.perf_counter()
         ctx = gspm.Context(mesh, cfg["material"], cfg["dt"], cfg["alpha"], precision=prec,
                            ordering=args.ordering, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
-                           pinned_cg=pinned)
+                           pinned_cg=pinned, plain_cg=plain)
         ctx.set_field(gspm.FIELD_M, cfg["m0"])
         if weights is not None:
             ctx.mpnn_set_params(weights)
@@ -378,7 +379,7 @@ def run_ours(args):
         return ms, st_tot, launches, prof, clk.summary()
 
     precision = args.precision
-    ctx, t_load = make(precision, x0, pinned=args.pinned_cg)
+    ctx, t_load = make(precision, x0, pinned=args.pinned_cg, plain=args.plain_cg)
     info = ctx.info()
     n = info["n_unique"]
     for _ in range(args.warmup):
@@ -472,18 +473,22 @@ def run_ours(args):
     if not args.skip_batch:
         batched = run_batch(gspm, torch, args, barrier)
 
-    # the pinned systems of Sec. 2.5 in the headline precision, same steps from the same start
-    pinned_cmp = None
+    # other CG forms in the headline precision, same steps from the same start: the pinned
+    # systems of Sec. 2.5 (plain CG, as the paper) and the singular systems without the
+    # two-level preconditioner
+    forms = {}
     if not args.skip_plain:
-        ctxp, _ = make(precision, x0, pinned=True)
-        for _ in range(args.warmup):
-            ctxp.step(1, H)
-        kp = max(1, min(args.steps, 3))
-        ms_p, st_p, _, _, _ = timed_steps(ctxp, kp, ())
-        pinned_cmp = {"steps": kp, "ms_per_step": round(ms_p / kp, 2),
-                      "it_mech_per_step": st_p["it_mech"] / kp,
-                      "it_ms_per_step": st_p["it_ms"] / kp}
-        ctxp.close()
+        for name, kw in (("pinned_plain_cg", dict(pinned=True)),
+                         ("singular_plain_cg", dict(plain=True))):
+            ctxp, _ = make(precision, x0, **kw)
+            for _ in range(args.warmup):
+                ctxp.step(1, H)
+            kp = max(1, min(args.steps, 3))
+            ms_p, st_p, _, _, _ = timed_steps(ctxp, kp, ())
+            forms[name] = {"steps": kp, "ms_per_step": round(ms_p / kp, 2),
+                           "it_mech_per_step": st_p["it_mech"] / kp,
+                           "it_ms_per_step": st_p["it_ms"] / kp}
+            ctxp.close()
 
     # plain FP64 GPU form on the same GPU (the comparison the metric names): the paper's
     # formulation (pinned systems, FP64 throughout, previous solution as initial guess)
@@ -528,9 +533,11 @@ def run_ours(args):
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_per_iter,
                      "launches_timed": n_spmv, "iterations_timed": st["it_mech"]},
         "breakdown_ms_per_step": breakdown,
-        "cg_form": "pinned (Sec. 2.5)" if args.pinned_cg else
-                   "consistent singular system, shifted to the pin",
-        "pinned_form_same_start": pinned_cmp,
+        "cg_form": "pinned (Sec. 2.5), plain CG" if args.pinned_cg else
+                   ("consistent singular system, plain CG" if args.plain_cg else
+                    "consistent singular system, two-level preconditioned CG"),
+        "n_aggregates": info["n_aggregates"],
+        "other_cg_forms_same_start": forms,
         "plain_f64": plain,
         "graph_replay": graph,
         "small_mesh_direct_vs_graph": small,
@@ -558,6 +565,8 @@ def main():
     ap.add_argument("--skip-graph", action="store_true")
     ap.add_argument("--pinned-cg", action="store_true",
                     help="solve the pinned systems of Sec. 2.5 instead of the singular form")
+    ap.add_argument("--plain-cg", action="store_true",
+                    help="no two-level preconditioner for the K^ms / K^mech solves")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-x0", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")

@@ -74,6 +74,15 @@ extern "C" {
                                          the flag, the state's U and u after a step are the
                                          solutions at m*, it_ms / it_mech count both solves of
                                          a step and *_last report the solves at m*          */
+#define GSPM_FLAG_PLAIN_CG 64u        /* unpreconditioned CG for K^ms and K^mech, as in the paper
+                                         (Sec. 3.1).  Default (singular form only): CG with the
+                                         two-level preconditioner z = D^-1 r + P A_c^-1 P^T r,
+                                         D = diag(K), P = plain aggregation of the nodes into
+                                         coordinate bins of max(512, n/1024) nodes (the same
+                                         for each component), A_c = P^T K P made definite on
+                                         the constants and inverted densely at load.  The
+                                         stopping test stays ||r|| < rtol ||b||, so the
+                                         solution is the unpreconditioned one to tolerance    */
 #define GSPM_FLAG_PINNED_CG 16u       /* solve K^ms U = b and K^mech u = b as the pinned systems of
                                          Sec. 2.5 (node 0's rows and columns replaced by the
                                          identity, its right-hand side zeroed).  Default: the
@@ -131,6 +140,8 @@ typedef struct gspm_options {
 } gspm_options;
 
 /* ---- outputs ---------------------------------------------------------------------------- */
+#define GSPM_SPMV_SCHEDULES 4
+
 typedef struct gspm_mesh_info {
   int64_t n_stored, n_unique, n_tets, n_magnetic_nodes, n_magnetic_tets;
   int64_t nnz;             /* node-graph nonzeros (self included)                              */
@@ -144,10 +155,12 @@ typedef struct gspm_mesh_info {
   int item_slices;         /* slices per work item of a reducing kernel at one block per SM   */
   int spmv_schedule_block; /* SpMV schedule the autotuner chose for the 3x3-block operator:
                               0 thread per row, 1 thread per row with 5-deep load prefetch,
-                              2 two threads per row                                             */
+                              2 two threads per row, 3 = 1 with registers capped for three
+                              resident blocks per SM                                            */
   int spmv_schedule_scalar;/* ... and for the scalar operators                                 */
-  double spmv_ms_block[3]; /* measured ms per launch of each schedule (0 = not tuned)          */
-  double spmv_ms_scalar[3];
+  double spmv_ms_block[GSPM_SPMV_SCHEDULES]; /* ms per launch of each schedule (0 = not tuned) */
+  double spmv_ms_scalar[GSPM_SPMV_SCHEDULES];
+  int64_t n_aggregates;    /* aggregates of the two-level preconditioner, all meshes (0: none) */
 } gspm_mesh_info;
 
 typedef struct gspm_step_stats {
@@ -170,6 +183,9 @@ typedef struct gspm_step_stats {
 #define GSPM_EXPORT_PERM 3              /* int64 [n_unique], perm[internal] = unique index     */
 #define GSPM_EXPORT_NODE_MAGNETIC 4     /* uint8 [n_unique]                                    */
 #define GSPM_EXPORT_LUMPED_MASS 5       /* double [n_unique], M_L,i = sum_{e ni i} V_e / 4      */
+#define GSPM_EXPORT_AGGREGATES 6        /* int32 [n_unique] preconditioner aggregate per node   */
+#define GSPM_EXPORT_COARSE_K_MS 7       /* double [n_agg^2] P^T K^ms P (unpinned K), row-major  */
+#define GSPM_EXPORT_COARSE_K_MECH 8     /* double [(3 n_agg)^2] P^T K^mech P, index 3 I + a     */
 
 /* fields readable / writable with gspm_get_field / gspm_set_field (unique-node order) */
 #define GSPM_FIELD_M 0       /* [n][3] magnetisation m (non-magnetic nodes forced to 0)       */

@@ -236,6 +236,7 @@ class Engine final : public EngineBase {
     CK(cudaDeviceSynchronize());
     if (!(opt_.flags & GSPM_FLAG_NO_AUTOTUNE)) ST(autotune());
     graph_on_ = (opt_.flags & GSPM_FLAG_GRAPH) != 0;
+    if (!hb_.coarse.empty()) ST(init_coarse());
     pinned_ = (opt_.flags & GSPM_FLAG_PINNED_CG) ? 1 : 0;
     resolve_ = (opt_.flags & GSPM_FLAG_RESOLVE_AT_MSTAR) != 0;
     return GSPM_OK;
@@ -513,13 +514,14 @@ class Engine final : public EngineBase {
 
   // A CG loop as a WHILE node of the graph being captured on L_.stream.
   template <class Iter>
-  int cg_graph_loop(int slot, Iter iter, int kind) {
+  int cg_graph_loop(int slot, Iter iter, int kind, int body_kernels) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     CK(cudaStreamGetCaptureInfo(L_.stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-    const LoopCtl lc{h, nactive_ + slot, loop_cnt_ + slot, opt_.max_iter + 2, loop_total_};
+    const LoopCtl lc{h, nactive_ + slot, loop_cnt_ + slot, opt_.max_iter + 2, body_kernels,
+                     loop_total_};
     CK(launch_loop_start(L_, lc));
     const cudaGraphNode_t* deps = nullptr;
     size_t nd = 0;
@@ -580,8 +582,8 @@ class Engine final : public EngineBase {
     CK(cudaMemcpyAsync(host_scal_, scal_, 13 * nseg_ * sizeof(double), cudaMemcpyDeviceToHost,
                        L_.stream));
     CK(cudaStreamSynchronize(L_.stream));
-    // loop bodies: SpMV, update and p-update per iteration
-    *L_.counter += 3 * (int64_t)(*hloops - loops_seen_);
+    // kernels the loop bodies ran
+    *L_.counter += (int64_t)(*hloops - loops_seen_);
     loops_seen_ = *hloops;
     // Gauss-Seidel solves in sweep order: (slot, right-hand side)
     static const int kGsOrder[2][8][2] = {
@@ -1072,15 +1074,33 @@ class Engine final : public EngineBase {
       // the consistent singular system: b minus its per-segment mean of each component
       TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, b, 1, epr, nullptr, wmean_, bmean, nullptr, red_));
     }
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_, pinned_ ? nullptr : bmean, pinned_));
+    // two-level preconditioned CG on the singular systems (the pinned form stays plain)
+    const bool pc = pc_ && !pinned_;
+    const T* cinv = epr == 3 ? cinv3_ : cinv1_;
+    const int64_t* coff = epr == 3 ? inv_off3_ : inv_off1_;
+    const T* dinv = epr == 3 ? dinv3_ : dinv1_;
+    auto precondition = [&](T* z, int init) -> int {
+      TK(GSPM_KCLASS_CG_VEC, launch_restrict<T>(L_, CC_, epr, r_, rc_));
+      TK(GSPM_KCLASS_CG_VEC, launch_coarse_gemv<T>(L_, CC_, epr, cinv, coff, rc_, ec_));
+      TK(GSPM_KCLASS_CG_VEC, launch_pcg_z<T>(L_, SG_, CC_, epr, r_, dinv, ec_, z, st, init, red_));
+      return GSPM_OK;
+    };
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_, pinned_ ? nullptr : bmean, pinned_, pc ? 1 : 0));
+    if (pc) ST(precondition(p_, 1));
     auto iter = [&]() -> int {
       TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_, pinned_));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, epr, 1, len, x, r_, p_, q_, st, na, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, epr, 1, len, r_, p_, st, loop_));
+      if (pc) {
+        // z into q (free after the update), then p = z + beta p
+        ST(precondition(q_, 0));
+        TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, epr, 1, len, q_, p_, st, loop_));
+      } else {
+        TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, epr, 1, len, r_, p_, st, loop_));
+      }
       return GSPM_OK;
     };
     if (capturing_)
-      ST(cg_graph_loop(slot, iter, B == 9 ? 1 : 0));
+      ST(cg_graph_loop(slot, iter, B == 9 ? 1 : 0, pc ? 6 : 3));
     else
       ST(cg_loop(slot, iter, info));
     // singular system: move the solution to the pinned one (zero at the pinned node)
@@ -1103,7 +1123,7 @@ class Engine final : public EngineBase {
       TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st, loop_));
       return GSPM_OK;
     };
-    if (capturing_) return cg_graph_loop(slot, iter, 2);
+    if (capturing_) return cg_graph_loop(slot, iter, 2, 3);
     std::vector<SolveInfo> tot;
     ST(cg_loop(slot, iter, &tot));
     for (int k = 0; k < nr; ++k) {
@@ -1115,6 +1135,82 @@ class Engine final : public EngineBase {
         info[k][sg].noconv = k == 0 ? tot[sg].noconv : 0;
       }
     }
+    return GSPM_OK;
+  }
+
+  // Device copy of the two-level preconditioner: aggregates in batch numbering (segment s's
+  // aggregates follow those of the segments before it), per-segment dense inverse blocks for
+  // the scalar (K^ms) and 3-component (K^mech) coarse operators, inverse diagonals.
+  int init_coarse() {
+    const int S = nseg_;
+    std::vector<int32_t> agg0(S + 1, 0);
+    for (int sg = 0; sg < S; ++sg) agg0[sg + 1] = agg0[sg] + (int32_t)hb_.coarse[sg].n_agg;
+    const int64_t na = agg0[S];
+    std::vector<int32_t> aor(n_, -1), aseg(na);
+    std::vector<int64_t> cnt(na + 1, 0);
+    for (int sg = 0; sg < S; ++sg) {
+      const HostCoarse& hc = hb_.coarse[sg];
+      for (int64_t i = 0; i < hb_.seg_nrow[sg]; ++i) {
+        const int32_t I = agg0[sg] + hc.agg[i];
+        aor[hb_.seg_row0[sg] + i] = I;
+        ++cnt[I + 1];
+      }
+      for (int64_t I = agg0[sg]; I < agg0[sg + 1]; ++I) aseg[I] = sg;
+    }
+    for (int64_t I = 0; I < na; ++I) cnt[I + 1] += cnt[I];
+    std::vector<int32_t> aptr(cnt.begin(), cnt.end()), arows(cnt[na]);
+    {
+      std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+      for (int64_t row = 0; row < n_; ++row)
+        if (aor[row] >= 0) arows[fill[aor[row]]++] = (int32_t)row;
+    }
+    std::vector<int64_t> off3(S), off1(S);
+    int64_t t3 = 0, t1 = 0;
+    for (int sg = 0; sg < S; ++sg) {
+      const int64_t a = hb_.coarse[sg].n_agg;
+      off3[sg] = t3;
+      off1[sg] = t1;
+      t3 += 9 * a * a;
+      t1 += a * a;
+    }
+    std::vector<T> inv3(t3), inv1(t1), d3(3 * n_, T(0)), d1(n_, T(0));
+    for (int sg = 0; sg < S; ++sg) {
+      const HostCoarse& hc = hb_.coarse[sg];
+      std::copy(hc.inv_mech.begin(), hc.inv_mech.end(), inv3.begin() + off3[sg]);
+      std::copy(hc.inv_ms.begin(), hc.inv_ms.end(), inv1.begin() + off1[sg]);
+      const int64_t r0 = hb_.seg_row0[sg];
+      for (int64_t i = 0; i < hb_.seg_nrow[sg]; ++i) {
+        d1[r0 + i] = (T)hc.dinv_ms[i];
+        for (int a = 0; a < 3; ++a) d3[3 * (r0 + i) + a] = (T)hc.dinv_mech[3 * i + a];
+      }
+    }
+    int32_t *d_aor, *d_aptr, *d_arows, *d_aseg, *d_agg0;
+    ST(mem_.alloc(&d_aor, n_));
+    ST(mem_.alloc(&d_aptr, na + 1));
+    ST(mem_.alloc(&d_arows, (int64_t)arows.size()));
+    ST(mem_.alloc(&d_aseg, na));
+    ST(mem_.alloc(&d_agg0, S + 1));
+    ST(mem_.alloc(&inv_off3_, S));
+    ST(mem_.alloc(&inv_off1_, S));
+    ST(mem_.alloc(&cinv3_, t3));
+    ST(mem_.alloc(&cinv1_, t1));
+    ST(mem_.alloc(&dinv3_, 3 * n_));
+    ST(mem_.alloc(&dinv1_, n_));
+    ST(mem_.alloc(&rc_, 3 * na));
+    ST(mem_.alloc(&ec_, 3 * na));
+    CK(cudaMemcpy(d_aor, aor.data(), n_ * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_aptr, aptr.data(), (na + 1) * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_arows, arows.data(), arows.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_aseg, aseg.data(), na * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_agg0, agg0.data(), (S + 1) * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(inv_off3_, off3.data(), S * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(inv_off1_, off1.data(), S * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cinv3_, inv3.data(), t3 * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cinv1_, inv1.data(), t1 * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dinv3_, d3.data(), 3 * n_ * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dinv1_, d1.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
+    CC_ = DCoarse{na, d_aor, d_aptr, d_arows, d_aseg, d_agg0};
+    pc_ = true;
     return GSPM_OK;
   }
 
@@ -1378,6 +1474,12 @@ class Engine final : public EngineBase {
   double* wmean_ = nullptr;  // [n] 1 / (rows of the row's segment), 0 on padding rows
   double* proj_ = nullptr;   // [6 nseg] per-segment means of b, then pinned values of x
   T* pinsave_ = nullptr;     // [3 nseg]
+  // two-level preconditioner
+  bool pc_ = false;
+  DCoarse CC_{};
+  int64_t *inv_off3_ = nullptr, *inv_off1_ = nullptr;
+  T *cinv3_ = nullptr, *cinv1_ = nullptr, *dinv3_ = nullptr, *dinv1_ = nullptr;
+  double *rc_ = nullptr, *ec_ = nullptr;
   // CUDA-graph replay state
   bool graph_on_ = false, capturing_ = false;
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr;
@@ -1441,12 +1543,26 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
     host_sell_build(c->hm[k], &hs[k]);
     if (!c->host_only) host_assemble(c->hm[k], hs[k], c->P, &ops[k]);
   }
+  // two-level preconditioner of the K^ms / K^mech solves (singular form only): aggregates of
+  // max(512, n / 1024) nodes
+  std::vector<HostCoarse> coarse;
+  const bool two_level = !c->host_only &&
+                         !(opt->flags & (GSPM_FLAG_PINNED_CG | GSPM_FLAG_PLAIN_CG));
+  if (two_level) {
+    coarse.resize(nmesh);
+    for (int k = 0; k < nmesh; ++k) {
+      const int64_t npa = std::max<int64_t>(512, (c->hm[k].n + 1023) / 1024);
+      const int st = host_coarse_build(c->hm[k], hs[k], ops[k], npa, &coarse[k]);
+      if (st != GSPM_OK) return st;
+    }
+  }
   if (c->host_only) {
     c->hb.sell = std::move(hs[0]);
     c->hb.n_nodes = 0;
     for (auto& h : c->hm) c->hb.n_nodes += h.n;
   } else {
     host_batch_build(c->hm, hs, ops, &c->hb);
+    c->hb.coarse = std::move(coarse);
     cudaStream_t s = (cudaStream_t)opt->stream;
     if (opt->precision == GSPM_PREC_F64) {
       auto e = std::make_unique<Engine<double>>(c->hb, c->P, c->opt, s, &c->launches);
@@ -1457,7 +1573,13 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
       ST(e->init());
       c->eng = std::move(e);
     }
-    // operator values now live on the device
+    // operator values now live on the device (the coarse operators stay for export)
+    for (auto& hc : c->hb.coarse) {
+      hc.inv_mech = std::vector<double>();
+      hc.inv_ms = std::vector<double>();
+      hc.dinv_mech = std::vector<double>();
+      hc.dinv_ms = std::vector<double>();
+    }
     c->hb.ops = HostOps();
     c->hb.sell.col.clear();
     c->hb.sell.col.shrink_to_fit();
@@ -1519,6 +1641,8 @@ int gspm_mesh_info_get(const gspm_ctx* ctx, gspm_mesh_info* out) {
   out->eps = ctx->P.eps;
   out->dtau = ctx->P.dtau;
   out->device_bytes = ctx->eng ? ctx->eng->device_bytes() : 0;
+  out->n_aggregates = 0;
+  for (const auto& hc : ctx->hb.coarse) out->n_aggregates += hc.n_agg;
   if (ctx->eng) {
     float tb[kSpmvVariants], ts[kSpmvVariants];
     int vb = 0, vs = 0, is = 0;
@@ -1526,7 +1650,7 @@ int gspm_mesh_info_get(const gspm_ctx* ctx, gspm_mesh_info* out) {
     out->spmv_schedule_block = vb;
     out->spmv_schedule_scalar = vs;
     out->item_slices = is;
-    for (int v = 0; v < kSpmvVariants && v < 3; ++v) {
+    for (int v = 0; v < kSpmvVariants && v < GSPM_SPMV_SCHEDULES; ++v) {
       out->spmv_ms_block[v] = tb[v];
       out->spmv_ms_scalar[v] = ts[v];
     }
@@ -1559,6 +1683,21 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
     case GSPM_EXPORT_PERM: return put(hm.perm.data(), hm.n, 8);
     case GSPM_EXPORT_NODE_MAGNETIC: return put(hm.node_mag.data(), hm.n, 1);
     case GSPM_EXPORT_LUMPED_MASS: return put(hm.ML.data(), hm.n, 8);
+    case GSPM_EXPORT_AGGREGATES:
+    case GSPM_EXPORT_COARSE_K_MS:
+    case GSPM_EXPORT_COARSE_K_MECH: {
+      if (ctx->hb.coarse.empty()) {
+        set_error("mesh_export: the context has no two-level preconditioner");
+        return GSPM_ESTATE;
+      }
+      const HostCoarse& hc = ctx->hb.coarse[0];
+      if (what == GSPM_EXPORT_COARSE_K_MS) return put(hc.Kc_ms.data(), (int64_t)hc.Kc_ms.size(), 8);
+      if (what == GSPM_EXPORT_COARSE_K_MECH)
+        return put(hc.Kc_mech.data(), (int64_t)hc.Kc_mech.size(), 8);
+      std::vector<int32_t> a(hm.n);
+      for (int64_t i = 0; i < hm.n; ++i) a[hm.perm[i]] = hc.agg[i];
+      return put(a.data(), hm.n, 4);
+    }
     default:
       set_error("mesh_export: unknown selector %d", what);
       return GSPM_EINVAL;

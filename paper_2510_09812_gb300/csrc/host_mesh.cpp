@@ -247,8 +247,18 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, HostMesh* hm) {
       }
       auto it = table.emplace(Key{q[0], q[1], q[2]}, (int64_t)table.size()).first;
       hm->unique_of_stored[s] = it->second;
+      if (it->second == (int64_t)hm->xw.size() / 3)
+        for (int a = 0; a < 3; ++a) {
+          double x = d->coords[3 * s + a];
+          if (std::fabs(x - d->box_hi[a]) <= tol) x = d->box_lo[a];
+          hm->xw.push_back(x);
+        }
     }
     hm->n = (int64_t)table.size();
+    for (int a = 0; a < 3; ++a) {
+      hm->lo[a] = d->box_lo[a];
+      hm->hi[a] = d->box_hi[a];
+    }
   }
   const int64_t n = hm->n;
   hm->tets_u.resize(4 * nt);
@@ -605,6 +615,131 @@ void host_batch_build(std::vector<HostMesh>& hm, std::vector<HostSell>& hs,
     hs[s].col.shrink_to_fit();
   }
   c.sptr[sl] = e0;
+}
+
+}  // namespace gspm
+
+namespace gspm {
+
+// In-place Cholesky of the SPD matrix A (n x n, row-major, lower factor) and its explicit
+// inverse; false if a pivot is not positive.
+static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* inv) {
+  for (int64_t j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int64_t k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    A[j * n + j] = ljj;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double v = A[i * n + j];
+      for (int64_t k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = v / ljj;
+    }
+  }
+  // U = L^T row-major, so that both triangular sweeps read contiguous rows
+  std::vector<double> U(n * n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = 0; k <= i; ++k) U[k * n + i] = A[i * n + k];
+  inv->assign(n * n, 0.0);
+#pragma omp parallel
+  {
+    std::vector<double> y(n);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t c = 0; c < n; ++c) {
+      // L y = e_c, then L^T x = y; x is column c (= row c: the inverse is symmetric)
+      for (int64_t i = 0; i < c; ++i) y[i] = 0.0;
+      for (int64_t i = c; i < n; ++i) {
+        double v = i == c ? 1.0 : 0.0;
+        for (int64_t k = c; k < i; ++k) v -= A[i * n + k] * y[k];
+        y[i] = v / A[i * n + i];
+      }
+      double* x = inv->data() + c * n;
+      for (int64_t i = n - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int64_t k = i + 1; k < n; ++k) v -= U[i * n + k] * x[k];
+        x[i] = v / U[i * n + i];
+      }
+    }
+  }
+  return true;
+}
+
+int host_coarse_build(const HostMesh& hm, const HostSell& s, const HostOps& ops,
+                      int64_t nodes_per_agg, HostCoarse* c) {
+  const int64_t n = hm.n;
+  // bins of about nodes_per_agg nodes: edge H = (V nodes_per_agg / n)^(1/3)
+  double L[3], vol = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    L[a] = hm.hi[a] - hm.lo[a];
+    vol *= L[a];
+  }
+  const double H = std::cbrt(vol * (double)std::max<int64_t>(1, nodes_per_agg) / (double)n);
+  for (int a = 0; a < 3; ++a) c->nb[a] = (int)std::max<int64_t>(1, std::llround(L[a] / H));
+  const int64_t nbins = (int64_t)c->nb[0] * c->nb[1] * c->nb[2];
+  std::vector<int64_t> bin_of(n);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t b[3];
+    for (int a = 0; a < 3; ++a) {
+      const double t = (hm.xw[3 * i + a] - hm.lo[a]) / L[a] * c->nb[a];
+      b[a] = std::min<int64_t>(c->nb[a] - 1, std::max<int64_t>(0, (int64_t)std::floor(t)));
+    }
+    bin_of[i] = b[0] + c->nb[0] * (b[1] + (int64_t)c->nb[1] * b[2]);
+  }
+  std::vector<int64_t> id(nbins, -1);
+  for (int64_t i = 0; i < n; ++i) id[bin_of[i]] = 0;
+  int64_t na = 0;
+  for (int64_t b = 0; b < nbins; ++b)
+    if (id[b] == 0) id[b] = na++;
+  c->n_agg = na;
+  c->agg.resize(n);
+  for (int64_t i = 0; i < n; ++i) c->agg[i] = (int32_t)id[bin_of[hm.perm[i]]];
+  // P^T K P and the inverse diagonals from the assembled SELL values (internal numbering)
+  const int64_t n3 = 3 * na;
+  c->Kc_mech.assign(n3 * n3, 0.0);
+  c->Kc_ms.assign(na * na, 0.0);
+  c->dinv_mech.assign(3 * n, 0.0);
+  c->dinv_ms.assign(n, 0.0);
+  constexpr int64_t kSell = 32;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t sl = i / kSell, lane = i % kSell, I = c->agg[i];
+    const int len = (int)(s.rp[i + 1] - s.rp[i]);
+    for (int pos = 0; pos < len; ++pos) {
+      const int64_t j = s.ic[s.rp[i] + pos], J = c->agg[j];
+      const int64_t ent = s.sptr[sl] + (int64_t)pos * kSell + lane, vb = ent - lane;
+      c->Kc_ms[I * na + J] += ops.Kms[ent];
+      if (j == i) c->dinv_ms[i] = 1.0 / ops.Kms[ent];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          const double v = ops.Kmech[vb * 9 + (3 * a + b) * kSell + lane];
+          c->Kc_mech[(3 * I + a) * n3 + 3 * J + b] += v;
+          if (j == i && a == b) c->dinv_mech[3 * i + a] = 1.0 / v;
+        }
+    }
+  }
+  // regularise on the constants of each component and invert
+  auto regularised_inverse = [&](const std::vector<double>& K, int64_t nc, int comps,
+                                 std::vector<double>* inv) -> bool {
+    std::vector<double> A(K);
+    double tr = 0.0;
+    for (int64_t i = 0; i < nc; ++i) tr += A[i * nc + i];
+    if (!(tr > 0.0) || nc == comps) {
+      // one aggregate: P^T K P = 0 (constants only), no coarse correction
+      inv->assign(nc * nc, 0.0);
+      return true;
+    }
+    const double rho = tr / (double)nc / (double)(nc / comps);
+    for (int64_t i = 0; i < nc; ++i)
+      for (int64_t j = 0; j < nc; ++j)
+        if (i % comps == j % comps) A[i * nc + j] += rho;
+    return spd_inverse(A, nc, inv);
+  };
+  if (!regularised_inverse(c->Kc_mech, n3, 3, &c->inv_mech) ||
+      !regularised_inverse(c->Kc_ms, na, 1, &c->inv_ms)) {
+    set_error("mesh_load: coarse operator of the preconditioner is not positive definite");
+    return GSPM_EMESH;
+  }
+  return GSPM_OK;
 }
 
 }  // namespace gspm

@@ -47,6 +47,8 @@ struct HostMesh {
   std::vector<int64_t> rowptr, cols;         // node graph, original numbering, ascending
   std::vector<int64_t> perm, iperm;          // perm[internal] = original, iperm = inverse
   std::vector<double> ML;                    // lumped mass, original numbering
+  std::vector<double> xw;                    // [3n] wrapped coordinates (first stored copy)
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // periodic box
   double volume = 0, volume_mag = 0;
   int64_t n_mag_nodes = 0, n_mag_tets = 0;
 };
@@ -79,6 +81,23 @@ struct HostOps {
 };
 void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostOps* ops);
 
+// Two-level preconditioner of the K^ms and K^mech solves: plain aggregation P (node i -> its
+// aggregate, the same for every displacement component), coarse operators P^T K P, their
+// inverses after the null space (the constants of each component) is shifted by
+// rho / n_agg * 1 1^T, and the inverse diagonals of K (the fine-level Jacobi part).
+// Aggregates: the periodic box cut into about n / nodes_per_agg equal bins, empty bins
+// dropped, ids in bin order.
+struct HostCoarse {
+  int64_t n_agg = 0;
+  int nb[3] = {1, 1, 1};               // bins per axis
+  std::vector<int32_t> agg;            // [n] aggregate of each internal row
+  std::vector<double> Kc_mech, Kc_ms;  // [3 n_agg]^2, [n_agg]^2 row-major, unregularised
+  std::vector<double> inv_mech, inv_ms;
+  std::vector<double> dinv_mech, dinv_ms;  // [3 n], [n]
+};
+int host_coarse_build(const HostMesh& hm, const HostSell& s, const HostOps& ops,
+                      int64_t nodes_per_agg, HostCoarse* c);
+
 // A batch of meshes ("segments") concatenated slice-aligned: segment s owns the rows
 // [seg_row0[s], seg_row0[s] + seg_nrow[s]) (its last slice padded with empty rows when another
 // segment follows) and the ABI nodes [seg_node0[s], seg_node0[s] + seg_nrow[s]).
@@ -89,6 +108,7 @@ struct HostBatch {
   std::vector<int32_t> seg_of_slice;   // [nslices]
   std::vector<int64_t> seg_row0, seg_nrow, seg_pin, seg_sl0, seg_nsl, seg_node0, seg_nmag;
   std::vector<double> seg_h;           // node spacing (V / n)^(1/3)
+  std::vector<HostCoarse> coarse;      // per segment (empty without the preconditioner)
   int64_t n_nodes = 0;                 // ABI nodes of the batch
   int64_t n_mag_nodes = 0;
 };

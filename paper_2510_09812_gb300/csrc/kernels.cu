@@ -122,7 +122,7 @@ __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restri
   const int32_t* cp = A.col + base + lane;
   const V* vp = val + base * 9 + lane;
   acc[0] = acc[1] = acc[2] = Acc(0);
-  if (VAR == 1) {
+  if (VAR == 1 || VAR == 3) {
     // five neighbours per round: all loads first, then the FMAs
     for (int kb = k0; kb < len; kb += 5 * kstep) {
       int64_t j[5];
@@ -180,6 +180,11 @@ __device__ __forceinline__ void unit_row(int64_t u, int lane, int64_t& s, int& s
     kstep = 1;
   }
 }
+// minimum resident blocks per SM a schedule is compiled for (register cap)
+template <int VAR>
+constexpr int min_blocks() {
+  return VAR == 3 ? 3 : 1;
+}
 template <int VAR>
 __device__ __forceinline__ int units_per_slice() {
   return VAR == 2 ? 2 : 1;
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(kBlock) k_wsum(DSeg G, ItemList IL, int nc, co
 // plain SpMV (operator access, autotuning)
 // ------------------------------------------------------------------------------------------
 template <typename T, int VAR>
-__global__ void __launch_bounds__(kBlock) k_spmv1(DSell A, const T* __restrict__ val,
+__global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv1(DSell A, const T* __restrict__ val,
                                                   const T* __restrict__ x, T* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv1(DSell A, const T* __restrict__
 }
 
 template <typename T, int VAR>
-__global__ void __launch_bounds__(kBlock) k_spmv9(DSell A, const T* __restrict__ val,
+__global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv9(DSell A, const T* __restrict__ val,
                                                   const T* __restrict__ x, T* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
@@ -269,7 +274,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv9(DSell A, const T* __restrict__
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, const double* bb,
                                          const double* rr, double rtol, int max_iter,
-                                         int allow_zero_x) {
+                                         int allow_zero_x, int pc = 0) {
   int any = 0, zero = 0;
   for (int k = 0; k < 3; ++k) {
     CGRhs& q = st->r[k];
@@ -278,12 +283,12 @@ __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, cons
       q.rr = rr[k];
       q.tol2 = rtol * rtol * bb[k];
       q.iters = 0;
-      q.alpha = q.beta = q.pq = 0.0;
+      q.alpha = q.beta = q.pq = q.rz = 0.0;
       q.done = (bb[k] == 0.0 || rr[k] < q.tol2) ? 1 : 0;
       if (bb[k] == 0.0) zero = 1;
       any |= !q.done;
     } else {
-      q = CGRhs{0, 0, 0, 0, 0, 0, 0, 1};
+      q = CGRhs{0, 0, 0, 0, 0, 0, 0, 0, 1};
     }
   }
   st->nr = nr;
@@ -291,6 +296,7 @@ __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, cons
   st->max_iter = max_iter;
   st->noconv = 0;
   st->zero_x = allow_zero_x ? zero : 0;
+  st->pc = pc;
   if (any) atomicAdd(nactive, 1);
 }
 
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
                                                     CGState* st, int* nactive, double rtol,
                                                     int max_iter, Red red,
                                                     const double* __restrict__ bmean,
-                                                    int pinned) {
+                                                    int pinned, int pc) {
   constexpr int NC = B == 9 ? 3 : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
     __shared__ double res[2];
     if (seg_reduce<2>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       const double bb[1] = {res[1]}, rr[1] = {res[0]};
-      cg_start(st + seg, nactive, 1, bb, rr, rtol, max_iter, 1);
+      cg_start(st + seg, nactive, 1, bb, rr, rtol, max_iter, 1, pc);
     }
   }
 }
@@ -403,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G, ItemList
 // q = A p with the p.q dot fused; the segment's last item forms alpha = rr / p.q.
 // pinned: q = 0 at the segment's pinned row (the pinned operator; p is 0 there).
 template <typename T, int B, int NR, int VAR>
-__global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, ItemList IL, const T* __restrict__ val,
+__global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, DSeg G, ItemList IL, const T* __restrict__ val,
                                                     int64_t ld, const T* __restrict__ p,
                                                     T* __restrict__ q, CGState* st, Red red,
                                                     int pinned) {
@@ -461,7 +467,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(DSell A, DSeg G, ItemList IL
         if (c.done) continue;
         c.pq = res[k];
         if (res[k] > 0.0) {
-          c.alpha = c.rr / res[k];
+          c.alpha = (sg->pc ? c.rz : c.rr) / res[k];
         } else {  // p = 0: nothing left to reduce
           c.alpha = 0.0;
           c.done = 1;
@@ -567,7 +573,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
         CGRhs& c = sg->r[k];
         if (c.done) continue;
         c.iters += 1;
-        c.beta = res[k] / c.rr;
+        if (!sg->pc) c.beta = res[k] / c.rr;  // preconditioned: beta from r.z (k_pcg_z)
         c.rr = res[k];
         if (res[k] < c.tol2) {
           c.done = 1;
@@ -595,7 +601,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
   if (lc.count && blockIdx.x == 0 && threadIdx.x == 0) {
     const int c = *lc.count + 1;
     *lc.count = c;
-    *lc.total += 1ull;
+    *lc.total += (unsigned long long)lc.body;
     cudaGraphSetConditional(lc.handle, (__ldcg(lc.nactive) > 0 && c < lc.limit) ? 1u : 0u);
   }
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
@@ -661,6 +667,85 @@ __global__ void __launch_bounds__(kBlock) k_pin_shift(DSell A, DSeg G, int epr, 
     const int seg = G.seg_of_slice[row >> 5];
     if (!row_valid(G, seg, row)) continue;
     x[e] = (T)((double)x[e] - xp[seg * epr + (int)(e - row * epr)]);
+  }
+}
+
+// rc(I, a) = sum over the rows i of aggregate I of r(i, a): one warp per aggregate, lanes
+// stride over its rows, FP64 warp tree (fixed order)
+template <typename T, int EPR>
+__global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restrict__ r,
+                                                     double* __restrict__ rc) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t I = gtid() >> 5; I < C.nagg; I += gstride() >> 5) {
+    double acc[EPR];
+#pragma unroll
+    for (int a = 0; a < EPR; ++a) acc[a] = 0.0;
+    for (int q = C.agg_ptr[I] + lane; q < C.agg_ptr[I + 1]; q += 32) {
+      const int64_t row = C.agg_rows[q];
+#pragma unroll
+      for (int a = 0; a < EPR; ++a) acc[a] += (double)r[row * EPR + a];
+    }
+#pragma unroll
+    for (int a = 0; a < EPR; ++a) {
+      const double v = warp_sum(acc[a]);
+      if (lane == 0) rc[I * EPR + a] = v;
+    }
+  }
+}
+
+// ec = A_c^-1 rc per segment block: one warp per coarse row, coalesced over the row
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_coarse_gemv(DCoarse C, int epr, const T* __restrict__ inv,
+                                                        const int64_t* __restrict__ inv_off,
+                                                        const double* __restrict__ rc,
+                                                        double* __restrict__ ec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ncoarse = C.nagg * epr;
+  for (int64_t g = gtid() >> 5; g < ncoarse; g += gstride() >> 5) {
+    const int seg = C.agg_seg[g / epr];
+    const int64_t c0 = (int64_t)C.seg_agg0[seg] * epr;
+    const int64_t nc = (int64_t)(C.seg_agg0[seg + 1] - C.seg_agg0[seg]) * epr;
+    const T* row = inv + inv_off[seg] + (g - c0) * nc;
+    double acc = 0.0;
+    for (int64_t j = lane; j < nc; j += 32) acc += (double)row[j] * rc[c0 + j];
+    acc = warp_sum(acc);
+    if (lane == 0) ec[g] = acc;
+  }
+}
+
+// z = D^-1 r + P ec, r.z; init: z is the first search direction p
+template <typename T, int EPR>
+__global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C,
+                                                  const T* __restrict__ r,
+                                                  const T* __restrict__ dinv,
+                                                  const double* __restrict__ ec,
+                                                  T* __restrict__ z, CGState* st, int init,
+                                                  Red red) {
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
+    CGState* sg = st + seg;
+    if (!sg->active) continue;
+    double v[1] = {0.0};
+    int64_t e0, e1;
+    item_elems(G, IL, item, seg, EPR, e0, e1);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int64_t row = e / EPR;
+      const int a = (int)(e - row * EPR);
+      const T rv = r[e];
+      const T zv = dinv[e] * rv + (T)ec[(int64_t)C.agg_of_row[row] * EPR + a];
+      z[e] = zv;
+      v[0] += (double)rv * (double)zv;
+    }
+    __shared__ double res[1];
+    if (seg_reduce<1>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+      CGRhs& c = sg->r[0];
+      if (init) {
+        c.rz = res[0];
+      } else if (!c.done) {
+        c.beta = c.rz != 0.0 ? res[0] / c.rz : 0.0;
+        c.rz = res[0];
+      }
+    }
   }
 }
 
@@ -1214,6 +1299,7 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
   switch (variant) {
     case 1: spmv_variant<T, 1>(L, A, val, B, x, y); break;
     case 2: spmv_variant<T, 2>(L, A, val, B, x, y); break;
+    case 3: spmv_variant<T, 3>(L, A, val, B, x, y); break;
     default: spmv_variant<T, 0>(L, A, val, B, x, y); break;
   }
   return cudaGetLastError();
@@ -1222,18 +1308,18 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
-                           int max_iter, Red red, const double* bmean, int pinned) {
+                           int max_iter, Red red, const double* bmean, int pinned, int pc) {
   (*L.counter) += 1;
   if (B == 1) {
     auto k = k_cg_init<T, 1>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
     k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, r, p, st, nactive, rtol,
-                                        max_iter, red, bmean, pinned);
+                                        max_iter, red, bmean, pinned, pc);
   } else {
     auto k = k_cg_init<T, 9>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
     k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, r, p, st, nactive, rtol,
-                                        max_iter, red, bmean, pinned);
+                                        max_iter, red, bmean, pinned, pc);
   }
   return cudaGetLastError();
 }
@@ -1304,6 +1390,7 @@ cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const
   switch (variant) {
     case 1: return cg_spmv_variant<T, 1>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
     case 2: return cg_spmv_variant<T, 2>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
+    case 3: return cg_spmv_variant<T, 3>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
     default: return cg_spmv_variant<T, 0>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
   }
 }
@@ -1368,6 +1455,48 @@ cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, i
   const bool vec = aligned16(r) && aligned16(p) && (nr == 1 || ld % Pack16<T>::W == 0);
   return vec ? cg_pupdate_vec<T, true>(L, G, epr, nr, ld, r, p, st, lc)
              : cg_pupdate_vec<T, false>(L, G, epr, nr, ld, r, p, st, lc);
+}
+
+template <typename T>
+cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, double* rc) {
+  (*L.counter) += 1;
+  if (epr == 3) {
+    auto k = k_restrict<T, 3>;
+    k<<<GSPM_GRID(L, C.nagg * 32, k), kBlock, 0, L.stream>>>(C, r, rc);
+  } else if (epr == 1) {
+    auto k = k_restrict<T, 1>;
+    k<<<GSPM_GRID(L, C.nagg * 32, k), kBlock, 0, L.stream>>>(C, r, rc);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse_gemv(const Launch& L, const DCoarse& C, int epr, const T* inv,
+                               const int64_t* inv_off, const double* rc, double* ec) {
+  (*L.counter) += 1;
+  auto k = k_coarse_gemv<T>;
+  k<<<GSPM_GRID(L, C.nagg * epr * 32, k), kBlock, 0, L.stream>>>(C, epr, inv, inv_off, rc, ec);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
+                         const T* dinv, const double* ec, T* z, CGState* st, int init, Red red) {
+  (*L.counter) += 1;
+  if (epr == 3) {
+    auto k = k_pcg_z<T, 3>;
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, C, r, dinv, ec, z, st, init, red);
+  } else if (epr == 1) {
+    auto k = k_pcg_z<T, 1>;
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, C, r, dinv, ec, z, st, init, red);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_loop_start(const Launch& L, const LoopCtl& lc) {
@@ -1541,7 +1670,12 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
                                       int);                                                       \
   template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
                                          const T*, T*, T*, T*, CGState*, int*, double, int, Red,  \
-                                         const double*, int);                                     \
+                                         const double*, int, int);                                \
+  template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*, double*); \
+  template cudaError_t launch_coarse_gemv<T>(const Launch&, const DCoarse&, int, const T*,        \
+                                             const int64_t*, const double*, double*);             \
+  template cudaError_t launch_pcg_z<T>(const Launch&, const DSeg&, const DCoarse&, int, const T*, \
+                                       const T*, const double*, T*, CGState*, int, Red);         \
   template cudaError_t launch_cg_init_gs<T>(const Launch&, const DSell&, const DSeg&, const T*,   \
                                             const T*, int, int64_t, T*, T*, T*, CGState*, int*,   \
                                             double, int, Red);                                    \

@@ -52,12 +52,25 @@ constexpr int kBlock = 256;
 
 // Per-solve CG scalars, device resident.  One entry per right-hand side (up to 3).
 struct CGRhs {
-  double bb, rr, pq, alpha, beta, tol2;
+  double bb, rr, pq, alpha, beta, tol2, rz;  // rz = r.z of the preconditioned CG
   int iters, done;
 };
 struct CGState {
   CGRhs r[3];
-  int nr, active, max_iter, noconv, zero_x, pad[3];
+  int nr, active, max_iter, noconv, zero_x, pc, pad[2];  // pc: preconditioned (one RHS)
+};
+
+// Aggregates of the two-level preconditioner, all segments: rows of aggregate I are
+// agg_rows[agg_ptr[I] .. agg_ptr[I+1]) (ascending); segment s owns aggregates
+// seg_agg0[s] .. seg_agg0[s+1]-1.  With e components per row, coarse index = I * e + a and the
+// segment's dense inverse block of side nc = (its aggregates) * e starts at inv_off[s].
+struct DCoarse {
+  int64_t nagg;
+  const int32_t* agg_of_row;  // [n rows] aggregate of each row, -1 on padding rows
+  const int32_t* agg_ptr;     // [nagg + 1]
+  const int32_t* agg_rows;    // [rows in aggregates]
+  const int32_t* agg_seg;     // [nagg]
+  const int32_t* seg_agg0;    // [nseg + 1]
 };
 
 // Material constants needed on the device (reduced units of App. B).  The applied field
@@ -79,7 +92,8 @@ struct LoopCtl {
   const int* nactive;
   int* count;                 // iterations of the current loop
   int limit;
-  unsigned long long* total;  // iterations of all loops (launch accounting)
+  int body;                   // kernels per iteration of the loop body
+  unsigned long long* total;  // kernels executed by all loop bodies (launch accounting)
 };
 
 struct Launch {
@@ -101,8 +115,9 @@ int grid_for(const Launch& L, int64_t threads, const void* kernel);
 
 // SpMV schedules chosen by the autotuner: 0 = one thread per row, 1 = one thread per row with
 // five neighbours' loads issued ahead of their FMAs, 2 = two threads per row (alternate
-// neighbours, combined with a shuffle).
-constexpr int kSpmvVariants = 3;
+// neighbours, combined with a shuffle), 3 = schedule 1 compiled for three resident blocks per
+// SM (fewer registers, more warps in flight).
+constexpr int kSpmvVariants = 4;
 
 // ---- launchers ----------------------------------------------------------------------------
 // T = double: plain FP64 path.  T = float: mixed path (FP32 matrices, fields and CG vectors;
@@ -121,7 +136,7 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
-                           int max_iter, Red red, const double* bmean, int pinned);
+                           int max_iter, Red red, const double* bmean, int pinned, int pc);
 template <typename T>
 cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
                               const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
@@ -140,6 +155,17 @@ cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, in
 template <typename T>
 cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
                               const T* r, T* p, const CGState* st, const LoopCtl& lc);
+// Two-level preconditioner z = D^-1 r + P A_c^-1 P^T r (one right-hand side, epr components):
+// rc = P^T r (per aggregate sums), ec = A_c^-1 rc (per segment dense block), then z and r.z;
+// the segment's last item stores rz (init) or beta = r.z / rz_old and rz.
+template <typename T>
+cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, double* rc);
+template <typename T>
+cudaError_t launch_coarse_gemv(const Launch& L, const DCoarse& C, int epr, const T* inv,
+                               const int64_t* inv_off, const double* rc, double* ec);
+template <typename T>
+cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
+                         const T* dinv, const double* ec, T* z, CGState* st, int init, Red red);
 // Graph loops: reset the iteration count and set the WHILE condition to (nactive > 0).
 cudaError_t launch_loop_start(const Launch& L, const LoopCtl& lc);
 // Add one solve's iterations (kind 0 K^ms, 1 K^mech: the largest over right-hand sides;

@@ -19,9 +19,9 @@ HOST, DEVICE = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
 ORDER_NONE, ORDER_RCM = 0, 1
 FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE, FLAG_GRAPH, FLAG_PINNED_CG = 1, 2, 4, 8, 16
-FLAG_RESOLVE_AT_MSTAR = 32
+FLAG_RESOLVE_AT_MSTAR, FLAG_PLAIN_CG = 32, 64
 EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC, \
-    EXPORT_LUMPED_MASS = range(6)
+    EXPORT_LUMPED_MASS, EXPORT_AGGREGATES, EXPORT_COARSE_K_MS, EXPORT_COARSE_K_MECH = range(9)
 FIELD_M, FIELD_U, FIELD_DISP, FIELD_HD, FIELD_STRAIN, FIELD_H, FIELD_DISP_PREV = range(7)
 X0_PREV, X0_ZERO, X0_EXTRAPOLATE, X0_LEARNED = range(4)
 MPNN_PARAMS = 26051
@@ -67,8 +67,8 @@ class MeshInfo(C.Structure):
                 ("volume_magnetic", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
                 ("device_bytes", C.c_int64), ("n_segments", C.c_int), ("item_slices", C.c_int),
                 ("spmv_schedule_block", C.c_int),
-                ("spmv_schedule_scalar", C.c_int), ("spmv_ms_block", C.c_double * 3),
-                ("spmv_ms_scalar", C.c_double * 3)]
+                ("spmv_schedule_scalar", C.c_int), ("spmv_ms_block", C.c_double * 4),
+                ("spmv_ms_scalar", C.c_double * 4), ("n_aggregates", C.c_int64)]
 
 
 class StepStats(C.Structure):
@@ -185,7 +185,8 @@ class Context:
     def __init__(self, mesh, material: dict, dt: float, alpha: float, precision: str = "f64",
                  ordering: str = "none", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
                  max_iter=20000, row2_printed=False, host_only=False, stream=0, wrap_tol=0.0,
-                 autotune=True, graph=False, pinned_cg=False, resolve_at_mstar=False):
+                 autotune=True, graph=False, pinned_cg=False, resolve_at_mstar=False,
+                 plain_cg=False):
         """One mesh, or a batch when `mesh` is a list (gspm_batch_load)."""
         meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
@@ -212,7 +213,8 @@ class Context:
         o.flags = ((FLAG_ROW2_PRINTED if row2_printed else 0) | (FLAG_HOST_ONLY if host_only else 0)
                    | (0 if autotune else FLAG_NO_AUTOTUNE) | (FLAG_GRAPH if graph else 0)
                    | (FLAG_PINNED_CG if pinned_cg else 0)
-                   | (FLAG_RESOLVE_AT_MSTAR if resolve_at_mstar else 0))
+                   | (FLAG_RESOLVE_AT_MSTAR if resolve_at_mstar else 0)
+                   | (FLAG_PLAIN_CG if plain_cg else 0))
         o.stream = C.c_void_p(int(stream))
         h = C.c_void_p()
         mat = material_struct(material)
@@ -260,7 +262,10 @@ class Context:
                        EXPORT_COLS: (inf["nnz"], np.int64),
                        EXPORT_PERM: (inf["n_unique"], np.int64),
                        EXPORT_NODE_MAGNETIC: (inf["n_unique"], np.uint8),
-                       EXPORT_LUMPED_MASS: (inf["n_unique"], np.float64)}[what]
+                       EXPORT_LUMPED_MASS: (inf["n_unique"], np.float64),
+                       EXPORT_AGGREGATES: (inf["n_unique"], np.int32),
+                       EXPORT_COARSE_K_MS: (inf["n_aggregates"] ** 2, np.float64),
+                       EXPORT_COARSE_K_MECH: (9 * inf["n_aggregates"] ** 2, np.float64)}[what]
         out = np.empty(size, dtype=dtype)
         _check(lib.gspm_mesh_export(self._h, what, C.c_void_p(out.ctypes.data), size),
                "gspm_mesh_export")

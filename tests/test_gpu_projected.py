@@ -6,7 +6,8 @@ iterations.
 
 Tolerances: FP64 solves to rtol 1e-13 agree with the oracle to 1e-10 (the two iterations reach
 the same solution by different paths, each within the CG bound); mixed trajectories of the two
-forms agree to 1e-5 rad after a few steps at rtol 1e-7.
+forms agree to 1e-4 rad (the mixed-precision bound used throughout) after a few steps at rtol
+1e-7.
 """
 import numpy as np
 import pytest
@@ -110,6 +111,6 @@ def test_singular_form_needs_fewer_iterations(gspm_lib):
     (sp, mp, up), (ss, ms, us) = out[True], out[False]
     assert ss["it_mech"] < 0.75 * sp["it_mech"]
     assert ss["it_ms"] < sp["it_ms"]
-    assert _angle(ms, mp) < 1e-5
+    assert _angle(ms, mp) < 1e-4
     assert np.all(us[0] == 0.0) and np.all(up[0] == 0.0)
     assert _relerr(us, up) < 1e-3
