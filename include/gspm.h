@@ -82,7 +82,9 @@ extern "C" {
                                          for each component), A_c = P^T K P made definite on
                                          the constants and inverted densely at load.  The
                                          stopping test stays ||r|| < rtol ||b||, so the
-                                         solution is the unpreconditioned one to tolerance    */
+                                         solution is the unpreconditioned one to tolerance.
+                                         The GSPM solves (M + c eps K) g = M f use Jacobi
+                                         (z = D^-1 r) unless this flag or PINNED_CG is set    */
 #define GSPM_FLAG_PINNED_CG 16u       /* solve K^ms U = b and K^mech u = b as the pinned systems of
                                          Sec. 2.5 (node 0's rows and columns replaced by the
                                          identity, its right-hand side zeroed).  Default: the

@@ -154,6 +154,27 @@ class Engine final : public EngineBase {
     ST(upload(&F_, ops.F));
     ST(upload(&G_, ops.G));
     ST(upload(&Kmech_, ops.Kmech));
+    // inverse diagonals of M + eps K and M + alpha eps K (Jacobi preconditioner of the GSPM
+    // solves): a row's diagonal is the sum of its entries in its own column (SELL padding
+    // entries point at the row itself and hold 0)
+    if (!(opt_.flags & (GSPM_FLAG_PLAIN_CG | GSPM_FLAG_PINNED_CG))) {
+      std::vector<double> de(n, 0.0), da(n, 0.0);
+      for (int64_t sl = 0; sl < nslices_; ++sl)
+        for (int k = 0; k < hs.slen[sl]; ++k)
+          for (int lane = 0; lane < 32; ++lane) {
+            const int64_t row = sl * 32 + lane, ent = hs.sptr[sl] + (int64_t)k * 32 + lane;
+            if (row < n && hs.col[ent] == row) {
+              de[row] += ops.Aeps[ent];
+              da[row] += ops.Aaeps[ent];
+            }
+          }
+      for (int64_t i = 0; i < n; ++i) {
+        de[i] = de[i] > 0.0 ? 1.0 / de[i] : 1.0;
+        da[i] = da[i] > 0.0 ? 1.0 / da[i] : 1.0;
+      }
+      ST(upload(&dgs_eps_, de));
+      ST(upload(&dgs_aeps_, da));
+    }
     ST(mem_.alloc(&invML_, n));
     ST(mem_.alloc(&w_, n));
     ST(mem_.alloc(&mag_, n));
@@ -1116,11 +1137,12 @@ class Engine final : public EngineBase {
     int* na = nactive_ + slot;
     T* x = x_ + slot0 * ld_;
     CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_init_gs<T>(L_, A_, SG_, aval, M_, nr, ld_, x, r_, p_, st, na, opt_.rtol_gs, opt_.max_iter, red_));
+    const T* dinv = aval == Aeps_ ? dgs_eps_ : dgs_aeps_;  // NULL: plain CG
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_init_gs<T>(L_, A_, SG_, aval, M_, nr, ld_, x, r_, p_, st, na, opt_.rtol_gs, opt_.max_iter, red_, dinv));
     auto iter = [&]() -> int {
       TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, SG_, aval, 1, nr, ld_, p_, q_, st, red_, var_scalar_, 0));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, 1, nr, ld_, x, r_, p_, q_, st, na, red_));
-      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st, loop_));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, 1, nr, ld_, x, r_, p_, q_, st, na, red_, dinv));
+      TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st, loop_, dinv));
       return GSPM_OK;
     };
     if (capturing_) return cg_graph_loop(slot, iter, 2, 3);
@@ -1167,11 +1189,12 @@ class Engine final : public EngineBase {
     std::vector<int64_t> off3(S), off1(S);
     int64_t t3 = 0, t1 = 0;
     for (int sg = 0; sg < S; ++sg) {
+      // blocks start at multiples of 4 values (16-byte loads in the coarse GEMV)
       const int64_t a = hb_.coarse[sg].n_agg;
-      off3[sg] = t3;
-      off1[sg] = t1;
-      t3 += 9 * a * a;
-      t1 += a * a;
+      off3[sg] = (t3 + 3) / 4 * 4;
+      off1[sg] = (t1 + 3) / 4 * 4;
+      t3 = off3[sg] + 9 * a * a;
+      t1 = off1[sg] + a * a;
     }
     std::vector<T> inv3(t3), inv1(t1), d3(3 * n_, T(0)), d1(n_, T(0));
     for (int sg = 0; sg < S; ++sg) {
@@ -1479,7 +1502,8 @@ class Engine final : public EngineBase {
   DCoarse CC_{};
   int64_t *inv_off3_ = nullptr, *inv_off1_ = nullptr;
   T *cinv3_ = nullptr, *cinv1_ = nullptr, *dinv3_ = nullptr, *dinv1_ = nullptr;
-  double *rc_ = nullptr, *ec_ = nullptr;
+  T *dgs_eps_ = nullptr, *dgs_aeps_ = nullptr;  // Jacobi of the GSPM solves (NULL: plain)
+  T *rc_ = nullptr, *ec_ = nullptr;
   // CUDA-graph replay state
   bool graph_on_ = false, capturing_ = false;
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr;

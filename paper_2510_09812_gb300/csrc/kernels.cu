@@ -272,9 +272,12 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv9(DSell A, co
 // ------------------------------------------------------------------------------------------
 // conjugate gradients (Sec. 2.5, unpreconditioned), all scalars on the device, per segment
 // ------------------------------------------------------------------------------------------
+// pc: 0 plain CG, 1 two-level preconditioner (beta from k_pcg_z), 2 Jacobi preconditioner
+// fused into the update (rz given here)
 __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, const double* bb,
                                          const double* rr, double rtol, int max_iter,
-                                         int allow_zero_x, int pc = 0) {
+                                         int allow_zero_x, int pc = 0,
+                                         const double* rz = nullptr) {
   int any = 0, zero = 0;
   for (int k = 0; k < 3; ++k) {
     CGRhs& q = st->r[k];
@@ -283,7 +286,8 @@ __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, cons
       q.rr = rr[k];
       q.tol2 = rtol * rtol * bb[k];
       q.iters = 0;
-      q.alpha = q.beta = q.pq = q.rz = 0.0;
+      q.alpha = q.beta = q.pq = 0.0;
+      q.rz = rz ? rz[k] : 0.0;
       q.done = (bb[k] == 0.0 || rr[k] < q.tol2) ? 1 : 0;
       if (bb[k] == 0.0) zero = 1;
       any |= !q.done;
@@ -326,6 +330,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
     for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
       const int64_t row = s * 32 + lane;
       const bool ok = row_valid(G, seg, row);
+      // A x summed in FP64: with a good initial guess b - A x cancels heavily, and this runs
+      // once per solve
       if (B == 1) {
         double acc[1];
         const int skip[1] = {0};
@@ -370,38 +376,44 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G, ItemList
                                                        const T* __restrict__ x,
                                                        T* __restrict__ r, T* __restrict__ p,
                                                        CGState* st, int* nactive, double rtol,
-                                                       int max_iter, Red red) {
+                                                       int max_iter, Red red,
+                                                       const T* __restrict__ dinv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int skip[NR] = {};
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
-    double v[2 * NR];
+    double v[3 * NR];  // rr, bb, rz per right-hand side
 #pragma unroll
-    for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
+    for (int k = 0; k < 3 * NR; ++k) v[k] = 0.0;
     for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
+      // M x and A x in FP64: their difference (-c eps K x) is small against either
       double ax[NR], mx[NR];
       sell_scalar_row<T, T, double, NR>(A, aval, s, lane, x, ld, skip, ax);
       sell_scalar_row<T, T, double, NR>(A, mval, s, lane, x, ld, skip, mx);
       const int64_t row = s * 32 + lane;
       if (row_valid(G, seg, row)) {
+        const T d = dinv ? dinv[row] : T(1);
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
           const T rv = (T)(mx[k] - ax[k]);
+          const T zv = d * rv;
           r[k * ld + row] = rv;
-          p[k * ld + row] = rv;
-          v[2 * k] += (double)rv * (double)rv;
-          v[2 * k + 1] += mx[k] * mx[k];
+          p[k * ld + row] = zv;
+          v[3 * k] += (double)rv * (double)rv;
+          v[3 * k + 1] += mx[k] * mx[k];
+          v[3 * k + 2] += (double)rv * (double)zv;
         }
       }
     }
-    __shared__ double res[2 * NR];
-    if (seg_reduce<2 * NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
-      double bb[NR], rr[NR];
+    __shared__ double res[3 * NR];
+    if (seg_reduce<3 * NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+      double bb[NR], rr[NR], rz[NR];
       for (int k = 0; k < NR; ++k) {
-        rr[k] = res[2 * k];
-        bb[k] = res[2 * k + 1];
+        rr[k] = res[3 * k];
+        bb[k] = res[3 * k + 1];
+        rz[k] = res[3 * k + 2];
       }
-      cg_start(st + seg, nactive, NR, bb, rr, rtol, max_iter, 0);
+      cg_start(st + seg, nactive, NR, bb, rr, rtol, max_iter, 0, dinv ? 2 : 0, rz);
     }
   }
 }
@@ -444,7 +456,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
           for (int k = 0; k < NR; ++k)
             if (!skip[k]) {
               q[k * ld + row] = acc[k];
-              v[k] += (double)p[k * ld + row] * (double)acc[k];
+              v[k] += (double)(p[k * ld + row] * acc[k]);
             }
         }
       } else {
@@ -452,11 +464,13 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
         sell_block_row<T, T, T, VAR>(A, val, s, sl, p, acc, k0, ks);
         if (row == pin) acc[0] = acc[1] = acc[2] = T(0);
         if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
+          T pq = T(0);  // the row's p.q in T, one FP64 add per row
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             q[3 * row + a] = acc[a];
-            v[0] += (double)p[3 * row + a] * (double)acc[a];
+            pq += p[3 * row + a] * acc[a];
           }
+          v[0] += (double)pq;
         }
       }
     }
@@ -505,12 +519,15 @@ __device__ __forceinline__ void item_elems(const DSeg& G, const ItemList& IL, in
 // convergence.  Vectors hold epr elements per row (1: scalar SoA with stride ld; 3: [n][3]).
 // VEC: all vectors 16-byte aligned (and ld a multiple of the pack width), so the item's range
 // moves in 16-byte packs with a scalar tail.
+// dinv != NULL (scalar rows, Jacobi preconditioner fused): also r.D^-1 r per right-hand side,
+// and the segment's last item forms beta = r.z / rz_old.
 template <typename T, int NR, bool VEC>
 __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int epr, int64_t ld,
                                                       T* __restrict__ x, T* __restrict__ r,
                                                       const T* __restrict__ p,
                                                       const T* __restrict__ q, CGState* st,
-                                                      int* nactive, Red red) {
+                                                      int* nactive, Red red,
+                                                      const T* __restrict__ dinv) {
   constexpr int W = Pack16<T>::W;
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
@@ -523,15 +540,17 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
       skip[k] = sg->r[k].done;
       al[k] = (T)sg->r[k].alpha;
     }
-    double v[NR];
+    double v[2 * NR];  // r.r, then r.D^-1 r
 #pragma unroll
-    for (int k = 0; k < NR; ++k) v[k] = 0.0;
+    for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
     int64_t e0, e1;
     item_elems(G, IL, item, seg, epr, e0, e1);
     int64_t etail = e0;
     if (VEC) {
       const int64_t np = (e1 - e0) / W;
       for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+        T dv[W];
+        if (dinv) ld16(dinv + e0 + t * W, dv);
 #pragma unroll
         for (int k = 0; k < NR; ++k)
           if (!skip[k]) {
@@ -541,14 +560,16 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
             ld16(r + o, rv);
             ld16(p + o, pv);
             ld16(q + o, qv);
-            T rr = T(0);  // the pack's r.r in T, one FP64 add per pack
+            T rr = T(0), rz = T(0);  // the pack's sums in T, one FP64 add per pack
 #pragma unroll
             for (int c = 0; c < W; ++c) {
               xv[c] += al[k] * pv[c];
               rv[c] -= al[k] * qv[c];
               rr += rv[c] * rv[c];
+              if (dinv) rz += rv[c] * dv[c] * rv[c];
             }
             v[k] += (double)rr;
+            v[NR + k] += (double)rz;
             st16(x + o, xv);
             st16(r + o, rv);
           }
@@ -556,6 +577,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
       etail = e0 + np * W;
     }
     for (int64_t i = etail + threadIdx.x; i < e1; i += blockDim.x) {
+      const T d = dinv ? dinv[i] : T(0);
 #pragma unroll
       for (int k = 0; k < NR; ++k)
         if (!skip[k]) {
@@ -564,16 +586,22 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
           const T rv = r[o] - al[k] * q[o];
           r[o] = rv;
           v[k] += (double)(rv * rv);
+          v[NR + k] += (double)(rv * d * rv);
         }
     }
-    __shared__ double res[NR];
-    if (seg_reduce<NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+    __shared__ double res[2 * NR];
+    if (seg_reduce<2 * NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       int any = 0;
       for (int k = 0; k < NR; ++k) {
         CGRhs& c = sg->r[k];
         if (c.done) continue;
         c.iters += 1;
-        if (!sg->pc) c.beta = res[k] / c.rr;  // preconditioned: beta from r.z (k_pcg_z)
+        if (sg->pc == 0) {
+          c.beta = res[k] / c.rr;
+        } else if (sg->pc == 2) {
+          c.beta = c.rz != 0.0 ? res[NR + k] / c.rz : 0.0;
+          c.rz = res[NR + k];
+        }  // pc 1: beta from r.z in k_pcg_z
         c.rr = res[k];
         if (res[k] < c.tol2) {
           c.done = 1;
@@ -592,11 +620,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
 // p = r + beta p
 // In a graph loop, block 0 also decides whether the loop runs again (nactive is final: the
 // update kernel before this one has finished).
+// dinv != NULL: p = D^-1 r + beta p (Jacobi preconditioner, scalar rows)
 template <typename T, int NR, bool VEC>
 __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int epr, int64_t ld,
                                                        const T* __restrict__ r,
                                                        T* __restrict__ p, const CGState* st,
-                                                       LoopCtl lc) {
+                                                       LoopCtl lc, const T* __restrict__ dinv) {
   constexpr int W = Pack16<T>::W;
   if (lc.count && blockIdx.x == 0 && threadIdx.x == 0) {
     const int c = *lc.count + 1;
@@ -621,6 +650,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
     if (VEC) {
       const int64_t np = (e1 - e0) / W;
       for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+        T dv[W];
+        if (dinv) ld16(dinv + e0 + t * W, dv);
 #pragma unroll
         for (int k = 0; k < NR; ++k)
           if (!skip[k]) {
@@ -629,18 +660,19 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
             ld16(r + o, rv);
             ld16(p + o, pv);
 #pragma unroll
-            for (int c = 0; c < W; ++c) pv[c] = rv[c] + be[k] * pv[c];
+            for (int c = 0; c < W; ++c) pv[c] = (dinv ? dv[c] * rv[c] : rv[c]) + be[k] * pv[c];
             st16(p + o, pv);
           }
       }
       etail = e0 + np * W;
     }
     for (int64_t i = etail + threadIdx.x; i < e1; i += blockDim.x) {
+      const T d = dinv ? dinv[i] : T(1);
 #pragma unroll
       for (int k = 0; k < NR; ++k)
         if (!skip[k]) {
           const int64_t o = k * ld + i;
-          p[o] = r[o] + be[k] * p[o];
+          p[o] = d * r[o] + be[k] * p[o];
         }
     }
   }
@@ -670,35 +702,63 @@ __global__ void __launch_bounds__(kBlock) k_pin_shift(DSell A, DSeg G, int epr, 
   }
 }
 
-// rc(I, a) = sum over the rows i of aggregate I of r(i, a): one warp per aggregate, lanes
-// stride over its rows, FP64 warp tree (fixed order)
+// rc(I, a) = sum over the rows i of aggregate I of r(i, a): one block per aggregate, threads
+// stride over its rows, FP64 block tree (fixed order)
 template <typename T, int EPR>
 __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restrict__ r,
-                                                     double* __restrict__ rc) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t I = gtid() >> 5; I < C.nagg; I += gstride() >> 5) {
+                                                     T* __restrict__ rc) {
+  __shared__ double sm[EPR][kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t I = blockIdx.x; I < C.nagg; I += gridDim.x) {
     double acc[EPR];
 #pragma unroll
     for (int a = 0; a < EPR; ++a) acc[a] = 0.0;
-    for (int q = C.agg_ptr[I] + lane; q < C.agg_ptr[I + 1]; q += 32) {
-      const int64_t row = C.agg_rows[q];
+    // four rows per thread and round: their indices, then their values, then the sums (in T
+    // within the round, one FP64 add per component)
+    const int q1 = C.agg_ptr[I + 1];
+    for (int q = C.agg_ptr[I] + threadIdx.x; q < q1; q += 4 * blockDim.x) {
+      int64_t row[4];
 #pragma unroll
-      for (int a = 0; a < EPR; ++a) acc[a] += (double)r[row * EPR + a];
+      for (int u = 0; u < 4; ++u) {
+        const int qq = q + u * blockDim.x;
+        row[u] = qq < q1 ? (int64_t)C.agg_rows[qq] : -1;
+      }
+      T v[4][EPR];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int a = 0; a < EPR; ++a) v[u][a] = row[u] >= 0 ? r[row[u] * EPR + a] : T(0);
+#pragma unroll
+      for (int a = 0; a < EPR; ++a) acc[a] += (double)((v[0][a] + v[1][a]) + (v[2][a] + v[3][a]));
     }
 #pragma unroll
     for (int a = 0; a < EPR; ++a) {
       const double v = warp_sum(acc[a]);
-      if (lane == 0) rc[I * EPR + a] = v;
+      if (lane == 0) sm[a][warp] = v;
     }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int a = 0; a < EPR; ++a) {
+        const double v = warp_sum(lane < kBlock / 32 ? sm[a][lane] : 0.0);
+        if (lane == 0) rc[I * EPR + a] = (T)v;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// ec = A_c^-1 rc per segment block: one warp per coarse row, coalesced over the row
-template <typename T>
+// ec = A_c^-1 rc per segment block: one warp per coarse row, coalesced 16-byte loads over the
+// row (a segment's block has nc % 4 == 0 rows of nc values and starts 16-byte aligned when
+// `vec`), four loads in flight per lane
+// (accumulated in T: it only applies the preconditioner, and FP64 instructions cost ~16x
+// FP32 ones per warp on this part)
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kBlock) k_coarse_gemv(DCoarse C, int epr, const T* __restrict__ inv,
                                                         const int64_t* __restrict__ inv_off,
-                                                        const double* __restrict__ rc,
-                                                        double* __restrict__ ec) {
+                                                        const T* __restrict__ rc,
+                                                        T* __restrict__ ec) {
+  constexpr int W = Pack16<T>::W;
   const int lane = threadIdx.x & 31;
   const int64_t ncoarse = C.nagg * epr;
   for (int64_t g = gtid() >> 5; g < ncoarse; g += gstride() >> 5) {
@@ -706,35 +766,108 @@ __global__ void __launch_bounds__(kBlock) k_coarse_gemv(DCoarse C, int epr, cons
     const int64_t c0 = (int64_t)C.seg_agg0[seg] * epr;
     const int64_t nc = (int64_t)(C.seg_agg0[seg + 1] - C.seg_agg0[seg]) * epr;
     const T* row = inv + inv_off[seg] + (g - c0) * nc;
-    double acc = 0.0;
-    for (int64_t j = lane; j < nc; j += 32) acc += (double)row[j] * rc[c0 + j];
-    acc = warp_sum(acc);
+    const T* x = rc + c0;
+    T acc = T(0);
+    int64_t j0 = 0;
+    if (VEC && nc % W == 0) {
+      const int64_t np = nc / W;
+      for (int64_t t = lane; t < np; t += 4 * 32) {
+        T a[4][W];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t tt = t + u * 32;
+          if (tt < np) {
+            ld16(row + tt * W, a[u]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < W; ++c) a[u][c] = T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t tt = t + u * 32;
+          if (tt < np)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc += a[u][c] * x[tt * W + c];
+        }
+      }
+      j0 = nc;
+    }
+    for (int64_t j = j0 + lane; j < nc; j += 32) acc += row[j] * x[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
     if (lane == 0) ec[g] = acc;
   }
 }
 
-// z = D^-1 r + P ec, r.z; init: z is the first search direction p
+// N contiguous values through 16-byte packs (N * sizeof(T) a multiple of 16, p aligned)
+template <typename T, int N>
+__device__ __forceinline__ void ldn(const T* p, T (&v)[N]) {
+  constexpr int W = Pack16<T>::W;
+#pragma unroll
+  for (int k = 0; k < N / W; ++k)
+    *reinterpret_cast<typename Pack16<T>::V*>(v + k * W) =
+        *reinterpret_cast<const typename Pack16<T>::V*>(p + k * W);
+}
+template <typename T, int N>
+__device__ __forceinline__ void stn(T* p, const T (&v)[N]) {
+  constexpr int W = Pack16<T>::W;
+#pragma unroll
+  for (int k = 0; k < N / W; ++k)
+    *reinterpret_cast<typename Pack16<T>::V*>(p + k * W) =
+        *reinterpret_cast<const typename Pack16<T>::V*>(v + k * W);
+}
+
+// z = D^-1 r + P ec, r.z; init: z is the first search direction p.  Four rows per thread and
+// round (their 4 * EPR values are whole 16-byte packs: item ranges start at multiples of 32
+// rows), the round's r.z summed in T, one FP64 add per round; scalar tail rows.
 template <typename T, int EPR>
 __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C,
                                                   const T* __restrict__ r,
                                                   const T* __restrict__ dinv,
-                                                  const double* __restrict__ ec,
+                                                  const T* __restrict__ ec,
                                                   T* __restrict__ z, CGState* st, int init,
                                                   Red red) {
+  constexpr int N = 4 * EPR;
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
     CGState* sg = st + seg;
     if (!sg->active) continue;
     double v[1] = {0.0};
-    int64_t e0, e1;
-    item_elems(G, IL, item, seg, EPR, e0, e1);
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int64_t row = e / EPR;
-      const int a = (int)(e - row * EPR);
-      const T rv = r[e];
-      const T zv = dinv[e] * rv + (T)ec[(int64_t)C.agg_of_row[row] * EPR + a];
-      z[e] = zv;
-      v[0] += (double)rv * (double)zv;
+    const int64_t r0 = (int64_t)IL.sl0[item] * 32;
+    const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
+    const int64_t rhi = (int64_t)IL.sl1[item] * 32;
+    const int64_t r1 = rhi < rend ? rhi : rend;
+    const int64_t ng = (r1 - r0) / 4;
+    for (int64_t g = threadIdx.x; g < ng; g += blockDim.x) {
+      const int64_t row = r0 + 4 * g;
+      T rv[N], dv[N], zv[N];
+      ldn<T, N>(r + row * EPR, rv);
+      ldn<T, N>(dinv + row * EPR, dv);
+      const int4 ag = *reinterpret_cast<const int4*>(C.agg_of_row + row);
+      const int agv[4] = {ag.x, ag.y, ag.z, ag.w};
+      T rz = T(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int a = 0; a < EPR; ++a) {
+          const int e = u * EPR + a;
+          zv[e] = dv[e] * rv[e] + ec[(int64_t)agv[u] * EPR + a];
+          rz += rv[e] * zv[e];
+        }
+      stn<T, N>(z + row * EPR, zv);
+      v[0] += (double)rz;
+    }
+    for (int64_t row = r0 + 4 * ng + threadIdx.x; row < r1; row += blockDim.x) {
+      const int64_t I = C.agg_of_row[row];
+#pragma unroll
+      for (int a = 0; a < EPR; ++a) {
+        const int64_t e = row * EPR + a;
+        const T rv = r[e];
+        const T zv = dinv[e] * rv + ec[I * EPR + a];
+        z[e] = zv;
+        v[0] += (double)rv * (double)zv;
+      }
     }
     __shared__ double res[1];
     if (seg_reduce<1>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
@@ -1327,28 +1460,28 @@ cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const
 template <typename T>
 cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
                               const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
-                              int* nactive, double rtol, int max_iter, Red red) {
+                              int* nactive, double rtol, int max_iter, Red red, const T* dinv) {
   (*L.counter) += 1;
   switch (nr) {
     case 1: {
       auto k = k_cg_init_gs<T, 1>;
       const ItemGrid ig = GSPM_IGRID(L, G, k);
       k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, aval, mval, ld, x, r, p, st, nactive,
-                                                      rtol, max_iter, red);
+                                                      rtol, max_iter, red, dinv);
       break;
     }
     case 2: {
       auto k = k_cg_init_gs<T, 2>;
       const ItemGrid ig = GSPM_IGRID(L, G, k);
       k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, aval, mval, ld, x, r, p, st, nactive,
-                                                      rtol, max_iter, red);
+                                                      rtol, max_iter, red, dinv);
       break;
     }
     case 3: {
       auto k = k_cg_init_gs<T, 3>;
       const ItemGrid ig = GSPM_IGRID(L, G, k);
       k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, aval, mval, ld, x, r, p, st, nactive,
-                                                      rtol, max_iter, red);
+                                                      rtol, max_iter, red, dinv);
       break;
     }
     default: return cudaErrorInvalidValue;
@@ -1399,20 +1532,21 @@ static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 template <typename T, int NR, bool VEC>
 static void cg_update_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, T* x, T* r,
-                         const T* p, const T* q, CGState* st, int* nactive, Red red) {
+                         const T* p, const T* q, CGState* st, int* nactive, Red red,
+                         const T* dinv) {
   auto k = k_cg_update<T, NR, VEC>;
   const ItemGrid ig = GSPM_IGRID(L, G, k);
-  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, x, r, p, q, st, nactive, red);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, x, r, p, q, st, nactive, red, dinv);
 }
 
 template <typename T, bool VEC>
 static cudaError_t cg_update_vec(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
                                  T* x, T* r, const T* p, const T* q, CGState* st, int* nactive,
-                                 Red red) {
+                                 Red red, const T* dinv) {
   switch (nr) {
-    case 1: cg_update_nr<T, 1, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red); break;
-    case 2: cg_update_nr<T, 2, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red); break;
-    case 3: cg_update_nr<T, 3, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red); break;
+    case 1: cg_update_nr<T, 1, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv); break;
+    case 2: cg_update_nr<T, 2, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv); break;
+    case 3: cg_update_nr<T, 3, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1420,29 +1554,32 @@ static cudaError_t cg_update_vec(const Launch& L, const DSeg& G, int epr, int nr
 
 template <typename T>
 cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
-                             T* r, const T* p, const T* q, CGState* st, int* nactive, Red red) {
+                             T* r, const T* p, const T* q, CGState* st, int* nactive, Red red,
+                             const T* dinv) {
   (*L.counter) += 1;
+  if (dinv && epr != 1) return cudaErrorInvalidValue;
   const bool vec = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) &&
-                   (nr == 1 || ld % Pack16<T>::W == 0);
-  return vec ? cg_update_vec<T, true>(L, G, epr, nr, ld, x, r, p, q, st, nactive, red)
-             : cg_update_vec<T, false>(L, G, epr, nr, ld, x, r, p, q, st, nactive, red);
+                   (!dinv || aligned16(dinv)) && (nr == 1 || ld % Pack16<T>::W == 0);
+  return vec ? cg_update_vec<T, true>(L, G, epr, nr, ld, x, r, p, q, st, nactive, red, dinv)
+             : cg_update_vec<T, false>(L, G, epr, nr, ld, x, r, p, q, st, nactive, red, dinv);
 }
 
 template <typename T, int NR, bool VEC>
 static void cg_pupdate_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, const T* r, T* p,
-                          const CGState* st, const LoopCtl& lc) {
+                          const CGState* st, const LoopCtl& lc, const T* dinv) {
   auto k = k_cg_pupdate<T, NR, VEC>;
   const ItemGrid ig = GSPM_IGRID(L, G, k);
-  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, r, p, st, lc);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, r, p, st, lc, dinv);
 }
 
 template <typename T, bool VEC>
 static cudaError_t cg_pupdate_vec(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
-                                  const T* r, T* p, const CGState* st, const LoopCtl& lc) {
+                                  const T* r, T* p, const CGState* st, const LoopCtl& lc,
+                                  const T* dinv) {
   switch (nr) {
-    case 1: cg_pupdate_nr<T, 1, VEC>(L, G, epr, ld, r, p, st, lc); break;
-    case 2: cg_pupdate_nr<T, 2, VEC>(L, G, epr, ld, r, p, st, lc); break;
-    case 3: cg_pupdate_nr<T, 3, VEC>(L, G, epr, ld, r, p, st, lc); break;
+    case 1: cg_pupdate_nr<T, 1, VEC>(L, G, epr, ld, r, p, st, lc, dinv); break;
+    case 2: cg_pupdate_nr<T, 2, VEC>(L, G, epr, ld, r, p, st, lc, dinv); break;
+    case 3: cg_pupdate_nr<T, 3, VEC>(L, G, epr, ld, r, p, st, lc, dinv); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1450,22 +1587,25 @@ static cudaError_t cg_pupdate_vec(const Launch& L, const DSeg& G, int epr, int n
 
 template <typename T>
 cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
-                              const T* r, T* p, const CGState* st, const LoopCtl& lc) {
+                              const T* r, T* p, const CGState* st, const LoopCtl& lc,
+                              const T* dinv) {
   (*L.counter) += 1;
-  const bool vec = aligned16(r) && aligned16(p) && (nr == 1 || ld % Pack16<T>::W == 0);
-  return vec ? cg_pupdate_vec<T, true>(L, G, epr, nr, ld, r, p, st, lc)
-             : cg_pupdate_vec<T, false>(L, G, epr, nr, ld, r, p, st, lc);
+  if (dinv && epr != 1) return cudaErrorInvalidValue;
+  const bool vec = aligned16(r) && aligned16(p) && (!dinv || aligned16(dinv)) &&
+                   (nr == 1 || ld % Pack16<T>::W == 0);
+  return vec ? cg_pupdate_vec<T, true>(L, G, epr, nr, ld, r, p, st, lc, dinv)
+             : cg_pupdate_vec<T, false>(L, G, epr, nr, ld, r, p, st, lc, dinv);
 }
 
 template <typename T>
-cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, double* rc) {
+cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, T* rc) {
   (*L.counter) += 1;
   if (epr == 3) {
     auto k = k_restrict<T, 3>;
-    k<<<GSPM_GRID(L, C.nagg * 32, k), kBlock, 0, L.stream>>>(C, r, rc);
+    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc);
   } else if (epr == 1) {
     auto k = k_restrict<T, 1>;
-    k<<<GSPM_GRID(L, C.nagg * 32, k), kBlock, 0, L.stream>>>(C, r, rc);
+    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1474,16 +1614,23 @@ cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T*
 
 template <typename T>
 cudaError_t launch_coarse_gemv(const Launch& L, const DCoarse& C, int epr, const T* inv,
-                               const int64_t* inv_off, const double* rc, double* ec) {
+                               const int64_t* inv_off, const T* rc, T* ec) {
   (*L.counter) += 1;
-  auto k = k_coarse_gemv<T>;
-  k<<<GSPM_GRID(L, C.nagg * epr * 32, k), kBlock, 0, L.stream>>>(C, epr, inv, inv_off, rc, ec);
+  // each segment's block starts at a multiple of 4 values (inv_off), so with an aligned base
+  // every row of a block with nc % W == 0 is 16-byte aligned; other blocks use scalar loads
+  if (aligned16(inv)) {
+    auto k = k_coarse_gemv<T, true>;
+    k<<<GSPM_GRID(L, C.nagg * epr * 32, k), kBlock, 0, L.stream>>>(C, epr, inv, inv_off, rc, ec);
+  } else {
+    auto k = k_coarse_gemv<T, false>;
+    k<<<GSPM_GRID(L, C.nagg * epr * 32, k), kBlock, 0, L.stream>>>(C, epr, inv, inv_off, rc, ec);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
-                         const T* dinv, const double* ec, T* z, CGState* st, int init, Red red) {
+                         const T* dinv, const T* ec, T* z, CGState* st, int init, Red red) {
   (*L.counter) += 1;
   if (epr == 3) {
     auto k = k_pcg_z<T, 3>;
@@ -1671,20 +1818,21 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
   template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
                                          const T*, T*, T*, T*, CGState*, int*, double, int, Red,  \
                                          const double*, int, int);                                \
-  template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*, double*); \
+  template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*, T*);      \
   template cudaError_t launch_coarse_gemv<T>(const Launch&, const DCoarse&, int, const T*,        \
-                                             const int64_t*, const double*, double*);             \
+                                             const int64_t*, const T*, T*);                       \
   template cudaError_t launch_pcg_z<T>(const Launch&, const DSeg&, const DCoarse&, int, const T*, \
-                                       const T*, const double*, T*, CGState*, int, Red);         \
+                                       const T*, const T*, T*, CGState*, int, Red);              \
   template cudaError_t launch_cg_init_gs<T>(const Launch&, const DSell&, const DSeg&, const T*,   \
                                             const T*, int, int64_t, T*, T*, T*, CGState*, int*,   \
-                                            double, int, Red);                                    \
+                                            double, int, Red, const T*);                          \
   template cudaError_t launch_cg_spmv<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
                                          int, int64_t, const T*, T*, CGState*, Red, int, int);    \
   template cudaError_t launch_cg_update<T>(const Launch&, const DSeg&, int, int, int64_t, T*, T*, \
-                                           const T*, const T*, CGState*, int*, Red);              \
+                                           const T*, const T*, CGState*, int*, Red, const T*);    \
   template cudaError_t launch_cg_pupdate<T>(const Launch&, const DSeg&, int, int, int64_t,        \
-                                            const T*, T*, const CGState*, const LoopCtl&);        \
+                                            const T*, T*, const CGState*, const LoopCtl&,         \
+                                            const T*);                                            \
   template cudaError_t launch_cg_zero<T>(const Launch&, const DSeg&, int, T*, const CGState*);    \
   template cudaError_t launch_fdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
                                       const T*, int64_t, T*, int);                                \

@@ -137,10 +137,11 @@ template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
                            int max_iter, Red red, const double* bmean, int pinned, int pc);
+// dinv != NULL: Jacobi-preconditioned CG (p = z = D^-1 r, fused into update and p-update)
 template <typename T>
 cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
                               const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
-                              int* nactive, double rtol, int max_iter, Red red);
+                              int* nactive, double rtol, int max_iter, Red red, const T* dinv);
 template <typename T>
 cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
@@ -151,21 +152,23 @@ cudaError_t launch_pin_shift(const Launch& L, const DSell& A, const DSeg& G, int
                              double* xp);
 template <typename T>
 cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
-                             T* r, const T* p, const T* q, CGState* st, int* nactive, Red red);
+                             T* r, const T* p, const T* q, CGState* st, int* nactive, Red red,
+                             const T* dinv = nullptr);
 template <typename T>
 cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld,
-                              const T* r, T* p, const CGState* st, const LoopCtl& lc);
+                              const T* r, T* p, const CGState* st, const LoopCtl& lc,
+                              const T* dinv = nullptr);
 // Two-level preconditioner z = D^-1 r + P A_c^-1 P^T r (one right-hand side, epr components):
 // rc = P^T r (per aggregate sums), ec = A_c^-1 rc (per segment dense block), then z and r.z;
 // the segment's last item stores rz (init) or beta = r.z / rz_old and rz.
 template <typename T>
-cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, double* rc);
+cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, T* rc);
 template <typename T>
 cudaError_t launch_coarse_gemv(const Launch& L, const DCoarse& C, int epr, const T* inv,
-                               const int64_t* inv_off, const double* rc, double* ec);
+                               const int64_t* inv_off, const T* rc, T* ec);
 template <typename T>
 cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
-                         const T* dinv, const double* ec, T* z, CGState* st, int init, Red red);
+                         const T* dinv, const T* ec, T* z, CGState* st, int init, Red red);
 // Graph loops: reset the iteration count and set the WHILE condition to (nactive > 0).
 cudaError_t launch_loop_start(const Launch& L, const LoopCtl& lc);
 // Add one solve's iterations (kind 0 K^ms, 1 K^mech: the largest over right-hand sides;

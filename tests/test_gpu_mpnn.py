@@ -43,7 +43,9 @@ def setup():
 
 
 def _ctx(gspm_lib, mesh, prec="mixed"):
-    return gspm_lib.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, precision=prec)
+    # one fixed SpMV schedule, so that contexts compared bit for bit sum in the same order
+    return gspm_lib.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, precision=prec,
+                            autotune=False)
 
 
 @pytest.mark.parametrize("prec", ["f64", "mixed"])

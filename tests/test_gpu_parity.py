@@ -133,10 +133,12 @@ def test_first_step_fields_match_oracle(gspm_lib, ragged, ordering, pinned):
         # stopping threshold
         assert abs(st["it_ms_last"] - info["it_ms"]) <= 2
         assert abs(st["it_mech_last"] - info["it_mech"]) <= 2
+        assert np.abs(np.array(st["it_gs_last"][:7]) - info["it_gs"]).max() <= 2
     else:
-        # the equivalent consistent singular systems converge faster to the same solution
+        # the equivalent consistent singular systems with the two-level preconditioner, and the
+        # Jacobi-preconditioned GSPM solves, converge faster to the same solution
         assert st["it_ms_last"] < info["it_ms"] and st["it_mech_last"] < info["it_mech"]
-    assert np.abs(np.array(st["it_gs_last"][:7]) - info["it_gs"]).max() <= 2
+        assert sum(st["it_gs_last"][:7]) < sum(info["it_gs"])
     assert _relerr(ctx.get_field(gspm_lib.FIELD_U), U) < 1e-10
     assert _relerr(ctx.get_field(gspm_lib.FIELD_DISP), u) < 1e-10
     assert _relerr(ctx.get_field(gspm_lib.FIELD_HD), info["hd"]) < 1e-10
@@ -189,11 +191,14 @@ def test_printed_row2_variant_matches_oracle(gspm_lib, ragged):
     m0 = synth.random_unit_m(wm.n, 8)
     m0[~s.mag] = 0.0
     m_ref, _, _, infos = run(s, m0, np.array([0.0, 2e4, 0.0]), 3)
-    ctx = _ctx(gspm_lib, mesh, "f64", row2_printed=True)
-    ctx.set_field(gspm_lib.FIELD_M, m0)
-    st = ctx.step(3, [0.0, 2e4, 0.0])
-    assert np.abs(np.array(st["it_gs_last"]) - infos[-1]["it_gs"]).max() <= 2
-    assert _relerr(ctx.get_field(gspm_lib.FIELD_M), m_ref) < 1e-10
+    for literal in (True, False):
+        # literal: the paper's plain CG on the pinned systems, iteration counts as the oracle's
+        ctx = _ctx(gspm_lib, mesh, "f64", row2_printed=True, pinned_cg=literal)
+        ctx.set_field(gspm_lib.FIELD_M, m0)
+        st = ctx.step(3, [0.0, 2e4, 0.0])
+        if literal:
+            assert np.abs(np.array(st["it_gs_last"]) - infos[-1]["it_gs"]).max() <= 2
+        assert _relerr(ctx.get_field(gspm_lib.FIELD_M), m_ref) < 1e-10
 
 
 def test_device_pointer_state_roundtrip(gspm_lib, ragged):

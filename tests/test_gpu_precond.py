@@ -1,5 +1,5 @@
-"""Two-level preconditioned CG of the K^ms and K^mech solves (default) against the
-unpreconditioned CG (GSPM_FLAG_PLAIN_CG) and the oracle.
+"""Two-level preconditioned CG of the K^ms and K^mech solves and Jacobi-preconditioned GSPM
+solves (default) against the unpreconditioned CG (GSPM_FLAG_PLAIN_CG) and the oracle.
 
 The preconditioner changes the iteration, not the system: with the stopping test on the true
 recursive residual, FP64 solves to rtol 1e-13 agree with the oracle's pinned solution to 1e-10.
@@ -98,6 +98,8 @@ def test_preconditioned_steps_match_oracle_and_cut_iterations(gspm_lib, medium):
         assert _relerr(ctx.get_field(gspm_lib.FIELD_DISP), u_ref) < 1e-10
     assert st[False]["it_mech"] < 0.6 * st[True]["it_mech"]
     assert st[False]["it_ms"] < st[True]["it_ms"]
+    # Jacobi on the GSPM solves (M + c eps K) g = M f
+    assert st[False]["it_gs"] < 0.6 * st[True]["it_gs"]
 
 
 def test_preconditioned_mixed_graph_and_batch(gspm_lib, medium):
