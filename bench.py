@@ -352,7 +352,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         ctx = gspm.Context(mesh, cfg["material"], cfg["dt"], cfg["alpha"], precision=prec,
                            ordering=args.ordering, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
-                           pinned_cg=pinned, plain_cg=plain)
+                           pinned_cg=pinned, plain_cg=plain, coarse_nodes=args.coarse_nodes)
         ctx.set_field(gspm.FIELD_M, cfg["m0"])
         if weights is not None:
             ctx.mpnn_set_params(weights)
@@ -566,6 +566,8 @@ def main():
     ap.add_argument("--skip-graph", action="store_true")
     ap.add_argument("--pinned-cg", action="store_true",
                     help="solve the pinned systems of Sec. 2.5 instead of the singular form")
+    ap.add_argument("--coarse-nodes", type=int, default=0,
+                    help="nodes per aggregate of the two-level preconditioner (0: default)")
     ap.add_argument("--plain-cg", action="store_true",
                     help="no two-level preconditioner for the K^ms / K^mech solves")
     ap.add_argument("--skip-cpu", action="store_true")

@@ -1568,14 +1568,15 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
     if (!c->host_only) host_assemble(c->hm[k], hs[k], c->P, &ops[k]);
   }
   // two-level preconditioner of the K^ms / K^mech solves (singular form only): aggregates of
-  // max(512, n / 1024) nodes
+  // coarse_nodes nodes, by default max(512, n / 2048)
   std::vector<HostCoarse> coarse;
   const bool two_level = !c->host_only &&
                          !(opt->flags & (GSPM_FLAG_PINNED_CG | GSPM_FLAG_PLAIN_CG));
   if (two_level) {
     coarse.resize(nmesh);
     for (int k = 0; k < nmesh; ++k) {
-      const int64_t npa = std::max<int64_t>(512, (c->hm[k].n + 1023) / 1024);
+      const int64_t npa = opt->coarse_nodes > 0 ? opt->coarse_nodes
+                                                : std::max<int64_t>(512, (c->hm[k].n + 2047) / 2048);
       const int st = host_coarse_build(c->hm[k], hs[k], ops[k], npa, &coarse[k]);
       if (st != GSPM_OK) return st;
     }

@@ -621,21 +621,31 @@ void host_batch_build(std::vector<HostMesh>& hm, std::vector<HostSell>& hs,
 
 namespace gspm {
 
+// sum_{k < len} a[k] b[k] with four independent partial sums (the dependent chain of a single
+// sum bounds the host's dense factorisation)
+static inline double dot4(const double* a, const double* b, int64_t len) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t k = 0;
+  for (; k + 4 <= len; k += 4) {
+    s0 += a[k] * b[k];
+    s1 += a[k + 1] * b[k + 1];
+    s2 += a[k + 2] * b[k + 2];
+    s3 += a[k + 3] * b[k + 3];
+  }
+  for (; k < len; ++k) s0 += a[k] * b[k];
+  return (s0 + s1) + (s2 + s3);
+}
+
 // In-place Cholesky of the SPD matrix A (n x n, row-major, lower factor) and its explicit
 // inverse; false if a pivot is not positive.
 static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* inv) {
   for (int64_t j = 0; j < n; ++j) {
-    double d = A[j * n + j];
-    for (int64_t k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+    const double d = A[j * n + j] - dot4(&A[j * n], &A[j * n], j);
     if (!(d > 0.0)) return false;
     const double ljj = std::sqrt(d);
     A[j * n + j] = ljj;
 #pragma omp parallel for schedule(static)
-    for (int64_t i = j + 1; i < n; ++i) {
-      double v = A[i * n + j];
-      for (int64_t k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
-      A[i * n + j] = v / ljj;
-    }
+    for (int64_t i = j + 1; i < n; ++i) A[i * n + j] = (A[i * n + j] - dot4(&A[i * n], &A[j * n], j)) / ljj;
   }
   // U = L^T row-major, so that both triangular sweeps read contiguous rows
   std::vector<double> U(n * n, 0.0);
@@ -649,17 +659,11 @@ static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* 
     for (int64_t c = 0; c < n; ++c) {
       // L y = e_c, then L^T x = y; x is column c (= row c: the inverse is symmetric)
       for (int64_t i = 0; i < c; ++i) y[i] = 0.0;
-      for (int64_t i = c; i < n; ++i) {
-        double v = i == c ? 1.0 : 0.0;
-        for (int64_t k = c; k < i; ++k) v -= A[i * n + k] * y[k];
-        y[i] = v / A[i * n + i];
-      }
+      for (int64_t i = c; i < n; ++i)
+        y[i] = ((i == c ? 1.0 : 0.0) - dot4(&A[i * n + c], &y[c], i - c)) / A[i * n + i];
       double* x = inv->data() + c * n;
-      for (int64_t i = n - 1; i >= 0; --i) {
-        double v = y[i];
-        for (int64_t k = i + 1; k < n; ++k) v -= U[i * n + k] * x[k];
-        x[i] = v / U[i * n + i];
-      }
+      for (int64_t i = n - 1; i >= 0; --i)
+        x[i] = (y[i] - dot4(&U[i * n + i + 1], &x[i + 1], n - 1 - i)) / U[i * n + i];
     }
   }
   return true;

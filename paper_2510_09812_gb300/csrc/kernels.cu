@@ -30,6 +30,16 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Compensated summation (Kahan): s + c carries the running sum with the low-order part lost by
+// each add kept in c (subtracted at the end: total = s - c)
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+  const T y = x - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
@@ -434,9 +444,11 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
     int skip[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) skip[k] = sg->r[k].done;
-    double v[NR];
+    // p.q per thread in T with a compensated (Kahan) sum, across threads and items in FP64:
+    // the terms p_i (A p)_i cancel heavily for smooth p
+    T tv[NR], tc[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) v[k] = 0.0;
+    for (int k = 0; k < NR; ++k) tv[k] = tc[k] = T(0);
     const int64_t u0 = (int64_t)IL.sl0[item] * units_per_slice<VAR>();
     const int64_t u1 = (int64_t)IL.sl1[item] * units_per_slice<VAR>();
     for (int64_t u = u0 + warp; u < u1; u += kBlock / 32) {
@@ -456,7 +468,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
           for (int k = 0; k < NR; ++k)
             if (!skip[k]) {
               q[k * ld + row] = acc[k];
-              v[k] += (double)(p[k * ld + row] * acc[k]);
+              kahan_add(tv[k], tc[k], p[k * ld + row] * acc[k]);
             }
         }
       } else {
@@ -464,16 +476,19 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
         sell_block_row<T, T, T, VAR>(A, val, s, sl, p, acc, k0, ks);
         if (row == pin) acc[0] = acc[1] = acc[2] = T(0);
         if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
-          T pq = T(0);  // the row's p.q in T, one FP64 add per row
+          T pq = T(0);
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             q[3 * row + a] = acc[a];
             pq += p[3 * row + a] * acc[a];
           }
-          v[0] += (double)pq;
+          kahan_add(tv[0], tc[0], pq);
         }
       }
     }
+    double v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = (double)tv[k] - (double)tc[k];
     __shared__ double res[NR];
     if (seg_reduce<NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       for (int k = 0; k < NR; ++k) {
@@ -540,9 +555,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
       skip[k] = sg->r[k].done;
       al[k] = (T)sg->r[k].alpha;
     }
-    double v[2 * NR];  // r.r, then r.D^-1 r
+    // r.r, then r.D^-1 r: each thread sums its elements (a few hundred at most) in T, the
+    // block and the items in FP64
+    T tv[2 * NR];
 #pragma unroll
-    for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
+    for (int k = 0; k < 2 * NR; ++k) tv[k] = T(0);
     int64_t e0, e1;
     item_elems(G, IL, item, seg, epr, e0, e1);
     int64_t etail = e0;
@@ -560,16 +577,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
             ld16(r + o, rv);
             ld16(p + o, pv);
             ld16(q + o, qv);
-            T rr = T(0), rz = T(0);  // the pack's sums in T, one FP64 add per pack
 #pragma unroll
             for (int c = 0; c < W; ++c) {
               xv[c] += al[k] * pv[c];
               rv[c] -= al[k] * qv[c];
-              rr += rv[c] * rv[c];
-              if (dinv) rz += rv[c] * dv[c] * rv[c];
+              tv[k] += rv[c] * rv[c];
+              if (dinv) tv[NR + k] += rv[c] * dv[c] * rv[c];
             }
-            v[k] += (double)rr;
-            v[NR + k] += (double)rz;
             st16(x + o, xv);
             st16(r + o, rv);
           }
@@ -585,10 +599,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
           x[o] += al[k] * p[o];
           const T rv = r[o] - al[k] * q[o];
           r[o] = rv;
-          v[k] += (double)(rv * rv);
-          v[NR + k] += (double)(rv * d * rv);
+          tv[k] += rv * rv;
+          tv[NR + k] += rv * d * rv;
         }
     }
+    double v[2 * NR];
+#pragma unroll
+    for (int k = 0; k < 2 * NR; ++k) v[k] = (double)tv[k];
     __shared__ double res[2 * NR];
     if (seg_reduce<2 * NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       int any = 0;
@@ -710,9 +727,9 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
   __shared__ double sm[EPR][kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t I = blockIdx.x; I < C.nagg; I += gridDim.x) {
-    double acc[EPR];
+    T acc[EPR];  // per thread and per warp in T, across warps in FP64
 #pragma unroll
-    for (int a = 0; a < EPR; ++a) acc[a] = 0.0;
+    for (int a = 0; a < EPR; ++a) acc[a] = T(0);
     // four rows per thread and round: their indices, then their values, then the sums (in T
     // within the round, one FP64 add per component)
     const int q1 = C.agg_ptr[I + 1];
@@ -729,12 +746,14 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
 #pragma unroll
         for (int a = 0; a < EPR; ++a) v[u][a] = row[u] >= 0 ? r[row[u] * EPR + a] : T(0);
 #pragma unroll
-      for (int a = 0; a < EPR; ++a) acc[a] += (double)((v[0][a] + v[1][a]) + (v[2][a] + v[3][a]));
+      for (int a = 0; a < EPR; ++a) acc[a] += (v[0][a] + v[1][a]) + (v[2][a] + v[3][a]);
     }
 #pragma unroll
     for (int a = 0; a < EPR; ++a) {
-      const double v = warp_sum(acc[a]);
-      if (lane == 0) sm[a][warp] = v;
+      T v = acc[a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+      if (lane == 0) sm[a][warp] = (double)v;
     }
     __syncthreads();
     if (warp == 0) {
@@ -750,7 +769,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
 
 // ec = A_c^-1 rc per segment block: one warp per coarse row, coalesced 16-byte loads over the
 // row (a segment's block has nc % 4 == 0 rows of nc values and starts 16-byte aligned when
-// `vec`), four loads in flight per lane
+// `vec`), eight loads in flight per lane
 // (accumulated in T: it only applies the preconditioner, and FP64 instructions cost ~16x
 // FP32 ones per warp on this part)
 template <typename T, bool VEC>
@@ -771,10 +790,10 @@ __global__ void __launch_bounds__(kBlock) k_coarse_gemv(DCoarse C, int epr, cons
     int64_t j0 = 0;
     if (VEC && nc % W == 0) {
       const int64_t np = nc / W;
-      for (int64_t t = lane; t < np; t += 4 * 32) {
-        T a[4][W];
+      for (int64_t t = lane; t < np; t += 8 * 32) {
+        T a[8][W];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const int64_t tt = t + u * 32;
           if (tt < np) {
             ld16(row + tt * W, a[u]);
@@ -784,7 +803,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_gemv(DCoarse C, int epr, cons
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const int64_t tt = t + u * 32;
           if (tt < np)
 #pragma unroll

@@ -57,6 +57,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("ordering", C.c_int), ("dt", C.c_double),
                 ("alpha", C.c_double), ("rtol_gs", C.c_double), ("rtol_ms", C.c_double),
                 ("rtol_mech", C.c_double), ("max_iter", C.c_int), ("flags", C.c_uint),
+                ("coarse_nodes", C.c_int64),
                 ("stream", C.c_void_p)]
 
 
@@ -186,7 +187,7 @@ class Context:
                  ordering: str = "none", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
                  max_iter=20000, row2_printed=False, host_only=False, stream=0, wrap_tol=0.0,
                  autotune=True, graph=False, pinned_cg=False, resolve_at_mstar=False,
-                 plain_cg=False):
+                 plain_cg=False, coarse_nodes=0):
         """One mesh, or a batch when `mesh` is a list (gspm_batch_load)."""
         meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
@@ -215,6 +216,7 @@ class Context:
                    | (FLAG_PINNED_CG if pinned_cg else 0)
                    | (FLAG_RESOLVE_AT_MSTAR if resolve_at_mstar else 0)
                    | (FLAG_PLAIN_CG if plain_cg else 0))
+        o.coarse_nodes = int(coarse_nodes)
         o.stream = C.c_void_p(int(stream))
         h = C.c_void_p()
         mat = material_struct(material)
