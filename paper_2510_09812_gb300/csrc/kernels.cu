@@ -101,7 +101,7 @@ __device__ __forceinline__ bool row_valid(const DSeg& G, int seg, int64_t row) {
 
 // y_r(row) = sum_k A(row, k) x_r(col(row, k)) for one row of a scalar SELL matrix, neighbours
 // k = k0, k0 + kstep, ...
-template <typename V, typename X, typename Acc, int NR>
+template <typename V, typename X, typename Acc, int NR, int VAR = 0>
 __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restrict__ val,
                                                 int64_t s, int lane, const X* __restrict__ x,
                                                 int64_t ld, const int (&skip)[NR],
@@ -112,6 +112,31 @@ __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restr
   const V* vp = val + base + lane;
 #pragma unroll
   for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
+  if (VAR == 1 || VAR == 3) {
+    // eight neighbours per round: their columns and values first, then the gathers, then the
+    // FMAs (more loads in flight per thread)
+    for (int kb = k0; kb < len; kb += 8 * kstep) {
+      int j[8];
+      V w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = kb + u * kstep;
+        const bool ok = k < len;
+        j[u] = ok ? __ldcs(cp + (int64_t)k * 32) : 0;
+        w[u] = ok ? __ldcs(vp + (int64_t)k * 32) : V(0);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (!skip[r]) {
+          X g[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(x + r * ld + j[u]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[r] += (Acc)w[u] * (Acc)g[u];
+        }
+    }
+    return;
+  }
 #pragma unroll 4
   for (int k = k0; k < len; k += kstep) {
     const int j = __ldcs(cp + (int64_t)k * 32);
@@ -253,7 +278,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv1(DSell A, co
     int sl, k0, ks;
     unit_row<VAR>(u, lane, s, sl, k0, ks);
     T acc[1];
-    sell_scalar_row<T, T, T, 1>(A, val, s, sl, x, 0, skip, acc, k0, ks);
+    sell_scalar_row<T, T, T, 1, VAR>(A, val, s, sl, x, 0, skip, acc, k0, ks);
     const int64_t row = s * 32 + sl;
     if (unit_combine<VAR>(acc, lane) && row < A.n) y[row] = acc[0];
   }
@@ -458,7 +483,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
       const int64_t row = s * 32 + sl;
       if (B == 1) {
         T acc[NR];
-        sell_scalar_row<T, T, T, NR>(A, val, s, sl, p, ld, skip, acc, k0, ks);
+        sell_scalar_row<T, T, T, NR, VAR>(A, val, s, sl, p, ld, skip, acc, k0, ks);
         if (row == pin) {
 #pragma unroll
           for (int k = 0; k < NR; ++k) acc[k] = T(0);
