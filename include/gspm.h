@@ -49,6 +49,8 @@ extern "C" {
 #define GSPM_ENOCONV 5   /* a CG solve hit max_iter; the state was still advanced (best iterate) */
 #define GSPM_ETIMEOUT 6  /* a bounded device-side wait gave up                                  */
 #define GSPM_ESTATE 7    /* call not valid for this context (e.g. host-only context)           */
+#define GSPM_ENUMERIC 8  /* a step produced a non-finite or zero m** at a magnetic node (for
+                            example from non-finite input); the state is not valid             */
 
 /* ---- enums ------------------------------------------------------------------------------ */
 #define GSPM_HOST 0
@@ -286,9 +288,9 @@ GSPM_API int gspm_get_field(struct gspm_ctx* ctx, int field, double* data, int w
  *   -> Gauss-Seidel stages with (M + eps K) g = M f (x0 = f), giving m*
  *   -> h(m*) (local terms and far field at m*, h~_d and E held) -> (M + alpha eps K) m** = M f
  *   -> m = m** / |m**| on magnetic nodes.
- * stats may be NULL (then the call may return before the GPU finishes, except for the
- * convergence checks of the CG loops, which read one flag per solve).  Returns GSPM_ENOCONV if
- * any solve hit max_iter (the state is still advanced). */
+ * The call synchronises with its stream before returning.  Returns GSPM_ENOCONV if any solve
+ * hit max_iter (the state is still advanced), GSPM_ENUMERIC if a projection met a non-finite or
+ * zero m** at a magnetic node (the state is then not valid). */
 GSPM_API int gspm_step(struct gspm_ctx* ctx, int n_steps, const double H_ext[3],
                        gspm_step_stats* stats);
 

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "kernels.cuh"
 #include "mpnn.cuh"
@@ -45,6 +47,14 @@ void set_error(const char* fmt, ...) {
     int s_ = (call);             \
     if (s_ != GSPM_OK) return s_; \
   } while (0)
+
+// NVTX range for tools (Nsight); a no-op when no tool is attached
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
 
 // launch with optional event timing of its kernel class
 #define TK(cls, call) ST(timed((cls), [&]() -> int { CK(call); return GSPM_OK; }))
@@ -131,6 +141,7 @@ class Engine final : public EngineBase {
     if (body_stream_) cudaStreamDestroy(body_stream_);
     if (host_graph_) cudaFreeHost(host_graph_);
     if (host_state_) cudaFreeHost(host_state_);
+    if (host_bad_) cudaFreeHost(host_bad_);
     if (host_active_) cudaFreeHost(host_active_);
     if (host_scal_) cudaFreeHost(host_scal_);
     for (cudaEvent_t e : prof_ev_) cudaEventDestroy(e);
@@ -215,6 +226,9 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&tout_, 3 * ld));
     ST(mem_.alloc(&cg_, (int64_t)kSolveSlots * nseg_));
     ST(mem_.alloc(&proj_, 6 * (int64_t)nseg_));
+    ST(mem_.alloc(&bad_, (int64_t)nseg_));
+    CK(cudaMemset(bad_, 0, nseg_ * sizeof(int)));
+    CK(cudaMallocHost(&host_bad_, nseg_ * sizeof(int)));
     ST(mem_.alloc(&pinsave_, 3 * (int64_t)nseg_));
     ST(mem_.alloc(&wmean_, n));
     {
@@ -353,7 +367,13 @@ class Engine final : public EngineBase {
         host_scal_[3 * s + a] = (per_segment ? H[3 * s + a] : H[a]) / P_.Ms;
     CK(cudaMemcpyAsync(hz(), host_scal_, 3 * nseg_ * sizeof(double), cudaMemcpyHostToDevice,
                        L_.stream));
-    if (graph_on_ && prof_mask_ == 0) return step_graph(n_steps, D, printed, st);
+    CK(cudaMemsetAsync(bad_, 0, nseg_ * sizeof(int), L_.stream));
+    if (graph_on_ && prof_mask_ == 0) {
+      const int rc = step_graph(n_steps, D, printed, st);
+      if (rc != GSPM_OK && rc != GSPM_ENOCONV) return rc;
+      ST(check_finite());
+      return rc;
+    }
     std::vector<gspm_step_stats> acc(nseg_);
     for (auto& a : acc) memset(&a, 0, sizeof(a));
     StepInfo si;
@@ -398,13 +418,28 @@ class Engine final : public EngineBase {
       }
     }
     CK(cudaGetLastError());
+    ST(check_finite());
     return noconv ? GSPM_ENOCONV : GSPM_OK;
+  }
+
+  // GSPM_ENUMERIC if a projection of this call met a non-finite or zero m** (synchronises)
+  int check_finite() {
+    CK(cudaMemcpyAsync(host_bad_, bad_, nseg_ * sizeof(int), cudaMemcpyDeviceToHost, L_.stream));
+    CK(cudaStreamSynchronize(L_.stream));
+    for (int sg = 0; sg < nseg_; ++sg)
+      if (host_bad_[sg] > 0) {
+        set_error("step: m** not finite or zero at %d magnetic nodes of mesh %d", host_bad_[sg],
+                  sg);
+        return GSPM_ENUMERIC;
+      }
+    return GSPM_OK;
   }
 
   // The kernel sequence of one GSPM step (Algorithm B.1 with the field and equilibrium solves
   // of Sec. 2).  While a graph is being captured the CG loops become WHILE nodes and `si` is
   // left alone.
   int step_once(const DevParams& D, int printed, StepInfo* si) {
+    Trace trace_step("gspm_step");
     const int64_t n = n_, ld = ld_;
     // a1 volume average of m (Sec. 2.4)
     TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, m_, ld, 1, nullptr, w_, mbar(), nullptr, red_));
@@ -463,7 +498,7 @@ class Engine final : public EngineBase {
     ST(solve_gs(kSlotGsD, Aaeps_, 0, 3, &ig[ngs]));
     ngs += 3;
     // a13 projection and <|dm|>
-    TK(GSPM_KCLASS_POINTWISE, launch_project<T>(L_, SG_, ld, x_, mag_, m_, dmv(), inv_nmag(), red_));
+    TK(GSPM_KCLASS_POINTWISE, launch_project<T>(L_, SG_, ld, x_, mag_, m_, dmv(), inv_nmag(), red_, bad_));
     si->ngs = ngs;
     return GSPM_OK;
   }
@@ -495,6 +530,7 @@ class Engine final : public EngineBase {
   }
 
   int build_graph(const DevParams& D, int printed) {
+    Trace trace("gspm_graph_capture");
     ST(graph_alloc());
     if (gexec_) {
       CK(cudaGraphExecDestroy(gexec_));
@@ -1080,6 +1116,7 @@ class Engine final : public EngineBase {
   // K x = b for the pinned Omega_c systems (B = 1 scalar K^ms, B = 9 block K^mech)
   int solve_general(int slot, const T* val, int B, const T* b, T* x, double rtol,
                     std::vector<SolveInfo>* info) {
+    Trace trace(B == 9 ? "cg_mech" : "cg_ms");
     CGState* st = cg_ + (int64_t)slot * nseg_;
     int* na = nactive_ + slot;
     const int epr = B == 9 ? 3 : 1;
@@ -1133,6 +1170,7 @@ class Engine final : public EngineBase {
   // (M + c eps K) g = M f for nr right-hand sides held in x slots [slot0, slot0 + nr); info[k]
   // receives, per segment, the solve of right-hand side k
   int solve_gs(int slot, const T* aval, int slot0, int nr, std::vector<SolveInfo>* info) {
+    Trace trace(aval == Aeps_ ? "cg_gs_eps" : "cg_gs_alpha_eps");
     CGState* st = cg_ + (int64_t)slot * nseg_;
     int* na = nactive_ + slot;
     T* x = x_ + slot0 * ld_;
@@ -1497,6 +1535,8 @@ class Engine final : public EngineBase {
   double* wmean_ = nullptr;  // [n] 1 / (rows of the row's segment), 0 on padding rows
   double* proj_ = nullptr;   // [6 nseg] per-segment means of b, then pinned values of x
   T* pinsave_ = nullptr;     // [3 nseg]
+  int* bad_ = nullptr;       // [nseg] non-finite or zero m** met by the projection
+  int* host_bad_ = nullptr;  // pinned copy
   // two-level preconditioner
   bool pc_ = false;
   DCoarse CC_{};

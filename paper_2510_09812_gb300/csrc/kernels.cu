@@ -1329,11 +1329,13 @@ __global__ void __launch_bounds__(kBlock) k_gs_stage(int64_t n, int64_t ld, int 
 // Algorithm B.1 step 4: m = m** / |m**| on Omega_m; <|m_new - m_old|> over each segment's
 // magnetic nodes
 template <typename T>
+// (bad[seg] counts the segment's magnetic nodes whose m** is not finite or is zero: the step's
+// state is then not valid)
 __global__ void __launch_bounds__(kBlock) k_project(DSeg G, ItemList IL, int64_t ld, const T* __restrict__ x,
                                                     const uint8_t* __restrict__ mag,
                                                     T* __restrict__ m, double* dm_out,
                                                     const double* __restrict__ inv_nmag,
-                                                    Red red) {
+                                                    Red red, int* bad) {
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
     double v[1] = {0.0};
@@ -1341,7 +1343,9 @@ __global__ void __launch_bounds__(kBlock) k_project(DSeg G, ItemList IL, int64_t
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       if (!mag[i]) continue;
       const T a = x[i], b = x[ld + i], c = x[2 * ld + i];
-      const T inv = T(1) / sqrt(a * a + b * b + c * c);
+      const T n2 = a * a + b * b + c * c;
+      if (!(n2 > T(0)) || !isfinite(n2)) atomicAdd(bad + seg, 1);
+      const T inv = T(1) / sqrt(n2);
       const T na = a * inv, nb = b * inv, nc = c * inv;
       const T da = na - m[i], db = nb - m[ld + i], dc = nc - m[2 * ld + i];
       v[0] += (double)sqrt(da * da + db * db + dc * dc);
@@ -1801,11 +1805,11 @@ cudaError_t launch_gs_stage(const Launch& L, int64_t n, int64_t ld, int stage, i
 template <typename T>
 cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* x,
                            const uint8_t* mag, T* m, double* dm_out, const double* inv_nmag,
-                           Red red) {
+                           Red red, int* bad) {
   (*L.counter) += 1;
   auto k = k_project<T>;
   const ItemGrid ig = GSPM_IGRID(L, G, k);
-  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, ld, x, mag, m, dm_out, inv_nmag, red);
+  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, ld, x, mag, m, dm_out, inv_nmag, red, bad);
   return cudaGetLastError();
 }
 
@@ -1898,7 +1902,7 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
   template cudaError_t launch_gs_stage<T>(const Launch&, int64_t, int64_t, int, int, const T*,    \
                                           const T*, double, T*, T*);                              \
   template cudaError_t launch_project<T>(const Launch&, const DSeg&, int64_t, const T*,           \
-                                         const uint8_t*, T*, double*, const double*, Red);        \
+                                         const uint8_t*, T*, double*, const double*, Red, int*);  \
   template cudaError_t launch_import<T>(const Launch&, int64_t, int, const double*,               \
                                         const int64_t*, T*, int64_t, int64_t, const uint8_t*);    \
   template cudaError_t launch_export<T>(const Launch&, int64_t, int, const T*, int64_t, int64_t,  \

@@ -211,7 +211,7 @@ cudaError_t launch_gs_stage(const Launch& L, int64_t n, int64_t ld, int stage, i
 template <typename T>
 cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* x,
                            const uint8_t* mag, T* m, double* dm_out, const double* inv_nmag,
-                           Red red);  // dm_out[seg]
+                           Red red, int* bad);  // dm_out[seg]; bad[seg] += non-finite or zero m**
 
 template <typename T>
 cudaError_t launch_import(const Launch& L, int64_t n, int nc, const double* src,

@@ -14,7 +14,7 @@ import numpy as np
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgspm.so")
 
-OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE = range(8)
+OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE, ENUMERIC = range(9)
 HOST, DEVICE = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
 ORDER_NONE, ORDER_RCM = 0, 1
