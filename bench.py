@@ -178,7 +178,8 @@ def run_batch(gspm, torch, args, barrier):
     H = np.array([c["H"] for c in members])
     t0 = time.perf_counter()
     ctx = gspm.Context(meshes, members[0]["material"], members[0]["dt"], members[0]["alpha"],
-                       precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7)
+                       precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
+                       coarse_nodes=args.batch_coarse_nodes)
     t_load = time.perf_counter() - t0
     m_all = np.concatenate([c["m0"] for c in members])
     ctx.set_field(gspm.FIELD_M, m_all)
@@ -568,6 +569,8 @@ def main():
                     help="solve the pinned systems of Sec. 2.5 instead of the singular form")
     ap.add_argument("--coarse-nodes", type=int, default=0,
                     help="nodes per aggregate of the two-level preconditioner (0: default)")
+    ap.add_argument("--batch-coarse-nodes", type=int, default=0,
+                    help="nodes per aggregate in the batched workload's meshes (0: default)")
     ap.add_argument("--plain-cg", action="store_true",
                     help="no two-level preconditioner for the K^ms / K^mech solves")
     ap.add_argument("--skip-cpu", action="store_true")

@@ -53,7 +53,9 @@ def test_checkpoint_resume_is_bitwise(gspm_lib, mesh, prec):
 @pytest.mark.parametrize("graph", [False, True])
 def test_non_finite_state_is_reported_and_recoverable(gspm_lib, mesh, graph):
     g = gspm_lib
-    ctx = _ctx(g, mesh, "mixed", max_iter=50, graph=graph)
+    # a NaN right-hand side ends each CG after one iteration (p.q is NaN: the solve stops), so
+    # the ordinary iteration cap applies
+    ctx = _ctx(g, mesh, "mixed", graph=graph)
     m0 = synth.random_unit_m(mesh.n_unique, 93)
     bad = m0.copy()
     bad[::7] = np.nan  # some of these are magnetic nodes
