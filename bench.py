@@ -162,6 +162,20 @@ def cpu_oracle_sample(wall_budget=25.0, steps=None, warmup=1):
     return (1.0 / per) * (wm.n / full_n), per, desc, k
 
 
+def cpu_oracle_sample_1core(steps=None, warmup=1):
+    """cpu_oracle_sample in a fresh child process with one BLAS / OpenMP thread, so that the
+    sample runs on exactly one core."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_oracle_sample(steps=%r, warmup=%r)))"
+            % (ROOT, steps, warmup))
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, check=True,
+                         capture_output=True, text=True).stdout
+    rate, per, desc, k = json.loads(out.strip().splitlines()[-1])
+    return rate, per, desc, k
+
+
 def run_batch(gspm, torch, args, barrier):
     """64 independent meshes of log-uniform size 2k-200k nodes, each with its own inclusion and
     applied field, stepped together (mixed precision) by gspm_batch_step with graph replay (and
@@ -300,7 +314,7 @@ def run_reference(args):
     if rank != 0:
         return
     per_steps = []
-    rate, per, desc, k = cpu_oracle_sample(steps=args.steps, warmup=args.warmup)
+    rate, per, desc, k = cpu_oracle_sample_1core(steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak",
@@ -512,7 +526,7 @@ def run_ours(args):
         return
     cpu = None
     if ws == 1 and not args.skip_cpu:
-        rate, per, desc, k = cpu_oracle_sample()
+        rate, per, desc, k = cpu_oracle_sample_1core()
         cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
