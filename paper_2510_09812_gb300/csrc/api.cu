@@ -1124,12 +1124,15 @@ class Engine final : public EngineBase {
     double* bmean = proj_;
     double* xpin = proj_ + 3 * nseg_;
     CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
-    // x0 moved to zero at the pinned node: the pinned system (Sec. 2.5) needs it, and for the
-    // singular system it removes any large constant from x0, whose product with K would only
-    // add rounding noise to the residual
-    TK(GSPM_KCLASS_CG_INIT, launch_pin_shift<T>(L_, A_, SG_, epr, x, xpin));
-    if (!pinned_) {
-      // the consistent singular system: b minus its per-segment mean of each component
+    if (pinned_) {
+      // the pinned system (Sec. 2.5): x0 moved to zero at the pinned node
+      TK(GSPM_KCLASS_CG_INIT, launch_pin_shift<T>(L_, A_, SG_, epr, x, xpin));
+    } else {
+      // the consistent singular system: x0 minus its per-segment mean of each component (the
+      // constants only add rounding noise to K x0: with K in FP32, K 1 is not 0), and b minus
+      // its mean
+      TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, x, 1, epr, nullptr, wmean_, xpin, nullptr, red_));
+      TK(GSPM_KCLASS_CG_INIT, launch_seg_shift<T>(L_, A_, SG_, epr, x, xpin));
       TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, b, 1, epr, nullptr, wmean_, bmean, nullptr, red_));
     }
     // two-level preconditioned CG on the singular systems (the pinned form stays plain)
@@ -1145,6 +1148,8 @@ class Engine final : public EngineBase {
     };
     TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_, pinned_ ? nullptr : bmean, pinned_, pc ? 1 : 0));
     if (pc) ST(precondition(p_, 1));
+    // singular system: p0 projected off the constants
+    if (!pinned_) TK(GSPM_KCLASS_CG_INIT, launch_cg_psub<T>(L_, A_, SG_, epr, p_, st));
     auto iter = [&]() -> int {
       TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_, pinned_));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, epr, 1, len, x, r_, p_, q_, st, na, red_));

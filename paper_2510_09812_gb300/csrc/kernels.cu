@@ -336,6 +336,8 @@ __device__ __forceinline__ void cg_start(CGState* st, int* nactive, int nr, cons
   st->noconv = 0;
   st->zero_x = allow_zero_x ? zero : 0;
   st->pc = pc;
+  st->proj = 0;
+  for (int a = 0; a < 3; ++a) st->sr[a] = st->sub[a] = 0.0;
   if (any) atomicAdd(nactive, 1);
 }
 
@@ -361,7 +363,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
     double bm[NC];
 #pragma unroll
     for (int a = 0; a < NC; ++a) bm[a] = bmean ? bmean[NC * seg + a] : 0.0;
-    double v[2] = {0.0, 0.0};  // rr, bb
+    double v[2 + NC];  // rr, bb, per-component sums of r
+#pragma unroll
+    for (int a = 0; a < 2 + NC; ++a) v[a] = 0.0;
     for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
       const int64_t row = s * 32 + lane;
       const bool ok = row_valid(G, seg, row);
@@ -378,6 +382,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
           p[row] = rv;
           v[0] += (double)rv * (double)rv;
           v[1] += bv * bv;
+          v[2] += (double)rv;
         }
       } else {
         double acc[3];
@@ -391,14 +396,28 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
             p[3 * row + a] = rv;
             v[0] += (double)rv * (double)rv;
             v[1] += bv * bv;
+            v[2 + a] += (double)rv;
           }
         }
       }
     }
-    __shared__ double res[2];
-    if (seg_reduce<2>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
-      const double bb[1] = {res[1]}, rr[1] = {res[0]};
-      cg_start(st + seg, nactive, 1, bb, rr, rtol, max_iter, 1, pc);
+    __shared__ double res[2 + NC];
+    if (seg_reduce<2 + NC>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+      // projected form: r.r without the constant part of r, p0 = r0 minus its mean
+      const double inv_n = 1.0 / (double)G.seg_nrow[seg];
+      double s2 = 0.0;
+      for (int a = 0; a < NC; ++a) s2 += res[2 + a] * res[2 + a];
+      const double rrp = res[0] - s2 * inv_n;
+      const double bb[1] = {res[1]}, rr[1] = {bmean ? (rrp > 0.0 ? rrp : 0.0) : res[0]};
+      CGState* sg = st + seg;
+      cg_start(sg, nactive, 1, bb, rr, rtol, max_iter, 1, pc);
+      if (bmean) {
+        sg->proj = 1;
+        for (int a = 0; a < NC; ++a) {
+          sg->sr[a] = res[2 + a];
+          sg->sub[a] = res[2 + a] * inv_n;
+        }
+      }
     }
   }
 }
@@ -580,11 +599,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
       skip[k] = sg->r[k].done;
       al[k] = (T)sg->r[k].alpha;
     }
+    const bool proj = NR == 1 && sg->proj;
     // r.r, then r.D^-1 r: each thread sums its elements (a few hundred at most) in T, the
-    // block and the items in FP64
-    T tv[2 * NR];
+    // block and the items in FP64; projected form: also the sums of r per component (element
+    // e of the item has component e mod epr: item ranges start at whole rows)
+    T tv[2 * NR + 3];
 #pragma unroll
-    for (int k = 0; k < 2 * NR; ++k) tv[k] = T(0);
+    for (int k = 0; k < 2 * NR + 3; ++k) tv[k] = T(0);
     int64_t e0, e1;
     item_elems(G, IL, item, seg, epr, e0, e1);
     int64_t etail = e0;
@@ -593,6 +614,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
       for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
         T dv[W];
         if (dinv) ld16(dinv + e0 + t * W, dv);
+        const int cb = epr == 3 ? (int)((t * W) % 3) : 0;
 #pragma unroll
         for (int k = 0; k < NR; ++k)
           if (!skip[k]) {
@@ -608,6 +630,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
               rv[c] -= al[k] * qv[c];
               tv[k] += rv[c] * rv[c];
               if (dinv) tv[NR + k] += rv[c] * dv[c] * rv[c];
+              if (proj) {
+                const int cc = epr == 3 ? (cb + c >= 3 ? cb + c - 3 : cb + c) : 0;
+                tv[2 * NR] += cc == 0 ? rv[c] : T(0);
+                tv[2 * NR + 1] += cc == 1 ? rv[c] : T(0);
+                tv[2 * NR + 2] += cc == 2 ? rv[c] : T(0);
+              }
             }
             st16(x + o, xv);
             st16(r + o, rv);
@@ -626,26 +654,45 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
           r[o] = rv;
           tv[k] += rv * rv;
           tv[NR + k] += rv * d * rv;
+          if (proj) {
+            const int cc = (int)(i % epr);
+            tv[2 * NR] += cc == 0 ? rv : T(0);
+            tv[2 * NR + 1] += cc == 1 ? rv : T(0);
+            tv[2 * NR + 2] += cc == 2 ? rv : T(0);
+          }
         }
     }
-    double v[2 * NR];
+    double v[2 * NR + 3];
 #pragma unroll
-    for (int k = 0; k < 2 * NR; ++k) v[k] = (double)tv[k];
-    __shared__ double res[2 * NR];
-    if (seg_reduce<2 * NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+    for (int k = 0; k < 2 * NR + 3; ++k) v[k] = (double)tv[k];
+    __shared__ double res[2 * NR + 3];
+    if (seg_reduce<2 * NR + 3>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       int any = 0;
       for (int k = 0; k < NR; ++k) {
         CGRhs& c = sg->r[k];
         if (c.done) continue;
         c.iters += 1;
+        double rrk = res[k];
+        if (proj) {
+          // r.r without r's constant part; plain CG subtracts r's mean in the p-update
+          const double inv_n = 1.0 / (double)G.seg_nrow[seg];
+          double s2 = 0.0;
+          for (int a = 0; a < 3; ++a) {
+            sg->sr[a] = res[2 * NR + a];
+            s2 += res[2 * NR + a] * res[2 * NR + a];
+            if (sg->pc == 0) sg->sub[a] = res[2 * NR + a] * inv_n;
+          }
+          rrk -= s2 * inv_n;
+          rrk = rrk > 0.0 ? rrk : 0.0;
+        }
         if (sg->pc == 0) {
-          c.beta = res[k] / c.rr;
+          c.beta = rrk / c.rr;
         } else if (sg->pc == 2) {
           c.beta = c.rz != 0.0 ? res[NR + k] / c.rz : 0.0;
           c.rz = res[NR + k];
         }  // pc 1: beta from r.z in k_pcg_z
-        c.rr = res[k];
-        if (res[k] < c.tol2) {
+        c.rr = rrk;
+        if (rrk < c.tol2) {
           c.done = 1;
         } else if (c.iters >= sg->max_iter) {
           c.done = 1;
@@ -686,6 +733,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
       skip[k] = sg->r[k].done;
       be[k] = (T)sg->r[k].beta;
     }
+    // projected form: the input's mean per component comes off (element e of the item has
+    // component e mod epr)
+    T sb[3] = {T(0), T(0), T(0)};
+    if (NR == 1 && sg->proj)
+      for (int a = 0; a < 3; ++a) sb[a] = (T)sg->sub[a];
     int64_t e0, e1;
     item_elems(G, IL, item, seg, epr, e0, e1);
     int64_t etail = e0;
@@ -694,6 +746,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
       for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
         T dv[W];
         if (dinv) ld16(dinv + e0 + t * W, dv);
+        const int cb = epr == 3 ? (int)((t * W) % 3) : 0;
 #pragma unroll
         for (int k = 0; k < NR; ++k)
           if (!skip[k]) {
@@ -702,7 +755,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
             ld16(r + o, rv);
             ld16(p + o, pv);
 #pragma unroll
-            for (int c = 0; c < W; ++c) pv[c] = (dinv ? dv[c] * rv[c] : rv[c]) + be[k] * pv[c];
+            for (int c = 0; c < W; ++c) {
+              const int cc = epr == 3 ? (cb + c >= 3 ? cb + c - 3 : cb + c) : 0;
+              const T sub = cc == 0 ? sb[0] : (cc == 1 ? sb[1] : sb[2]);
+              pv[c] = ((dinv ? dv[c] * rv[c] : rv[c]) - sub) + be[k] * pv[c];
+            }
             st16(p + o, pv);
           }
       }
@@ -710,11 +767,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
     }
     for (int64_t i = etail + threadIdx.x; i < e1; i += blockDim.x) {
       const T d = dinv ? dinv[i] : T(1);
+      const int cc = (int)(i % epr);
+      const T sub = cc == 0 ? sb[0] : (cc == 1 ? sb[1] : sb[2]);
 #pragma unroll
       for (int k = 0; k < NR; ++k)
         if (!skip[k]) {
           const int64_t o = k * ld + i;
-          p[o] = d * r[o] + be[k] * p[o];
+          p[o] = (d * r[o] - sub) + be[k] * p[o];
         }
     }
   }
@@ -741,6 +800,20 @@ __global__ void __launch_bounds__(kBlock) k_pin_shift(DSell A, DSeg G, int epr, 
     const int seg = G.seg_of_slice[row >> 5];
     if (!row_valid(G, seg, row)) continue;
     x[e] = (T)((double)x[e] - xp[seg * epr + (int)(e - row * epr)]);
+  }
+}
+
+// p(i, c) -= st[seg].sub[c] on the active segments of the projected CG (p0 = z0 minus its mean)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_psub(DSell A, DSeg G, int epr, T* __restrict__ p,
+                                                    const CGState* __restrict__ st) {
+  const int64_t len = (int64_t)A.nslices * 32 * epr;
+  for (int64_t e = gtid(); e < len; e += gstride()) {
+    const int64_t row = e / epr;
+    const int seg = G.seg_of_slice[row >> 5];
+    const CGState& sg = st[seg];
+    if (!row_valid(G, seg, row) || !sg.active || !sg.proj) continue;
+    p[e] -= (T)sg.sub[e - row * epr];
   }
 }
 
@@ -877,7 +950,10 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
     const int seg = IL.seg[item];
     CGState* sg = st + seg;
     if (!sg->active) continue;
-    double v[1] = {0.0};
+    const bool proj = sg->proj;
+    double v[1 + EPR];  // r.z, per-component sums of z (projected form)
+#pragma unroll
+    for (int a = 0; a < 1 + EPR; ++a) v[a] = 0.0;
     const int64_t r0 = (int64_t)IL.sl0[item] * 32;
     const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
     const int64_t rhi = (int64_t)IL.sl1[item] * 32;
@@ -890,7 +966,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
       ldn<T, N>(dinv + row * EPR, dv);
       const int4 ag = *reinterpret_cast<const int4*>(C.agg_of_row + row);
       const int agv[4] = {ag.x, ag.y, ag.z, ag.w};
-      T rz = T(0);
+      T rz = T(0), zs[EPR];
+#pragma unroll
+      for (int a = 0; a < EPR; ++a) zs[a] = T(0);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -898,9 +976,14 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
           const int e = u * EPR + a;
           zv[e] = dv[e] * rv[e] + ec[(int64_t)agv[u] * EPR + a];
           rz += rv[e] * zv[e];
+          zs[a] += zv[e];
         }
       stn<T, N>(z + row * EPR, zv);
       v[0] += (double)rz;
+      if (proj) {
+#pragma unroll
+        for (int a = 0; a < EPR; ++a) v[1 + a] += (double)zs[a];
+      }
     }
     for (int64_t row = r0 + 4 * ng + threadIdx.x; row < r1; row += blockDim.x) {
       const int64_t I = C.agg_of_row[row];
@@ -911,16 +994,27 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
         const T zv = dinv[e] * rv + ec[I * EPR + a];
         z[e] = zv;
         v[0] += (double)rv * (double)zv;
+        v[1 + a] += (double)zv;
       }
     }
-    __shared__ double res[1];
-    if (seg_reduce<1>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+    __shared__ double res[1 + EPR];
+    if (seg_reduce<1 + EPR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       CGRhs& c = sg->r[0];
+      double rz = res[0];
+      if (proj) {
+        // z projected off the constants (the p-update subtracts its mean): r.(z - zbar 1)
+        const double inv_n = 1.0 / (double)G.seg_nrow[seg];
+        for (int a = 0; a < EPR; ++a) {
+          const double zbar = res[1 + a] * inv_n;
+          rz -= zbar * sg->sr[a];
+          sg->sub[a] = zbar;
+        }
+      }
       if (init) {
-        c.rz = res[0];
+        c.rz = rz;
       } else if (!c.done) {
-        c.beta = c.rz != 0.0 ? res[0] / c.rz : 0.0;
-        c.rz = res[0];
+        c.beta = c.rz != 0.0 ? rz / c.rz : 0.0;
+        c.rz = rz;
       }
     }
   }
@@ -1718,6 +1812,24 @@ cudaError_t launch_pin_shift(const Launch& L, const DSell& A, const DSeg& G, int
 }
 
 template <typename T>
+cudaError_t launch_seg_shift(const Launch& L, const DSell& A, const DSeg& G, int epr, T* x,
+                             const double* xs) {
+  (*L.counter) += 1;
+  auto k = k_pin_shift<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32 * epr, k), kBlock, 0, L.stream>>>(A, G, epr, x, xs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_psub(const Launch& L, const DSell& A, const DSeg& G, int epr, T* p,
+                           const CGState* st) {
+  (*L.counter) += 1;
+  auto k = k_cg_psub<T>;
+  k<<<GSPM_GRID(L, A.nslices * 32 * epr, k), kBlock, 0, L.stream>>>(A, G, epr, p, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_cg_zero(const Launch& L, const DSeg& G, int epr, T* x, const CGState* st) {
   (*L.counter) += 1;
   auto k = k_cg_zero<T>;
@@ -1892,6 +2004,10 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
                                       const T*, T*, int);                                         \
   template cudaError_t launch_pin_shift<T>(const Launch&, const DSell&, const DSeg&, int, T*,     \
                                            double*);                                              \
+  template cudaError_t launch_seg_shift<T>(const Launch&, const DSell&, const DSeg&, int, T*,     \
+                                           const double*);                                        \
+  template cudaError_t launch_cg_psub<T>(const Launch&, const DSell&, const DSeg&, int, T*,       \
+                                         const CGState*);                                         \
   template cudaError_t launch_e0<T>(const Launch&, int64_t, const T*, int64_t, const uint8_t*,    \
                                     const DevParams&, T*, T*);                                    \
   template cudaError_t launch_hfield<T>(const Launch&, int64_t, const DSeg&, const T*, const T*,  \

@@ -57,7 +57,12 @@ struct CGRhs {
 };
 struct CGState {
   CGRhs r[3];
-  int nr, active, max_iter, noconv, zero_x, pc, pad[2];  // pc: preconditioned (one RHS)
+  int nr, active, max_iter, noconv, zero_x, pc;  // pc: preconditioned (one RHS)
+  // proj: CG on the singular system projected off the constants (one right-hand side):
+  // sr = per-component sums of r, sub = the per-component mean that the p-update subtracts
+  // from its input (z, or r without preconditioner)
+  int proj, pad;
+  double sr[3], sub[3];
 };
 
 // Aggregates of the two-level preconditioner, all segments: rows of aggregate I are
@@ -132,7 +137,12 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
 // CG pieces.  st and the arrival counters are per segment; nactive counts active segments.
 // epr = elements per row of the vectors (1: scalar, SoA with stride ld; 3: [n][3]).
 // bmean != NULL: solve the consistent singular system with b projected off the constants
-// (bmean = per-segment mean of each component); pinned: the pinned system (Sec. 2.5).
+// (bmean = per-segment mean of each component) by CG projected off the constants: r.r is taken
+// without r's constant part, and every search direction has its mean removed (the p-update
+// subtracts st.sub; after init, launch_cg_psub does it for p0).  In exact arithmetic these
+// means are zero (K 1 = 0); with K rounded to FP32 K 1 is not, and without the projection the
+// iteration would chase the constants, along which K has no curvature.
+// pinned: the pinned system (Sec. 2.5).
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
@@ -150,6 +160,14 @@ cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const
 template <typename T>
 cudaError_t launch_pin_shift(const Launch& L, const DSell& A, const DSeg& G, int epr, T* x,
                              double* xp);
+// x(i, c) -= xs[seg * epr + c] over each segment's rows
+template <typename T>
+cudaError_t launch_seg_shift(const Launch& L, const DSell& A, const DSeg& G, int epr, T* x,
+                             const double* xs);
+// p(i, c) -= st[seg].sub[c] for the active segments that run the projected CG
+template <typename T>
+cudaError_t launch_cg_psub(const Launch& L, const DSell& A, const DSeg& G, int epr, T* p,
+                           const CGState* st);
 template <typename T>
 cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, int64_t ld, T* x,
                              T* r, const T* p, const T* q, CGState* st, int* nactive, Red red,
