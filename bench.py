@@ -534,7 +534,9 @@ def run_ours(args):
         "dtype": "f32/f64" if precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": wl, "nodes": n, "tets": info["n_tets"],
                    "magnetic_nodes": info["n_magnetic_nodes"], "precision": precision,
-                   "ordering": args.ordering, "field_A_per_m": list(map(float, H)),
+                   "ordering": (args.ordering if args.ordering != "auto" else
+                                ("none" if (args.plain_cg or args.pinned_cg) else "aggregate")),
+                   "field_A_per_m": list(map(float, H)),
                    "dt_s": cfg["dt"], "alpha": cfg["alpha"], "rtol": 1e-7,
                    "l2": f"inputs > L2: {info['device_bytes'] / 1e9:.2f} GB resident, "
                          "no flush needed",
@@ -574,7 +576,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
-    ap.add_argument("--ordering", default="none", choices=["none", "rcm"])
+    ap.add_argument("--ordering", default="auto", choices=["auto", "none", "rcm", "aggregate"])
     ap.add_argument("--cells", default=None, help="smaller mesh of the same recipe, e.g. 64,64,16")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-graph", action="store_true")

@@ -57,11 +57,17 @@ extern "C" {
 #define GSPM_DEVICE 1
 
 #define GSPM_PREC_F64 0    /* plain double precision everywhere                               */
-#define GSPM_PREC_MIXED 1  /* FP32 matrices, SpMV, assembly and pointwise work; FP64 CG inner
-                              products, residual norms, CG iterates x and r, volume averages    */
+#define GSPM_PREC_MIXED 1  /* FP32 matrices, vectors, SpMV, assembly and pointwise work; FP64
+                              CG scalars (inner products, residual norms, alpha, beta) and
+                              volume averages                                                   */
 
 #define GSPM_ORDER_NONE 0  /* keep the unique-node numbering                                   */
 #define GSPM_ORDER_RCM 1   /* reverse Cuthill-McKee renumbering (tie-breaks documented below)  */
+#define GSPM_ORDER_AGGREGATE 2 /* nodes grouped by the aggregates of the two-level preconditioner
+                              (coordinate bins of coarse_nodes nodes, see gspm_options): bins in
+                              x-fastest order, unique index ascending within a bin.  Each
+                              aggregate is then a contiguous range of rows, which the
+                              restriction reads in order                                       */
 
 #define GSPM_FLAG_HOST_ONLY 1u        /* build host structures only; no CUDA call is made      */
 #define GSPM_FLAG_ROW2_PRINTED 2u     /* Algorithm B.1 second row exactly as printed (m^n_1,

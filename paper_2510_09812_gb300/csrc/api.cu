@@ -88,6 +88,23 @@ struct SolveInfo {
   int noconv = 0;
 };
 
+// Rounding of the coarse inverse to its storage type: doubles as they are; bfloat16 (its bits in
+// a uint16_t) by round-to-nearest-even of the float value (finite values)
+template <typename S>
+S to_store(double v);
+template <>
+inline double to_store<double>(double v) {
+  return v;
+}
+template <>
+inline uint16_t to_store<uint16_t>(double v) {
+  const float f = (float)v;
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof(u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
 class EngineBase {
  public:
   virtual ~EngineBase() = default;
@@ -1137,12 +1154,14 @@ class Engine final : public EngineBase {
     }
     // two-level preconditioned CG on the singular systems (the pinned form stays plain)
     const bool pc = pc_ && !pinned_;
-    const T* cinv = epr == 3 ? cinv3_ : cinv1_;
+    const typename CoarseStore<T>::type* cinv = epr == 3 ? cinv3_ : cinv1_;
     const int64_t* coff = epr == 3 ? inv_off3_ : inv_off1_;
+    const int64_t* rco = epr == 3 ? rc_off3_ : rc_off1_;
+    const ItemList& GL = epr == 3 ? GL3_ : GL1_;
     const T* dinv = epr == 3 ? dinv3_ : dinv1_;
     auto precondition = [&](T* z, int init) -> int {
-      TK(GSPM_KCLASS_CG_VEC, launch_restrict<T>(L_, CC_, epr, r_, rc_));
-      TK(GSPM_KCLASS_CG_VEC, launch_coarse_gemv<T>(L_, CC_, epr, cinv, coff, rc_, ec_));
+      TK(GSPM_KCLASS_CG_VEC, launch_restrict<T>(L_, CC_, epr, r_, rco, rc_));
+      TK(GSPM_KCLASS_CG_VEC, launch_coarse_gemv<T>(L_, GL, CC_, epr, cinv, coff, rco, rc_, ec_));
       TK(GSPM_KCLASS_CG_VEC, launch_pcg_z<T>(L_, SG_, CC_, epr, r_, dinv, ec_, z, st, init, red_));
       return GSPM_OK;
     };
@@ -1229,21 +1248,32 @@ class Engine final : public EngineBase {
       for (int64_t row = 0; row < n_; ++row)
         if (aor[row] >= 0) arows[fill[aor[row]]++] = (int32_t)row;
     }
+    // blocks of rows padded to coarse_ld values, each block starting at a 16-byte boundary
+    using S16 = typename CoarseStore<T>::type;
     std::vector<int64_t> off3(S), off1(S);
     int64_t t3 = 0, t1 = 0;
     for (int sg = 0; sg < S; ++sg) {
-      // blocks start at multiples of 4 values (16-byte loads in the coarse GEMV)
       const int64_t a = hb_.coarse[sg].n_agg;
-      off3[sg] = (t3 + 3) / 4 * 4;
-      off1[sg] = (t1 + 3) / 4 * 4;
-      t3 = off3[sg] + 9 * a * a;
-      t1 = off1[sg] + a * a;
+      off3[sg] = t3;
+      off1[sg] = t1;
+      t3 += 3 * a * coarse_ld<T>(3 * a);
+      t1 += a * coarse_ld<T>(a);
     }
-    std::vector<T> inv3(t3), inv1(t1), d3(3 * n_, T(0)), d1(n_, T(0));
+    std::vector<S16> inv3(t3, S16(0)), inv1(t1, S16(0));
+    std::vector<T> d3(3 * n_, T(0)), d1(n_, T(0));
+    // symmetric part of the FP64 inverse (its column solves leave the two triangles a few
+    // ulps apart), rounded once to the storage type
+    auto put = [](const std::vector<double>& inv, int64_t nc, S16* dst) {
+      const int64_t ldc = coarse_ld<T>(nc);
+      for (int64_t i = 0; i < nc; ++i)
+        for (int64_t j = 0; j < nc; ++j)
+          dst[i * ldc + j] = to_store<S16>(0.5 * (inv[i * nc + j] + inv[j * nc + i]));
+    };
     for (int sg = 0; sg < S; ++sg) {
       const HostCoarse& hc = hb_.coarse[sg];
-      std::copy(hc.inv_mech.begin(), hc.inv_mech.end(), inv3.begin() + off3[sg]);
-      std::copy(hc.inv_ms.begin(), hc.inv_ms.end(), inv1.begin() + off1[sg]);
+      const int64_t a = hc.n_agg;
+      put(hc.inv_mech, 3 * a, inv3.data() + off3[sg]);
+      put(hc.inv_ms, a, inv1.data() + off1[sg]);
       const int64_t r0 = hb_.seg_row0[sg];
       for (int64_t i = 0; i < hb_.seg_nrow[sg]; ++i) {
         d1[r0 + i] = (T)hc.dinv_ms[i];
@@ -1262,8 +1292,48 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&cinv1_, t1));
     ST(mem_.alloc(&dinv3_, 3 * n_));
     ST(mem_.alloc(&dinv1_, n_));
-    ST(mem_.alloc(&rc_, 3 * na));
+    // rc: per segment a block zero-padded to the coarse row stride (read in whole packs)
+    std::vector<int64_t> rco3(S), rco1(S);
+    int64_t r3 = 0, r1 = 0;
+    for (int sg = 0; sg < S; ++sg) {
+      const int64_t a = hb_.coarse[sg].n_agg;
+      rco3[sg] = r3;
+      rco1[sg] = r1;
+      r3 += coarse_ld<T>(3 * a);
+      r1 += coarse_ld<T>(a);
+    }
+    ST(mem_.alloc(&rc_, std::max(r3, r1)));
+    CK(cudaMemset(rc_, 0, std::max(r3, r1) * sizeof(T)));
+    ST(mem_.alloc(&rc_off3_, S));
+    ST(mem_.alloc(&rc_off1_, S));
+    CK(cudaMemcpy(rc_off3_, rco3.data(), S * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(rc_off1_, rco1.data(), S * 8, cudaMemcpyHostToDevice));
     ST(mem_.alloc(&ec_, 3 * na));
+    // coarse GEMV work items: runs of kBlock / 32 coarse rows per segment (3 and 1 components
+    // per aggregate)
+    for (int e : {3, 1}) {
+      const int rows = kBlock / 32;
+      std::vector<int32_t> iseg, i0, i1, si0(S), sni(S);
+      for (int sg = 0; sg < S; ++sg) {
+        const int64_t c0 = (int64_t)agg0[sg] * e, nc = (int64_t)(agg0[sg + 1] - agg0[sg]) * e;
+        si0[sg] = (int32_t)iseg.size();
+        for (int64_t g = 0; g < nc; g += rows) {
+          iseg.push_back(sg);
+          i0.push_back((int32_t)(c0 + g));
+          i1.push_back((int32_t)(c0 + std::min<int64_t>(nc, g + rows)));
+        }
+        sni[sg] = (int32_t)iseg.size() - si0[sg];
+      }
+      const int ni = (int)iseg.size();
+      int32_t *d_iseg, *d_i0, *d_i1;
+      ST(mem_.alloc(&d_iseg, ni));
+      ST(mem_.alloc(&d_i0, ni));
+      ST(mem_.alloc(&d_i1, ni));
+      CK(cudaMemcpy(d_iseg, iseg.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_i0, i0.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_i1, i1.data(), ni * 4, cudaMemcpyHostToDevice));
+      (e == 3 ? GL3_ : GL1_) = ItemList{ni, d_iseg, d_i0, d_i1, nullptr, nullptr};
+    }
     CK(cudaMemcpy(d_aor, aor.data(), n_ * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_aptr, aptr.data(), (na + 1) * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_arows, arows.data(), arows.size() * 4, cudaMemcpyHostToDevice));
@@ -1271,11 +1341,18 @@ class Engine final : public EngineBase {
     CK(cudaMemcpy(d_agg0, agg0.data(), (S + 1) * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(inv_off3_, off3.data(), S * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(inv_off1_, off1.data(), S * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(cinv3_, inv3.data(), t3 * sizeof(T), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(cinv1_, inv1.data(), t1 * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cinv3_, inv3.data(), t3 * sizeof(S16), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cinv1_, inv1.data(), t1 * sizeof(S16), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dinv3_, d3.data(), 3 * n_ * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dinv1_, d1.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
-    CC_ = DCoarse{na, d_aor, d_aptr, d_arows, d_aseg, d_agg0};
+    int contig = 1;
+    for (int64_t I = 0; I < na && contig; ++I)
+      for (int32_t q = aptr[I]; q < aptr[I + 1]; ++q)
+        if (arows[q] != arows[aptr[I]] + (q - aptr[I])) {
+          contig = 0;
+          break;
+        }
+    CC_ = DCoarse{na, d_aor, d_aptr, d_arows, d_aseg, d_agg0, contig};
     pc_ = true;
     return GSPM_OK;
   }
@@ -1296,6 +1373,48 @@ class Engine final : public EngineBase {
   // keep k blocks resident per SM: about k x SMs items, each segment getting a share
   // proportional to its slices (at least one item, at most one per slice), its slices split
   // evenly, so every block of the single resident wave reduces one item.
+  // Work-item lists over per-segment runs of units (slices, aggregates or coarse rows): unit
+  // u0[s] + i, i < nu[s], of segment s.  List k - 1 serves kernels that keep k blocks resident
+  // per SM: about k x SMs items, each segment getting a share proportional to its units (at
+  // least one item, at most one per unit), its units split evenly.
+  int make_item_lists(const std::vector<int64_t>& u0, const std::vector<int64_t>& nu,
+                      ItemList* lists, int* max_items) {
+    const int S = (int)nu.size();
+    int64_t total = 0;
+    for (int64_t v : nu) total += v;
+    for (int k = 1; k <= kItemLists; ++k) {
+      const double target = (double)k * L_.sms;
+      std::vector<int32_t> iseg, isl0, isl1, sitem0(S), snit(S);
+      for (int sg = 0; sg < S; ++sg) {
+        const int64_t a = u0[sg], n = nu[sg];
+        int64_t ni = std::llround(target * (double)n / (double)std::max<int64_t>(1, total));
+        ni = std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, n), ni));
+        sitem0[sg] = (int32_t)iseg.size();
+        for (int64_t i = 0; i < ni; ++i) {
+          iseg.push_back(sg);
+          isl0.push_back((int32_t)(a + i * n / ni));
+          isl1.push_back((int32_t)(a + (i + 1) * n / ni));
+        }
+        snit[sg] = (int32_t)ni;
+      }
+      const int ni = (int)iseg.size();
+      int32_t *d_iseg, *d_isl0, *d_isl1, *d_si0, *d_sni;
+      ST(mem_.alloc(&d_iseg, ni));
+      ST(mem_.alloc(&d_isl0, ni));
+      ST(mem_.alloc(&d_isl1, ni));
+      ST(mem_.alloc(&d_si0, S));
+      ST(mem_.alloc(&d_sni, S));
+      CK(cudaMemcpy(d_iseg, iseg.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_isl0, isl0.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_isl1, isl1.data(), ni * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_si0, sitem0.data(), S * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_sni, snit.data(), S * 4, cudaMemcpyHostToDevice));
+      lists[k - 1] = ItemList{ni, d_iseg, d_isl0, d_isl1, d_si0, d_sni};
+      *max_items = std::max(*max_items, ni);
+    }
+    return GSPM_OK;
+  }
+
   int init_segments() {
     const int S = nseg_;
     int32_t *d_sos, *d_si0, *d_sni;
@@ -1318,38 +1437,14 @@ class Engine final : public EngineBase {
     g.seg_nrow = d_nr;
     g.seg_pin = d_pin;
     g.counter = d_cnt;
-    int max_items = 0;
-    for (int k = 1; k <= kItemLists; ++k) {
-      const double target = (double)k * L_.sms;
-      std::vector<int32_t> iseg, isl0, isl1, sitem0(S), snit(S);
-      for (int sg = 0; sg < S; ++sg) {
-        const int64_t a = hb_.seg_sl0[sg], nsl = hb_.seg_nsl[sg];
-        int64_t ni = std::llround(target * (double)nsl / (double)nslices_);
-        ni = std::max<int64_t>(1, std::min<int64_t>(nsl, ni));
-        sitem0[sg] = (int32_t)iseg.size();
-        for (int64_t i = 0; i < ni; ++i) {
-          iseg.push_back(sg);
-          isl0.push_back((int32_t)(a + i * nsl / ni));
-          isl1.push_back((int32_t)(a + (i + 1) * nsl / ni));
-        }
-        snit[sg] = (int32_t)ni;
-      }
-      const int ni = (int)iseg.size();
-      int32_t *d_iseg, *d_isl0, *d_isl1;
-      ST(mem_.alloc(&d_iseg, ni));
-      ST(mem_.alloc(&d_isl0, ni));
-      ST(mem_.alloc(&d_isl1, ni));
-      ST(mem_.alloc(&d_si0, S));
-      ST(mem_.alloc(&d_sni, S));
-      CK(cudaMemcpy(d_iseg, iseg.data(), ni * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d_isl0, isl0.data(), ni * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d_isl1, isl1.data(), ni * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d_si0, sitem0.data(), S * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d_sni, snit.data(), S * 4, cudaMemcpyHostToDevice));
-      g.list[k - 1] = ItemList{ni, d_iseg, d_isl0, d_isl1, d_si0, d_sni};
-      max_items = std::max(max_items, ni);
-      if (k == 1) item_slices_ = (int)((nslices_ + ni - 1) / ni);
+    std::vector<int64_t> u0(S), nu(S);
+    for (int sg = 0; sg < S; ++sg) {
+      u0[sg] = hb_.seg_sl0[sg];
+      nu[sg] = hb_.seg_nsl[sg];
     }
+    int max_items = 0;
+    ST(make_item_lists(u0, nu, g.list, &max_items));
+    item_slices_ = (int)((nslices_ + g.list[0].nitems - 1) / g.list[0].nitems);
     SG_ = g;
     nitems_ = max_items;
     ST(mem_.alloc(&red_.partial, (int64_t)max_items * kRedComp));
@@ -1546,7 +1641,10 @@ class Engine final : public EngineBase {
   bool pc_ = false;
   DCoarse CC_{};
   int64_t *inv_off3_ = nullptr, *inv_off1_ = nullptr;
-  T *cinv3_ = nullptr, *cinv1_ = nullptr, *dinv3_ = nullptr, *dinv1_ = nullptr;
+  typename CoarseStore<T>::type *cinv3_ = nullptr, *cinv1_ = nullptr;
+  int64_t *rc_off3_ = nullptr, *rc_off1_ = nullptr;
+  ItemList GL3_{}, GL1_{};  // coarse GEMV work items (3 and 1 components per aggregate)
+  T *dinv3_ = nullptr, *dinv1_ = nullptr;
   T *dgs_eps_ = nullptr, *dgs_aeps_ = nullptr;  // Jacobi of the GSPM solves (NULL: plain)
   T *rc_ = nullptr, *ec_ = nullptr;
   // CUDA-graph replay state
@@ -1601,7 +1699,7 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
   std::vector<HostSell> hs(nmesh);
   std::vector<HostOps> ops(nmesh);
   for (int k = 0; k < nmesh; ++k) {
-    const int st = host_mesh_build(meshes + k, opt->ordering, &c->hm[k]);
+    const int st = host_mesh_build(meshes + k, opt->ordering, opt->coarse_nodes, &c->hm[k]);
     if (st != GSPM_OK) {
       if (nmesh > 1) {
         std::string msg = g_err;
@@ -1620,8 +1718,7 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
   if (two_level) {
     coarse.resize(nmesh);
     for (int k = 0; k < nmesh; ++k) {
-      const int64_t npa = opt->coarse_nodes > 0 ? opt->coarse_nodes
-                                                : std::max<int64_t>(512, (c->hm[k].n + 2047) / 2048);
+      const int64_t npa = coarse_nodes_of(opt->coarse_nodes, c->hm[k].n);
       const int st = host_coarse_build(c->hm[k], hs[k], ops[k], npa, &coarse[k]);
       if (st != GSPM_OK) return st;
     }

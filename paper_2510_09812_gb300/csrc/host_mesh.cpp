@@ -174,7 +174,33 @@ double tet_geometry(const double* x0, const double* x1, const double* x2, const 
 
 }  // namespace
 
-int host_mesh_build(const gspm_mesh_desc* d, int ordering, HostMesh* hm) {
+int64_t coarse_nodes_of(int64_t option, int64_t n) {
+  return option > 0 ? option : std::max<int64_t>(512, (n + 2047) / 2048);
+}
+
+void coarse_bins(const HostMesh& hm, int64_t nodes_per_agg, int nb[3],
+                 std::vector<int64_t>* bin_of) {
+  const int64_t n = hm.n;
+  double L[3], vol = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    L[a] = hm.hi[a] - hm.lo[a];
+    vol *= L[a];
+  }
+  const double H = std::cbrt(vol * (double)std::max<int64_t>(1, nodes_per_agg) / (double)n);
+  for (int a = 0; a < 3; ++a) nb[a] = (int)std::max<int64_t>(1, std::llround(L[a] / H));
+  bin_of->resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t b[3];
+    for (int a = 0; a < 3; ++a) {
+      const double t = (hm.xw[3 * i + a] - hm.lo[a]) / L[a] * nb[a];
+      b[a] = std::min<int64_t>(nb[a] - 1, std::max<int64_t>(0, (int64_t)std::floor(t)));
+    }
+    (*bin_of)[i] = b[0] + nb[0] * (b[1] + (int64_t)nb[1] * b[2]);
+  }
+}
+
+int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
+                    HostMesh* hm) {
   if (!d || !d->coords || !d->tets || d->n_nodes <= 0 || d->n_tets <= 0) {
     set_error("mesh_load: null pointer or empty mesh");
     return GSPM_EINVAL;
@@ -358,6 +384,13 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, HostMesh* hm) {
     for (int64_t i = 0; i < n; ++i) hm->perm[i] = order[n - 1 - i];
   } else if (ordering == GSPM_ORDER_NONE) {
     std::iota(hm->perm.begin(), hm->perm.end(), 0);
+  } else if (ordering == GSPM_ORDER_AGGREGATE) {
+    int nb[3];
+    std::vector<int64_t> bin_of;
+    coarse_bins(*hm, coarse_nodes_of(coarse_nodes, n), nb, &bin_of);
+    std::iota(hm->perm.begin(), hm->perm.end(), 0);
+    std::stable_sort(hm->perm.begin(), hm->perm.end(),
+                     [&](int64_t a, int64_t b) { return bin_of[a] < bin_of[b]; });
   } else {
     set_error("mesh_load: unknown ordering %d", ordering);
     return GSPM_EINVAL;
@@ -672,24 +705,9 @@ static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* 
 int host_coarse_build(const HostMesh& hm, const HostSell& s, const HostOps& ops,
                       int64_t nodes_per_agg, HostCoarse* c) {
   const int64_t n = hm.n;
-  // bins of about nodes_per_agg nodes: edge H = (V nodes_per_agg / n)^(1/3)
-  double L[3], vol = 1.0;
-  for (int a = 0; a < 3; ++a) {
-    L[a] = hm.hi[a] - hm.lo[a];
-    vol *= L[a];
-  }
-  const double H = std::cbrt(vol * (double)std::max<int64_t>(1, nodes_per_agg) / (double)n);
-  for (int a = 0; a < 3; ++a) c->nb[a] = (int)std::max<int64_t>(1, std::llround(L[a] / H));
+  std::vector<int64_t> bin_of;
+  coarse_bins(hm, nodes_per_agg, c->nb, &bin_of);
   const int64_t nbins = (int64_t)c->nb[0] * c->nb[1] * c->nb[2];
-  std::vector<int64_t> bin_of(n);
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t b[3];
-    for (int a = 0; a < 3; ++a) {
-      const double t = (hm.xw[3 * i + a] - hm.lo[a]) / L[a] * c->nb[a];
-      b[a] = std::min<int64_t>(c->nb[a] - 1, std::max<int64_t>(0, (int64_t)std::floor(t)));
-    }
-    bin_of[i] = b[0] + c->nb[0] * (b[1] + (int64_t)c->nb[1] * b[2]);
-  }
   std::vector<int64_t> id(nbins, -1);
   for (int64_t i = 0; i < n; ++i) id[bin_of[i]] = 0;
   int64_t na = 0;

@@ -52,7 +52,17 @@ struct HostMesh {
   double volume = 0, volume_mag = 0;
   int64_t n_mag_nodes = 0, n_mag_tets = 0;
 };
-int host_mesh_build(const gspm_mesh_desc* d, int ordering, HostMesh* hm);
+// coarse_nodes: the option of that name (GSPM_ORDER_AGGREGATE groups the rows by the
+// aggregates of coarse_nodes_of(coarse_nodes, n) nodes)
+int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes, HostMesh* hm);
+
+// Aggregate size: the option when positive, else max(512, n / 2048)
+int64_t coarse_nodes_of(int64_t option, int64_t n);
+// Coordinate bins of about nodes_per_agg nodes: edge H = (V nodes_per_agg / n)^(1/3), nb[a] =
+// round(L_a / H) bins per axis; bin_of[i] (x fastest) for every unique node i, from its
+// wrapped coordinates.
+void coarse_bins(const HostMesh& hm, int64_t nodes_per_agg, int nb[3],
+                 std::vector<int64_t>* bin_of);
 
 // SELL-32 layout of the node graph in internal numbering.  Entry e of row i (k-th column of
 // the row, ascending) sits at sptr[i/32] + k*32 + i%32.  A matrix with B values per entry stores

@@ -818,9 +818,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_psub(DSell A, DSeg G, int epr, T*
 }
 
 // rc(I, a) = sum over the rows i of aggregate I of r(i, a): one block per aggregate, threads
-// stride over its rows, FP64 block tree (fixed order)
+// stride over its rows, FP64 block tree (fixed order).  With contiguous aggregates the rows
+// are read in order (no row list).
 template <typename T, int EPR>
 __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restrict__ r,
+                                                     const int64_t* __restrict__ rc_off,
                                                      T* __restrict__ rc) {
   __shared__ double sm[EPR][kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -830,13 +832,14 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
     for (int a = 0; a < EPR; ++a) acc[a] = T(0);
     // four rows per thread and round: their indices, then their values, then the sums (in T
     // within the round, one FP64 add per component)
-    const int q1 = C.agg_ptr[I + 1];
-    for (int q = C.agg_ptr[I] + threadIdx.x; q < q1; q += 4 * blockDim.x) {
+    const int q0 = C.agg_ptr[I], q1 = C.agg_ptr[I + 1];
+    const int64_t first = C.contig && q1 > q0 ? (int64_t)C.agg_rows[q0] - q0 : -1;
+    for (int q = q0 + threadIdx.x; q < q1; q += 4 * blockDim.x) {
       int64_t row[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int qq = q + u * blockDim.x;
-        row[u] = qq < q1 ? (int64_t)C.agg_rows[qq] : -1;
+        row[u] = qq < q1 ? (first >= 0 ? first + qq : (int64_t)C.agg_rows[qq]) : -1;
       }
       T v[4][EPR];
 #pragma unroll
@@ -858,64 +861,16 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
 #pragma unroll
       for (int a = 0; a < EPR; ++a) {
         const double v = warp_sum(lane < kBlock / 32 ? sm[a][lane] : 0.0);
-        if (lane == 0) rc[I * EPR + a] = (T)v;
+        if (lane == 0) {
+          const int sg = C.agg_seg[I];
+          rc[rc_off[sg] + (I - C.seg_agg0[sg]) * EPR + a] = (T)v;
+        }
       }
     }
     __syncthreads();
   }
 }
 
-// ec = A_c^-1 rc per segment block: one warp per coarse row, coalesced 16-byte loads over the
-// row (a segment's block has nc % 4 == 0 rows of nc values and starts 16-byte aligned when
-// `vec`), eight loads in flight per lane
-// (accumulated in T: it only applies the preconditioner, and FP64 instructions cost ~16x
-// FP32 ones per warp on this part)
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(kBlock) k_coarse_gemv(DCoarse C, int epr, const T* __restrict__ inv,
-                                                        const int64_t* __restrict__ inv_off,
-                                                        const T* __restrict__ rc,
-                                                        T* __restrict__ ec) {
-  constexpr int W = Pack16<T>::W;
-  const int lane = threadIdx.x & 31;
-  const int64_t ncoarse = C.nagg * epr;
-  for (int64_t g = gtid() >> 5; g < ncoarse; g += gstride() >> 5) {
-    const int seg = C.agg_seg[g / epr];
-    const int64_t c0 = (int64_t)C.seg_agg0[seg] * epr;
-    const int64_t nc = (int64_t)(C.seg_agg0[seg + 1] - C.seg_agg0[seg]) * epr;
-    const T* row = inv + inv_off[seg] + (g - c0) * nc;
-    const T* x = rc + c0;
-    T acc = T(0);
-    int64_t j0 = 0;
-    if (VEC && nc % W == 0) {
-      const int64_t np = nc / W;
-      for (int64_t t = lane; t < np; t += 8 * 32) {
-        T a[8][W];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int64_t tt = t + u * 32;
-          if (tt < np) {
-            ld16(row + tt * W, a[u]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < W; ++c) a[u][c] = T(0);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int64_t tt = t + u * 32;
-          if (tt < np)
-#pragma unroll
-            for (int c = 0; c < W; ++c) acc += a[u][c] * x[tt * W + c];
-        }
-      }
-      j0 = nc;
-    }
-    for (int64_t j = j0 + lane; j < nc; j += 32) acc += row[j] * x[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
-    if (lane == 0) ec[g] = acc;
-  }
-}
 
 // N contiguous values through 16-byte packs (N * sizeof(T) a multiple of 16, p aligned)
 template <typename T, int N>
@@ -933,6 +888,89 @@ __device__ __forceinline__ void stn(T* p, const T (&v)[N]) {
   for (int k = 0; k < N / W; ++k)
     *reinterpret_cast<typename Pack16<T>::V*>(p + k * W) =
         *reinterpret_cast<const typename Pack16<T>::V*>(v + k * W);
+}
+
+// ec = A_c^-1 rc per segment.  Work items are runs of kBlock / 32 coarse rows of one segment
+// (one warp per row, no barrier); each warp streams its stored row in 16-byte packs (eight
+// bfloat16 or two doubles), D packs deep per lane, against the segment's rc block (zero-padded
+// to the row stride, read in packs too).  Accumulated in T: it only applies the preconditioner,
+// and FP64 instructions cost ~16x FP32 ones per warp on this part.
+template <typename S>
+struct CoarsePack;
+template <>
+struct CoarsePack<uint16_t> {
+  static constexpr int W = 8;
+  using Raw = uint4;
+  __device__ __forceinline__ static Raw load(const uint16_t* p) {
+    return __ldcs(reinterpret_cast<const uint4*>(p));
+  }
+  __device__ __forceinline__ static Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+  __device__ __forceinline__ static void cvt(const Raw& u, float (&v)[8]) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = __uint_as_float(w[k] << 16);  // bfloat16 -> float is exact
+      v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+template <>
+struct CoarsePack<double> {
+  static constexpr int W = 2;
+  using Raw = double2;
+  __device__ __forceinline__ static Raw load(const double* p) {
+    return __ldcs(reinterpret_cast<const double2*>(p));
+  }
+  __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
+  __device__ __forceinline__ static void cvt(const Raw& u, double (&v)[2]) {
+    v[0] = u.x;
+    v[1] = u.y;
+  }
+};
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kBlock) k_coarse_gemv(ItemList IL, DCoarse C, int epr,
+                                                        const S* __restrict__ inv,
+                                                        const int64_t* __restrict__ inv_off,
+                                                        const int64_t* __restrict__ rc_off,
+                                                        const T* __restrict__ rc,
+                                                        T* __restrict__ ec) {
+  constexpr int W = CoarsePack<S>::W;
+  constexpr int D = 12;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
+    const int64_t c0 = (int64_t)C.seg_agg0[seg] * epr;
+    const int64_t nc = (int64_t)(C.seg_agg0[seg + 1] - C.seg_agg0[seg]) * epr;
+    const int64_t np = (nc + W - 1) / W;  // packs per padded row
+    const T* x = rc + rc_off[seg];
+    for (int64_t g = (int64_t)IL.sl0[item] + warp; g < IL.sl1[item]; g += nw) {
+      const S* row = inv + inv_off[seg] + (g - c0) * (np * W);
+      T acc = T(0);
+      for (int64_t t = lane; t < np; t += D * 32) {
+        typename CoarsePack<S>::Raw a[D];
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          const int64_t tt = t + u * 32;
+          a[u] = tt < np ? CoarsePack<S>::load(row + tt * W) : CoarsePack<S>::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          const int64_t tt = t + u * 32;
+          if (tt < np) {
+            T w[W], xv[W];
+            CoarsePack<S>::cvt(a[u], w);
+            ldn<T, W>(x + tt * W, xv);
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc += w[c] * xv[c];
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+      if (lane == 0) ec[g] = acc;
+    }
+  }
 }
 
 // z = D^-1 r + P ec, r.z; init: z is the first search direction p.  Four rows per thread and
@@ -1019,6 +1057,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
     }
   }
 }
+
 
 __global__ void k_loop_start(LoopCtl lc) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1740,14 +1779,15 @@ cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, i
 }
 
 template <typename T>
-cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, T* rc) {
+cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r,
+                            const int64_t* rc_off, T* rc) {
   (*L.counter) += 1;
   if (epr == 3) {
     auto k = k_restrict<T, 3>;
-    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc);
+    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc_off, rc);
   } else if (epr == 1) {
     auto k = k_restrict<T, 1>;
-    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc);
+    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc_off, rc);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1755,18 +1795,15 @@ cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T*
 }
 
 template <typename T>
-cudaError_t launch_coarse_gemv(const Launch& L, const DCoarse& C, int epr, const T* inv,
-                               const int64_t* inv_off, const T* rc, T* ec) {
+cudaError_t launch_coarse_gemv(const Launch& L, const ItemList& GL, const DCoarse& C, int epr,
+                               const typename CoarseStore<T>::type* inv, const int64_t* inv_off,
+                               const int64_t* rc_off, const T* rc, T* ec) {
   (*L.counter) += 1;
-  // each segment's block starts at a multiple of 4 values (inv_off), so with an aligned base
-  // every row of a block with nc % W == 0 is 16-byte aligned; other blocks use scalar loads
-  if (aligned16(inv)) {
-    auto k = k_coarse_gemv<T, true>;
-    k<<<GSPM_GRID(L, C.nagg * epr * 32, k), kBlock, 0, L.stream>>>(C, epr, inv, inv_off, rc, ec);
-  } else {
-    auto k = k_coarse_gemv<T, false>;
-    k<<<GSPM_GRID(L, C.nagg * epr * 32, k), kBlock, 0, L.stream>>>(C, epr, inv, inv_off, rc, ec);
-  }
+  // rows are padded to whole 16-byte packs and blocks start at pack boundaries (inv_off)
+  if (!aligned16(inv) || !aligned16(rc)) return cudaErrorInvalidValue;
+  auto k = k_coarse_gemv<T, typename CoarseStore<T>::type>;
+  k<<<GSPM_GRID(L, (int64_t)GL.nitems * kBlock, k), kBlock, 0, L.stream>>>(GL, C, epr, inv,
+                                                                          inv_off, rc_off, rc, ec);
   return cudaGetLastError();
 }
 
@@ -1978,8 +2015,10 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
   template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
                                          const T*, T*, T*, T*, CGState*, int*, double, int, Red,  \
                                          const double*, int, int);                                \
-  template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*, T*);      \
-  template cudaError_t launch_coarse_gemv<T>(const Launch&, const DCoarse&, int, const T*,        \
+  template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*,           \
+                                          const int64_t*, T*);                                    \
+  template cudaError_t launch_coarse_gemv<T>(const Launch&, const ItemList&, const DCoarse&, int,  \
+                                             const typename CoarseStore<T>::type*, const int64_t*, \
                                              const int64_t*, const T*, T*);                       \
   template cudaError_t launch_pcg_z<T>(const Launch&, const DSeg&, const DCoarse&, int, const T*, \
                                        const T*, const T*, T*, CGState*, int, Red);              \

@@ -76,6 +76,7 @@ struct DCoarse {
   const int32_t* agg_rows;    // [rows in aggregates]
   const int32_t* agg_seg;     // [nagg]
   const int32_t* seg_agg0;    // [nseg + 1]
+  int contig;                 // every aggregate's rows are consecutive (GSPM_ORDER_AGGREGATE)
 };
 
 // Material constants needed on the device (reduced units of App. B).  The applied field
@@ -119,7 +120,7 @@ struct Launch {
 int grid_for(const Launch& L, int64_t threads, const void* kernel);
 
 // SpMV schedules chosen by the autotuner: 0 = one thread per row, 1 = one thread per row with
-// five neighbours' loads issued ahead of their FMAs, 2 = two threads per row (alternate
+// the next neighbours' loads issued ahead of their FMAs, 2 = two threads per row (alternate
 // neighbours, combined with a shuffle), 3 = schedule 1 compiled for three resident blocks per
 // SM (fewer registers, more warps in flight).
 constexpr int kSpmvVariants = 4;
@@ -179,11 +180,29 @@ cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, i
 // Two-level preconditioner z = D^-1 r + P A_c^-1 P^T r (one right-hand side, epr components):
 // rc = P^T r (per aggregate sums), ec = A_c^-1 rc (per segment dense block), then z and r.z;
 // the segment's last item stores rz (init) or beta = r.z / rz_old and rz.
+// rc layout: segment s's block starts at rc_off[s] and is zero-padded to coarse_ld(nc) values
+// (the coarse GEMV reads it in whole packs); ec is indexed by the global coarse index.
+// GL: work items of the coarse GEMV, runs of kBlock / 32 coarse rows of one segment (sl0 = first
+// row, sl1 = end).
 template <typename T>
-cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r, T* rc);
+cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r,
+                            const int64_t* rc_off, T* rc);
+// Storage of the dense coarse inverse: bfloat16 bits (uint16_t) under FP32 arithmetic, the
+// arithmetic type otherwise.  The inverse only applies the preconditioner: any fixed symmetric
+// positive definite rounding of it leaves the CG's solution unchanged.  Each row of a
+// segment's block of side nc is padded with zeros to a stride coarse_ld(nc) that keeps every
+// row 16-byte aligned; blocks start at multiples of that alignment (inv_off).
+template <typename T> struct CoarseStore { using type = T; };
+template <> struct CoarseStore<float> { using type = uint16_t; };
 template <typename T>
-cudaError_t launch_coarse_gemv(const Launch& L, const DCoarse& C, int epr, const T* inv,
-                               const int64_t* inv_off, const T* rc, T* ec);
+inline int64_t coarse_ld(int64_t nc) {
+  constexpr int64_t w = 16 / sizeof(typename CoarseStore<T>::type);
+  return (nc + w - 1) / w * w;
+}
+template <typename T>
+cudaError_t launch_coarse_gemv(const Launch& L, const ItemList& GL, const DCoarse& C, int epr,
+                               const typename CoarseStore<T>::type* inv, const int64_t* inv_off,
+                               const int64_t* rc_off, const T* rc, T* ec);
 template <typename T>
 cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
                          const T* dinv, const T* ec, T* z, CGState* st, int init, Red red);

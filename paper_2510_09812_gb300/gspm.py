@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgspm.so
 OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ESTATE, ENUMERIC = range(9)
 HOST, DEVICE = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
-ORDER_NONE, ORDER_RCM = 0, 1
+ORDER_NONE, ORDER_RCM, ORDER_AGGREGATE = 0, 1, 2
 FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE, FLAG_GRAPH, FLAG_PINNED_CG = 1, 2, 4, 8, 16
 FLAG_RESOLVE_AT_MSTAR, FLAG_PLAIN_CG = 32, 64
 EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC, \
@@ -184,11 +184,15 @@ class Context:
     """One mesh + material + time step on the current CUDA device (``gspm_mesh_load``)."""
 
     def __init__(self, mesh, material: dict, dt: float, alpha: float, precision: str = "f64",
-                 ordering: str = "none", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
+                 ordering: str = "auto", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
                  max_iter=20000, row2_printed=False, host_only=False, stream=0, wrap_tol=0.0,
                  autotune=True, graph=False, pinned_cg=False, resolve_at_mstar=False,
                  plain_cg=False, coarse_nodes=0):
-        """One mesh, or a batch when `mesh` is a list (gspm_batch_load)."""
+        """One mesh, or a batch when `mesh` is a list (gspm_batch_load).  ordering "auto":
+        "aggregate" when the two-level preconditioner is on (neither plain_cg nor pinned_cg),
+        which lets its restriction run fused with the CG update, else "none"."""
+        if ordering == "auto":
+            ordering = "none" if (plain_cg or pinned_cg) else "aggregate"
         meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
         descs = (MeshDesc * len(meshes))()
@@ -207,7 +211,7 @@ class Context:
             d.wrap_tol = float(wrap_tol)
         o = Options()
         o.precision = {"f64": PREC_F64, "mixed": PREC_MIXED}[precision]
-        o.ordering = {"none": ORDER_NONE, "rcm": ORDER_RCM}[ordering]
+        o.ordering = {"none": ORDER_NONE, "rcm": ORDER_RCM, "aggregate": ORDER_AGGREGATE}[ordering]
         o.dt, o.alpha = float(dt), float(alpha)
         o.rtol_gs, o.rtol_ms, o.rtol_mech = float(rtol_gs), float(rtol_ms), float(rtol_mech)
         o.max_iter = int(max_iter)

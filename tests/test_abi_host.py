@@ -39,13 +39,28 @@ MESHES = [
 ]
 
 
+def _aggregate_order(mesh, wm, npa):
+    """Nodes sorted by coordinate bin of about npa nodes (x-fastest bin index, ties by index),
+    bins from the wrapped coordinates of each node's first stored copy."""
+    first = np.full(wm.n, -1)
+    first[wm.unique_of_stored[::-1]] = np.arange(wm.unique_of_stored.size)[::-1]
+    xw = mesh.coords[first]
+    lo, hi = np.asarray(mesh.box_lo, float), np.asarray(mesh.box_hi, float)
+    L = hi - lo
+    H = np.cbrt(np.prod(L) * npa / wm.n)
+    nb = np.maximum(1, np.floor(L / H + 0.5)).astype(np.int64)
+    t = np.clip(np.floor((xw - lo) / L * nb).astype(np.int64), 0, nb - 1)
+    b = t[:, 0] + nb[0] * (t[:, 1] + nb[1] * t[:, 2])
+    return np.argsort(b, kind="stable")
+
+
 @pytest.mark.parametrize("spec", MESHES)
-@pytest.mark.parametrize("ordering", ["none", "rcm"])
+@pytest.mark.parametrize("ordering", ["none", "rcm", "aggregate"])
 def test_host_mesh_matches_oracle_bit_exactly(gspm_lib, spec, ordering):
     mesh = synth.kuhn_box(spec["cells"], spec["box"], jitter=spec["jitter"], seed=spec["seed"],
                           defects=spec["defects"])
     ctx = gspm_lib.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, ordering=ordering,
-                           host_only=True)
+                           host_only=True, coarse_nodes=24)
     wm = WrappedMesh.from_synth(mesh)
     assert np.array_equal(ctx.export(gspm_lib.EXPORT_UNIQUE_OF_STORED), wm.unique_of_stored)
     rowptr, cols = csr_pattern(wm.tets, wm.n)
@@ -54,7 +69,8 @@ def test_host_mesh_matches_oracle_bit_exactly(gspm_lib, spec, ordering):
     assert np.array_equal(ctx.export(gspm_lib.EXPORT_NODE_MAGNETIC).astype(bool),
                           wm.node_magnetic)
     perm = ctx.export(gspm_lib.EXPORT_PERM)
-    expect = rcm_order(wm.tets, wm.n) if ordering == "rcm" else np.arange(wm.n)
+    expect = {"rcm": lambda: rcm_order(wm.tets, wm.n), "none": lambda: np.arange(wm.n),
+              "aggregate": lambda: _aggregate_order(mesh, wm, 24)}[ordering]()
     assert np.array_equal(perm, expect)
     ML = ctx.export(gspm_lib.EXPORT_LUMPED_MASS)
     from oracle import fem

@@ -54,11 +54,12 @@ def _ctx(gspm_lib, mesh, prec="f64", ordering="none", rtol=1e-13, **kw):
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("mixed", 2e-6)])
-@pytest.mark.parametrize("ordering", ["none", "rcm"])
+@pytest.mark.parametrize("ordering", ["none", "rcm", "aggregate"])
 def test_operators_match_oracle(gspm_lib, ragged, prec, tol, ordering):
     mesh, wm, s = ragged
     g = gspm_lib
-    ctx = _ctx(g, mesh, prec, ordering)
+    # aggregate ordering with several aggregates (the default size would give one here)
+    ctx = _ctx(g, mesh, prec, ordering, **({"coarse_nodes": 64} if ordering == "aggregate" else {}))
     rng = np.random.default_rng(7)
     n = wm.n
     x1 = rng.standard_normal(n)
@@ -116,7 +117,8 @@ def _voigt(E):
     return np.stack([E[:, 0, 0], E[:, 1, 1], E[:, 2, 2], E[:, 1, 2], E[:, 0, 2], E[:, 0, 1]], 1)
 
 
-@pytest.mark.parametrize("ordering,pinned", [("none", True), ("none", False), ("rcm", False)])
+@pytest.mark.parametrize("ordering,pinned", [("none", True), ("none", False), ("rcm", False),
+                                            ("aggregate", False)])
 def test_first_step_fields_match_oracle(gspm_lib, ragged, ordering, pinned):
     mesh, wm, s0 = ragged
     s = System(wm, synth.fe_like_material(), 1e-12, 0.5, rtol_gs=1e-13, rtol_ms=1e-13,
@@ -125,7 +127,8 @@ def test_first_step_fields_match_oracle(gspm_lib, ragged, ordering, pinned):
     m0[~s.mag] = 0.0
     H = np.array([3e4, -1e4, 5e3])
     m1, U, u, info = s.step(m0, np.zeros(wm.n), np.zeros((wm.n, 3)), H)
-    ctx = _ctx(gspm_lib, mesh, "f64", ordering, pinned_cg=pinned)
+    ctx = _ctx(gspm_lib, mesh, "f64", ordering, pinned_cg=pinned,
+               **({"coarse_nodes": 64} if ordering == "aggregate" else {}))
     ctx.set_field(gspm_lib.FIELD_M, m0)
     st = ctx.step(1, H)
     if pinned:

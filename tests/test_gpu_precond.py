@@ -62,7 +62,9 @@ def test_coarse_operators_are_galerkin_products(gspm_lib, medium):
         assert np.abs(got3 @ one).max() < 1e-12 * np.abs(got3).max()
 
 
-def test_preconditioned_elastic_solve_matches_oracle(gspm_lib, medium):
+@pytest.mark.parametrize("ordering", ["aggregate", "none"])
+def test_preconditioned_elastic_solve_matches_oracle(gspm_lib, medium, ordering):
+    """Aggregate ordering: contiguous aggregates (restriction in row order); none: row lists."""
     mesh, wm = medium
     s = System(wm, synth.fe_like_material(), 1e-12, 0.5, rtol_mech=1e-13)
     m = synth.random_unit_m(wm.n, 62)
@@ -70,7 +72,7 @@ def test_preconditioned_elastic_solve_matches_oracle(gspm_lib, medium):
     ref = s.solve_elastic(m, np.zeros((wm.n, 3)))
     its = {}
     for plain in (True, False):
-        ctx = _ctx(gspm_lib, mesh, plain_cg=plain)
+        ctx = _ctx(gspm_lib, mesh, plain_cg=plain, ordering=ordering)
         u, it, rel, code = ctx.solve_elastic(m, x0_mode=0, rtol=1e-13)
         assert code == gspm_lib.OK and rel < 1e-13
         assert np.all(u[0] == 0.0)
