@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "kernels.cuh"
@@ -197,6 +198,67 @@ __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restri
   }
 }
 
+// Compensated dot product in FP32 (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM
+// J. Sci. Comput. 26 (2005), Algorithm Dot2): each product is split exactly into p + e with an
+// FMA, the running sum kept exactly as s plus the accumulated errors c by Knuth's TwoSum, so
+// s + c is as accurate as the dot product computed in twice the working precision.  The CG
+// initial residuals b - A x (which cancel heavily with a warm start) use it instead of FP64
+// arithmetic, whose rate on this part is 1/64 of FP32's.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  // the _rn intrinsics keep the compiler from contracting or reassociating these steps
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    c = __fadd_rn(c, __fadd_rn(d, e));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// sell_scalar_row / sell_block_row with Dot2 accumulators (FP32 operands)
+template <int NR>
+__device__ __forceinline__ void sell_scalar_row_dot2(const DSell& A, const float* __restrict__ val,
+                                                     int64_t s, int lane,
+                                                     const float* __restrict__ x, int64_t ld,
+                                                     Dot2 (&acc)[NR]) {
+  const int64_t base = A.sptr[s];
+  const int len = A.slen[s];
+  const int32_t* cp = A.col + base + lane;
+  const float* vp = val + base + lane;
+#pragma unroll 4
+  for (int k = 0; k < len; ++k) {
+    const int j = __ldcs(cp + (int64_t)k * 32);
+    const float a = __ldcs(vp + (int64_t)k * 32);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r].add(a, __ldg(x + r * ld + j));
+  }
+}
+__device__ __forceinline__ void sell_block_row_dot2(const DSell& A, const float* __restrict__ val,
+                                                    int64_t s, int lane,
+                                                    const float* __restrict__ x,
+                                                    Dot2 (&acc)[3]) {
+  const int64_t base = A.sptr[s];
+  const int len = A.slen[s];
+  const int32_t* cp = A.col + base + lane;
+  const float* vp = val + base * 9 + lane;
+#pragma unroll 2
+  for (int k = 0; k < len; ++k) {
+    const int64_t j = __ldcs(cp + (int64_t)k * 32);
+    const float* bp = vp + (int64_t)k * 288;
+    const float x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[a].add(__ldcs(bp + (3 * a + 0) * 32), x0);
+      acc[a].add(__ldcs(bp + (3 * a + 1) * 32), x1);
+      acc[a].add(__ldcs(bp + (3 * a + 2) * 32), x2);
+    }
+  }
+}
+
 // Work unit of the SELL kernels for schedule VAR: one slice per warp (VAR 0, 1), or half a slice
 // per warp with two lanes per row (VAR 2).  unit_row() gives, for this lane, the slice, the SELL
 // lane of its row, and the first neighbour and stride it handles.
@@ -369,12 +431,18 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
     for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
       const int64_t row = s * 32 + lane;
       const bool ok = row_valid(G, seg, row);
-      // A x summed in FP64: with a good initial guess b - A x cancels heavily, and this runs
-      // once per solve
+      // A x to twice the working precision (FP64, or compensated FP32): with a good initial
+      // guess b - A x cancels heavily
       if (B == 1) {
         double acc[1];
-        const int skip[1] = {0};
-        sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, acc);
+        if constexpr (std::is_same<T, float>::value) {
+          Dot2 d[1];
+          sell_scalar_row_dot2<1>(A, val, s, lane, x, 0, d);
+          acc[0] = d[0].value();
+        } else {
+          const int skip[1] = {0};
+          sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, acc);
+        }
         if (ok) {
           const double bv = (double)b[row] - bm[0];
           const T rv = row == pin ? T(0) : (T)(bv - acc[0]);
@@ -386,7 +454,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
         }
       } else {
         double acc[3];
-        sell_block_row<T, T, double, 0>(A, val, s, lane, x, acc);
+        if constexpr (std::is_same<T, float>::value) {
+          Dot2 d[3];
+          sell_block_row_dot2(A, val, s, lane, x, d);
+          for (int a = 0; a < 3; ++a) acc[a] = d[a].value();
+        } else {
+          sell_block_row<T, T, double, 0>(A, val, s, lane, x, acc);
+        }
         if (ok) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
@@ -440,10 +514,22 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G, ItemList
 #pragma unroll
     for (int k = 0; k < 3 * NR; ++k) v[k] = 0.0;
     for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
-      // M x and A x in FP64: their difference (-c eps K x) is small against either
+      // M x and A x to twice the working precision (FP64, or compensated FP32): their
+      // difference (-c eps K x) is small against either
       double ax[NR], mx[NR];
-      sell_scalar_row<T, T, double, NR>(A, aval, s, lane, x, ld, skip, ax);
-      sell_scalar_row<T, T, double, NR>(A, mval, s, lane, x, ld, skip, mx);
+      if constexpr (std::is_same<T, float>::value) {
+        Dot2 da[NR], dm[NR];
+        sell_scalar_row_dot2<NR>(A, aval, s, lane, x, ld, da);
+        sell_scalar_row_dot2<NR>(A, mval, s, lane, x, ld, dm);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          ax[k] = da[k].value();
+          mx[k] = dm[k].value();
+        }
+      } else {
+        sell_scalar_row<T, T, double, NR>(A, aval, s, lane, x, ld, skip, ax);
+        sell_scalar_row<T, T, double, NR>(A, mval, s, lane, x, ld, skip, mx);
+      }
       const int64_t row = s * 32 + lane;
       if (row_valid(G, seg, row)) {
         const T d = dinv ? dinv[row] : T(1);
@@ -818,20 +904,20 @@ __global__ void __launch_bounds__(kBlock) k_cg_psub(DSell A, DSeg G, int epr, T*
 }
 
 // rc(I, a) = sum over the rows i of aggregate I of r(i, a): one block per aggregate, threads
-// stride over its rows, FP64 block tree (fixed order).  With contiguous aggregates the rows
-// are read in order (no row list).
+// stride over its rows, block tree in a fixed order, all in T (rc only applies the
+// preconditioner; FP64 adds cost ~16x FP32 ones on this part and dominated this kernel).
+// With contiguous aggregates the rows are read in order (no row list).
 template <typename T, int EPR>
 __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restrict__ r,
                                                      const int64_t* __restrict__ rc_off,
                                                      T* __restrict__ rc) {
-  __shared__ double sm[EPR][kBlock / 32];
+  __shared__ T sm[EPR][kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t I = blockIdx.x; I < C.nagg; I += gridDim.x) {
-    T acc[EPR];  // per thread and per warp in T, across warps in FP64
+    T acc[EPR];
 #pragma unroll
     for (int a = 0; a < EPR; ++a) acc[a] = T(0);
-    // four rows per thread and round: their indices, then their values, then the sums (in T
-    // within the round, one FP64 add per component)
+    // four rows per thread and round: their indices, then their values, then the sums
     const int q0 = C.agg_ptr[I], q1 = C.agg_ptr[I + 1];
     const int64_t first = C.contig && q1 > q0 ? (int64_t)C.agg_rows[q0] - q0 : -1;
     for (int q = q0 + threadIdx.x; q < q1; q += 4 * blockDim.x) {
@@ -854,13 +940,15 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
       T v = acc[a];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-      if (lane == 0) sm[a][warp] = (double)v;
+      if (lane == 0) sm[a][warp] = v;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
       for (int a = 0; a < EPR; ++a) {
-        const double v = warp_sum(lane < kBlock / 32 ? sm[a][lane] : 0.0);
+        T v = lane < kBlock / 32 ? sm[a][lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
         if (lane == 0) {
           const int sg = C.agg_seg[I];
           rc[rc_off[sg] + (I - C.seg_agg0[sg]) * EPR + a] = (T)v;
@@ -997,6 +1085,11 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
     const int64_t rhi = (int64_t)IL.sl1[item] * 32;
     const int64_t r1 = rhi < rend ? rhi : rend;
     const int64_t ng = (r1 - r0) / 4;
+    // per thread in T (r.z Kahan-compensated, the sums of z plain: they only give the mean that
+    // the projection removes), FP64 across threads
+    T rzs = T(0), rzc = T(0), zs[EPR];
+#pragma unroll
+    for (int a = 0; a < EPR; ++a) zs[a] = T(0);
     for (int64_t g = threadIdx.x; g < ng; g += blockDim.x) {
       const int64_t row = r0 + 4 * g;
       T rv[N], dv[N], zv[N];
@@ -1004,9 +1097,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
       ldn<T, N>(dinv + row * EPR, dv);
       const int4 ag = *reinterpret_cast<const int4*>(C.agg_of_row + row);
       const int agv[4] = {ag.x, ag.y, ag.z, ag.w};
-      T rz = T(0), zs[EPR];
-#pragma unroll
-      for (int a = 0; a < EPR; ++a) zs[a] = T(0);
+      T rz = T(0);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -1017,11 +1108,12 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
           zs[a] += zv[e];
         }
       stn<T, N>(z + row * EPR, zv);
-      v[0] += (double)rz;
-      if (proj) {
+      kahan_add(rzs, rzc, rz);
+    }
+    v[0] += (double)rzs - (double)rzc;
+    if (proj) {
 #pragma unroll
-        for (int a = 0; a < EPR; ++a) v[1 + a] += (double)zs[a];
-      }
+      for (int a = 0; a < EPR; ++a) v[1 + a] += (double)zs[a];
     }
     for (int64_t row = r0 + 4 * ng + threadIdx.x; row < r1; row += blockDim.x) {
       const int64_t I = C.agg_of_row[row];
