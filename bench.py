@@ -278,14 +278,15 @@ def run_batch(gspm, torch, args, barrier):
 
 def run_small(gspm, torch, barrier, steps=200):
     """The 1024-node Fe box (16x16x4 cubes): kernels of a few microseconds, so the host's
-    launches and synchronisations dominate; direct launches against graph replay, same state."""
+    launches and synchronisations dominate; direct launches against graph replay, same state
+    (fixed SpMV schedule, so both contexts round alike and take the same iterations)."""
     from paper_2510_09812_gb300 import synth
     cfg = synth.fe_box_17x17x5()
     out = {"workload": cfg["name"], "steps": steps}
     for graph in (False, True):
         ctx = gspm.Context(cfg["mesh"], cfg["material"], cfg["dt"], cfg["alpha"],
                            precision="mixed", rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
-                           graph=graph)
+                           graph=graph, autotune=False)
         ctx.set_field(gspm.FIELD_M, cfg["m0"])
         ctx.step(3, cfg["H"], stats=False)
         barrier()

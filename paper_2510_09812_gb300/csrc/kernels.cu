@@ -44,28 +44,15 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
-// Block reduction of NC values into partial[item]; the last item of `seg` to arrive sums the
+// The last item of `seg` to arrive (its block partials already in red.partial[item]) sums the
 // segment's item partials in item order and returns true (totals in res[0..NC), valid in every
 // thread of that block).
 template <int NC>
-__device__ __forceinline__ bool seg_reduce(double (&v)[NC], int item, int seg, const DSeg& G,
-                                           const ItemList& IL, const Red& red, double* res) {
+__device__ __forceinline__ bool seg_arrive(int item, int seg, const DSeg& G, const ItemList& IL,
+                                           const Red& red, double* res) {
   __shared__ double sm[NC][32];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const double x = warp_sum(v[c]);
-    if (lane == 0) sm[c][warp] = x;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const double x = warp_sum(lane < nw ? sm[c][lane] : 0.0);
-      if (lane == 0) red.partial[(int64_t)item * kRedComp + c] = x;
-    }
-  }
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(G.counter + seg, 1u);
@@ -94,6 +81,86 @@ __device__ __forceinline__ bool seg_reduce(double (&v)[NC], int item, int seg, c
   if (threadIdx.x == 0) G.counter[seg] = 0u;
   __syncthreads();
   return true;
+}
+
+// Block reduction of NC values into partial[item] (FP64 tree), then seg_arrive.
+template <int NC>
+__device__ __forceinline__ bool seg_reduce(double (&v)[NC], int item, int seg, const DSeg& G,
+                                           const ItemList& IL, const Red& red, double* res) {
+  __shared__ double sm[NC][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const double x = warp_sum(v[c]);
+    if (lane == 0) sm[c][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double x = warp_sum(lane < nw ? sm[c][lane] : 0.0);
+      if (lane == 0) red.partial[(int64_t)item * kRedComp + c] = x;
+    }
+  }
+  return seg_arrive<NC>(item, seg, G, IL, red, res);
+}
+
+// Double-float addition (h, l) += (bh, bl): Knuth's TwoSum of the high parts, the low parts
+// added to its error term, renormalised (the _rn intrinsics keep the compiler from contracting
+// or reassociating the steps)
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  const float s = __fadd_rn(h, bh);
+  const float z = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(bh, z));
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// seg_reduce of per-thread values given as unevaluated sums hi + lo in T.  T = float: the warp
+// and block trees run in double-float arithmetic (FP32 operations, about 44 significant bits;
+// an FP64 instruction costs ~64 FP32 ones on this part and the FP64 trees dominated the short
+// CG vector kernels), one FP64 conversion per block and value.  T = double: seg_reduce.
+template <typename T, int NC>
+__device__ __forceinline__ bool seg_reduce_hl(const T (&hi)[NC], const T (&lo)[NC], int item,
+                                              int seg, const DSeg& G, const ItemList& IL,
+                                              const Red& red, double* res) {
+  if constexpr (std::is_same<T, double>::value) {
+    double v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = hi[c] + lo[c];
+    return seg_reduce<NC>(v, item, seg, G, IL, red, res);
+  } else {
+    __shared__ float smh[NC][32], sml[NC][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float h = hi[c], l = lo[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(kFull, h, o), bl = __shfl_down_sync(kFull, l, o);
+        df_add(h, l, bh, bl);
+      }
+      if (lane == 0) {
+        smh[c][warp] = h;
+        sml[c][warp] = l;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float h = lane < nw ? smh[c][lane] : 0.f, l = lane < nw ? sml[c][lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float bh = __shfl_down_sync(kFull, h, o), bl = __shfl_down_sync(kFull, l, o);
+          df_add(h, l, bh, bl);
+        }
+        if (lane == 0) red.partial[(int64_t)item * kRedComp + c] = (double)h + (double)l;
+      }
+    }
+    return seg_arrive<NC>(item, seg, G, IL, red, res);
+  }
 }
 
 __device__ __forceinline__ bool row_valid(const DSeg& G, int seg, int64_t row) {
@@ -616,11 +683,11 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
         }
       }
     }
-    double v[NR];
+    T lo[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) v[k] = (double)tv[k] - (double)tc[k];
+    for (int k = 0; k < NR; ++k) lo[k] = -tc[k];
     __shared__ double res[NR];
-    if (seg_reduce<NR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+    if (seg_reduce_hl<T, NR>(tv, lo, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       for (int k = 0; k < NR; ++k) {
         CGRhs& c = sg->r[k];
         if (c.done) continue;
@@ -748,11 +815,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
           }
         }
     }
-    double v[2 * NR + 3];
+    T lo[2 * NR + 3];
 #pragma unroll
-    for (int k = 0; k < 2 * NR + 3; ++k) v[k] = (double)tv[k];
+    for (int k = 0; k < 2 * NR + 3; ++k) lo[k] = T(0);
     __shared__ double res[2 * NR + 3];
-    if (seg_reduce<2 * NR + 3>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+    if (seg_reduce_hl<T, 2 * NR + 3>(tv, lo, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       int any = 0;
       for (int k = 0; k < NR; ++k) {
         CGRhs& c = sg->r[k];
@@ -1077,16 +1144,13 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
     CGState* sg = st + seg;
     if (!sg->active) continue;
     const bool proj = sg->proj;
-    double v[1 + EPR];  // r.z, per-component sums of z (projected form)
-#pragma unroll
-    for (int a = 0; a < 1 + EPR; ++a) v[a] = 0.0;
     const int64_t r0 = (int64_t)IL.sl0[item] * 32;
     const int64_t rend = G.seg_row0[seg] + G.seg_nrow[seg];
     const int64_t rhi = (int64_t)IL.sl1[item] * 32;
     const int64_t r1 = rhi < rend ? rhi : rend;
     const int64_t ng = (r1 - r0) / 4;
     // per thread in T (r.z Kahan-compensated, the sums of z plain: they only give the mean that
-    // the projection removes), FP64 across threads
+    // the projection removes), across threads in double-float
     T rzs = T(0), rzc = T(0), zs[EPR];
 #pragma unroll
     for (int a = 0; a < EPR; ++a) zs[a] = T(0);
@@ -1110,11 +1174,6 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
       stn<T, N>(z + row * EPR, zv);
       kahan_add(rzs, rzc, rz);
     }
-    v[0] += (double)rzs - (double)rzc;
-    if (proj) {
-#pragma unroll
-      for (int a = 0; a < EPR; ++a) v[1 + a] += (double)zs[a];
-    }
     for (int64_t row = r0 + 4 * ng + threadIdx.x; row < r1; row += blockDim.x) {
       const int64_t I = C.agg_of_row[row];
 #pragma unroll
@@ -1123,12 +1182,20 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
         const T rv = r[e];
         const T zv = dinv[e] * rv + ec[I * EPR + a];
         z[e] = zv;
-        v[0] += (double)rv * (double)zv;
-        v[1 + a] += (double)zv;
+        kahan_add(rzs, rzc, rv * zv);
+        zs[a] += zv;
       }
     }
+    T hi[1 + EPR], lo[1 + EPR];
+    hi[0] = rzs;
+    lo[0] = -rzc;
+#pragma unroll
+    for (int a = 0; a < EPR; ++a) {
+      hi[1 + a] = proj ? zs[a] : T(0);
+      lo[1 + a] = T(0);
+    }
     __shared__ double res[1 + EPR];
-    if (seg_reduce<1 + EPR>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+    if (seg_reduce_hl<T, 1 + EPR>(hi, lo, item, seg, G, IL, red, res) && threadIdx.x == 0) {
       CGRhs& c = sg->r[0];
       double rz = res[0];
       if (proj) {
