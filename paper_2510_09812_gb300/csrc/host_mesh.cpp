@@ -175,7 +175,7 @@ double tet_geometry(const double* x0, const double* x1, const double* x2, const 
 }  // namespace
 
 int64_t coarse_nodes_of(int64_t option, int64_t n) {
-  return option > 0 ? option : std::max<int64_t>(512, (n + 2047) / 2048);
+  return option > 0 ? option : std::max<int64_t>(512, (n + 4095) / 4096);
 }
 
 void coarse_bins(const HostMesh& hm, int64_t nodes_per_agg, int nb[3],
@@ -690,15 +690,20 @@ static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* 
     std::vector<double> y(n);
 #pragma omp for schedule(dynamic, 16)
     for (int64_t c = 0; c < n; ++c) {
-      // L y = e_c, then L^T x = y; x is column c (= row c: the inverse is symmetric)
+      // L y = e_c (y is zero above c), then L^T x = y from the bottom up to row c only: x is
+      // column c of the inverse, whose entries above c are those of later columns (symmetry)
       for (int64_t i = 0; i < c; ++i) y[i] = 0.0;
       for (int64_t i = c; i < n; ++i)
         y[i] = ((i == c ? 1.0 : 0.0) - dot4(&A[i * n + c], &y[c], i - c)) / A[i * n + i];
       double* x = inv->data() + c * n;
-      for (int64_t i = n - 1; i >= 0; --i)
+      for (int64_t i = n - 1; i >= c; --i)
         x[i] = (y[i] - dot4(&U[i * n + i + 1], &x[i + 1], n - 1 - i)) / U[i * n + i];
     }
   }
+  // rows hold the upper triangle (row c: entries c..n-1); mirror it
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t c = 0; c < i; ++c) (*inv)[i * n + c] = (*inv)[c * n + i];
   return true;
 }
 
