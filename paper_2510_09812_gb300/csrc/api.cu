@@ -1155,13 +1155,12 @@ class Engine final : public EngineBase {
     // two-level preconditioned CG on the singular systems (the pinned form stays plain)
     const bool pc = pc_ && !pinned_;
     const typename CoarseStore<T>::type* cinv = epr == 3 ? cinv3_ : cinv1_;
-    const int64_t* coff = epr == 3 ? inv_off3_ : inv_off1_;
+    const DSymTiles& TL = epr == 3 ? TL3_ : TL1_;
     const int64_t* rco = epr == 3 ? rc_off3_ : rc_off1_;
-    const ItemList& GL = epr == 3 ? GL3_ : GL1_;
     const T* dinv = epr == 3 ? dinv3_ : dinv1_;
     auto precondition = [&](T* z, int init) -> int {
       TK(GSPM_KCLASS_CG_VEC, launch_restrict<T>(L_, CC_, epr, r_, rco, rc_));
-      TK(GSPM_KCLASS_CG_VEC, launch_coarse_gemv<T>(L_, GL, CC_, epr, cinv, coff, rco, rc_, ec_));
+      TK(GSPM_KCLASS_CG_VEC, launch_coarse_symv<T>(L_, CC_, TL, epr, cinv, rco, rc_, qsym_, ec_));
       TK(GSPM_KCLASS_CG_VEC, launch_pcg_z<T>(L_, SG_, CC_, epr, r_, dinv, ec_, z, st, init, red_));
       return GSPM_OK;
     };
@@ -1182,7 +1181,7 @@ class Engine final : public EngineBase {
       return GSPM_OK;
     };
     if (capturing_)
-      ST(cg_graph_loop(slot, iter, B == 9 ? 1 : 0, pc ? 6 : 3));
+      ST(cg_graph_loop(slot, iter, B == 9 ? 1 : 0, pc ? 7 : 3));
     else
       ST(cg_loop(slot, iter, info));
     // singular system: move the solution to the pinned one (zero at the pinned node)
@@ -1248,59 +1247,99 @@ class Engine final : public EngineBase {
       for (int64_t row = 0; row < n_; ++row)
         if (aor[row] >= 0) arows[fill[aor[row]]++] = (int32_t)row;
     }
-    // blocks of rows padded to coarse_ld values, each block starting at a 16-byte boundary
+    // the inverses' stored upper-triangle tiles (see launch_coarse_symv): the symmetric part of
+    // the FP64 inverse (its column solves leave the two triangles a few ulps apart), rounded once
+    // to the storage type
     using S16 = typename CoarseStore<T>::type;
-    std::vector<int64_t> off3(S), off1(S);
-    int64_t t3 = 0, t1 = 0;
-    for (int sg = 0; sg < S; ++sg) {
-      const int64_t a = hb_.coarse[sg].n_agg;
-      off3[sg] = t3;
-      off1[sg] = t1;
-      t3 += 3 * a * coarse_ld<T>(3 * a);
-      t1 += a * coarse_ld<T>(a);
+    constexpr int64_t TS = kCoarseTile;
+    struct Tiles {
+      std::vector<S16> data;
+      std::vector<int32_t> tseg, tI, tJ, Tn;
+      std::vector<int64_t> t0, q0;
+      int64_t qn = 0;
+    } tl[2];  // [0]: 3 components (K^mech), [1]: 1 (K^ms)
+    for (int q = 0; q < 2; ++q) {
+      const int e = q == 0 ? 3 : 1;
+      Tiles& X = tl[q];
+      X.t0.resize(S);
+      X.Tn.resize(S);
+      X.q0.resize(S);
+      for (int sg = 0; sg < S; ++sg) {
+        const HostCoarse& hc = hb_.coarse[sg];
+        const std::vector<double>& inv = e == 3 ? hc.inv_mech : hc.inv_ms;
+        const int64_t nc = e * hc.n_agg, Tn = (nc + TS - 1) / TS;
+        X.t0[sg] = (int64_t)X.tseg.size();
+        X.Tn[sg] = (int32_t)Tn;
+        X.q0[sg] = X.qn;
+        X.qn += Tn * TS * Tn;
+        for (int64_t I = 0; I < Tn; ++I)
+          for (int64_t J = I; J < Tn; ++J) {
+            X.tseg.push_back(sg);
+            X.tI.push_back((int32_t)I);
+            X.tJ.push_back((int32_t)J);
+            const size_t base = X.data.size();
+            X.data.resize(base + TS * TS, S16(0));
+            for (int64_t r = 0; r < TS && I * TS + r < nc; ++r)
+              for (int64_t c = 0; c < TS && J * TS + c < nc; ++c) {
+                const int64_t gi = I * TS + r, gj = J * TS + c;
+                X.data[base + r * TS + c] =
+                    to_store<S16>(0.5 * (inv[gi * nc + gj] + inv[gj * nc + gi]));
+              }
+          }
+      }
     }
-    std::vector<S16> inv3(t3, S16(0)), inv1(t1, S16(0));
     std::vector<T> d3(3 * n_, T(0)), d1(n_, T(0));
-    // symmetric part of the FP64 inverse (its column solves leave the two triangles a few
-    // ulps apart), rounded once to the storage type
-    auto put = [](const std::vector<double>& inv, int64_t nc, S16* dst) {
-      const int64_t ldc = coarse_ld<T>(nc);
-      for (int64_t i = 0; i < nc; ++i)
-        for (int64_t j = 0; j < nc; ++j)
-          dst[i * ldc + j] = to_store<S16>(0.5 * (inv[i * nc + j] + inv[j * nc + i]));
-    };
     for (int sg = 0; sg < S; ++sg) {
       const HostCoarse& hc = hb_.coarse[sg];
-      const int64_t a = hc.n_agg;
-      put(hc.inv_mech, 3 * a, inv3.data() + off3[sg]);
-      put(hc.inv_ms, a, inv1.data() + off1[sg]);
       const int64_t r0 = hb_.seg_row0[sg];
       for (int64_t i = 0; i < hb_.seg_nrow[sg]; ++i) {
         d1[r0 + i] = (T)hc.dinv_ms[i];
         for (int a = 0; a < 3; ++a) d3[3 * (r0 + i) + a] = (T)hc.dinv_mech[3 * i + a];
       }
     }
+    int64_t max_q = 0;
+    for (int q = 0; q < 2; ++q) {
+      Tiles& X = tl[q];
+      const int64_t nt = (int64_t)X.tseg.size();
+      max_q = std::max(max_q, X.qn);
+      S16* d_data;
+      int32_t *d_tseg, *d_tI, *d_tJ, *d_Tn;
+      int64_t *d_t0, *d_q0;
+      ST(mem_.alloc(&d_data, nt * TS * TS));
+      ST(mem_.alloc(&d_tseg, nt));
+      ST(mem_.alloc(&d_tI, nt));
+      ST(mem_.alloc(&d_tJ, nt));
+      ST(mem_.alloc(&d_t0, S));
+      ST(mem_.alloc(&d_Tn, S));
+      ST(mem_.alloc(&d_q0, S));
+      CK(cudaMemcpy(d_data, X.data.data(), X.data.size() * sizeof(S16), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_tseg, X.tseg.data(), nt * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_tI, X.tI.data(), nt * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_tJ, X.tJ.data(), nt * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_t0, X.t0.data(), S * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_Tn, X.Tn.data(), S * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_q0, X.q0.data(), S * 8, cudaMemcpyHostToDevice));
+      (q == 0 ? cinv3_ : cinv1_) = d_data;
+      (q == 0 ? TL3_ : TL1_) = DSymTiles{nt, d_tseg, d_tI, d_tJ, d_t0, d_Tn, d_q0};
+    }
+    ST(mem_.alloc(&qsym_, max_q));
     int32_t *d_aor, *d_aptr, *d_arows, *d_aseg, *d_agg0;
     ST(mem_.alloc(&d_aor, n_));
     ST(mem_.alloc(&d_aptr, na + 1));
     ST(mem_.alloc(&d_arows, (int64_t)arows.size()));
     ST(mem_.alloc(&d_aseg, na));
     ST(mem_.alloc(&d_agg0, S + 1));
-    ST(mem_.alloc(&inv_off3_, S));
-    ST(mem_.alloc(&inv_off1_, S));
-    ST(mem_.alloc(&cinv3_, t3));
-    ST(mem_.alloc(&cinv1_, t1));
     ST(mem_.alloc(&dinv3_, 3 * n_));
     ST(mem_.alloc(&dinv1_, n_));
-    // rc: per segment a block zero-padded to the coarse row stride (read in whole packs)
+    // rc: per segment a block zero-padded to whole tiles
     std::vector<int64_t> rco3(S), rco1(S);
     int64_t r3 = 0, r1 = 0;
     for (int sg = 0; sg < S; ++sg) {
       const int64_t a = hb_.coarse[sg].n_agg;
       rco3[sg] = r3;
       rco1[sg] = r1;
-      r3 += coarse_ld<T>(3 * a);
-      r1 += coarse_ld<T>(a);
+      r3 += coarse_ld(3 * a);
+      r1 += coarse_ld(a);
     }
     ST(mem_.alloc(&rc_, std::max(r3, r1)));
     CK(cudaMemset(rc_, 0, std::max(r3, r1) * sizeof(T)));
@@ -1309,40 +1348,11 @@ class Engine final : public EngineBase {
     CK(cudaMemcpy(rc_off3_, rco3.data(), S * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(rc_off1_, rco1.data(), S * 8, cudaMemcpyHostToDevice));
     ST(mem_.alloc(&ec_, 3 * na));
-    // coarse GEMV work items: runs of kBlock / 32 coarse rows per segment (3 and 1 components
-    // per aggregate)
-    for (int e : {3, 1}) {
-      const int rows = kBlock / 32;
-      std::vector<int32_t> iseg, i0, i1, si0(S), sni(S);
-      for (int sg = 0; sg < S; ++sg) {
-        const int64_t c0 = (int64_t)agg0[sg] * e, nc = (int64_t)(agg0[sg + 1] - agg0[sg]) * e;
-        si0[sg] = (int32_t)iseg.size();
-        for (int64_t g = 0; g < nc; g += rows) {
-          iseg.push_back(sg);
-          i0.push_back((int32_t)(c0 + g));
-          i1.push_back((int32_t)(c0 + std::min<int64_t>(nc, g + rows)));
-        }
-        sni[sg] = (int32_t)iseg.size() - si0[sg];
-      }
-      const int ni = (int)iseg.size();
-      int32_t *d_iseg, *d_i0, *d_i1;
-      ST(mem_.alloc(&d_iseg, ni));
-      ST(mem_.alloc(&d_i0, ni));
-      ST(mem_.alloc(&d_i1, ni));
-      CK(cudaMemcpy(d_iseg, iseg.data(), ni * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d_i0, i0.data(), ni * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(d_i1, i1.data(), ni * 4, cudaMemcpyHostToDevice));
-      (e == 3 ? GL3_ : GL1_) = ItemList{ni, d_iseg, d_i0, d_i1, nullptr, nullptr};
-    }
     CK(cudaMemcpy(d_aor, aor.data(), n_ * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_aptr, aptr.data(), (na + 1) * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_arows, arows.data(), arows.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_aseg, aseg.data(), na * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_agg0, agg0.data(), (S + 1) * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(inv_off3_, off3.data(), S * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(inv_off1_, off1.data(), S * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(cinv3_, inv3.data(), t3 * sizeof(S16), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(cinv1_, inv1.data(), t1 * sizeof(S16), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dinv3_, d3.data(), 3 * n_ * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dinv1_, d1.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
     int contig = 1;
@@ -1640,10 +1650,10 @@ class Engine final : public EngineBase {
   // two-level preconditioner
   bool pc_ = false;
   DCoarse CC_{};
-  int64_t *inv_off3_ = nullptr, *inv_off1_ = nullptr;
-  typename CoarseStore<T>::type *cinv3_ = nullptr, *cinv1_ = nullptr;
+  typename CoarseStore<T>::type *cinv3_ = nullptr, *cinv1_ = nullptr;  // stored tiles
+  DSymTiles TL3_{}, TL1_{};
+  T* qsym_ = nullptr;  // partial products of the tiled coarse product
   int64_t *rc_off3_ = nullptr, *rc_off1_ = nullptr;
-  ItemList GL3_{}, GL1_{};  // coarse GEMV work items (3 and 1 components per aggregate)
   T *dinv3_ = nullptr, *dinv1_ = nullptr;
   T *dgs_eps_ = nullptr, *dgs_aeps_ = nullptr;  // Jacobi of the GSPM solves (NULL: plain)
   T *rc_ = nullptr, *ec_ = nullptr;

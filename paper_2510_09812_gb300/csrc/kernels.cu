@@ -1045,11 +1045,9 @@ __device__ __forceinline__ void stn(T* p, const T (&v)[N]) {
         *reinterpret_cast<const typename Pack16<T>::V*>(v + k * W);
 }
 
-// ec = A_c^-1 rc per segment.  Work items are runs of kBlock / 32 coarse rows of one segment
-// (one warp per row, no barrier); each warp streams its stored row in 16-byte packs (eight
-// bfloat16 or two doubles), D packs deep per lane, against the segment's rc block (zero-padded
-// to the row stride, read in packs too).  Accumulated in T: it only applies the preconditioner,
-// and FP64 instructions cost ~16x FP32 ones per warp on this part.
+// ec = A_c^-1 rc from the stored upper triangle (see launch_coarse_symv), loads of 16-byte packs
+// (eight bfloat16 or two doubles), accumulated in T: it only applies the preconditioner, and
+// FP64 instructions cost ~16x FP32 ones per warp on this part.
 template <typename S>
 struct CoarsePack;
 template <>
@@ -1083,48 +1081,91 @@ struct CoarsePack<double> {
   }
 };
 
+// Tile (I, J) of the stored upper triangle: A_IJ rc_J -> prow[t], and off the diagonal
+// A_IJ^T rc_I -> pcol[t].  A warp row-load covers RPW tile rows (LPR lanes per row, W values
+// per lane); the row sums reduce over a row's lanes, the column sums over the lanes that hold
+// the same columns and then over the warps in a fixed order.
 template <typename T, typename S>
-__global__ void __launch_bounds__(kBlock) k_coarse_gemv(ItemList IL, DCoarse C, int epr,
-                                                        const S* __restrict__ inv,
-                                                        const int64_t* __restrict__ inv_off,
-                                                        const int64_t* __restrict__ rc_off,
-                                                        const T* __restrict__ rc,
-                                                        T* __restrict__ ec) {
-  constexpr int W = CoarsePack<S>::W;
-  constexpr int D = 12;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
-    const int seg = IL.seg[item];
-    const int64_t c0 = (int64_t)C.seg_agg0[seg] * epr;
-    const int64_t nc = (int64_t)(C.seg_agg0[seg + 1] - C.seg_agg0[seg]) * epr;
-    const int64_t np = (nc + W - 1) / W;  // packs per padded row
-    const T* x = rc + rc_off[seg];
-    for (int64_t g = (int64_t)IL.sl0[item] + warp; g < IL.sl1[item]; g += nw) {
-      const S* row = inv + inv_off[seg] + (g - c0) * (np * W);
-      T acc = T(0);
-      for (int64_t t = lane; t < np; t += D * 32) {
-        typename CoarsePack<S>::Raw a[D];
+__global__ void __launch_bounds__(kBlock) k_coarse_symv_tiles(DSymTiles TL,
+                                                              const S* __restrict__ inv,
+                                                              const int64_t* __restrict__ rc_off,
+                                                              const T* __restrict__ rc,
+                                                              T* __restrict__ Q) {
+  constexpr int W = CoarsePack<S>::W, LPR = kCoarseTile / W, RPW = 32 / LPR;
+  constexpr int NW = kBlock / 32, RPP = NW * RPW, NP = kCoarseTile / RPP;
+  static_assert(LPR <= 32 && NP >= 1, "tile layout");
+  __shared__ T srow[kCoarseTile];
+  __shared__ T scol[NW][kCoarseTile];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cp = lane % LPR, rg = lane / LPR;
+  for (int64_t t = blockIdx.x; t < TL.ntiles; t += gridDim.x) {
+    const int seg = TL.tseg[t], I = TL.tI[t], J = TL.tJ[t];
+    const S* tile = inv + t * (int64_t)(kCoarseTile * kCoarseTile);
+    const T* xs = rc + rc_off[seg];
+    typename CoarsePack<S>::Raw a[NP];
 #pragma unroll
-        for (int u = 0; u < D; ++u) {
-          const int64_t tt = t + u * 32;
-          a[u] = tt < np ? CoarsePack<S>::load(row + tt * W) : CoarsePack<S>::zero();
-        }
+    for (int p = 0; p < NP; ++p)
+      a[p] = CoarsePack<S>::load(tile + (p * RPP + warp * RPW + rg) * kCoarseTile + cp * W);
+    T xj[W];
+    ldn<T, W>(xs + (int64_t)J * kCoarseTile + cp * W, xj);
+    T cs[W];
 #pragma unroll
-        for (int u = 0; u < D; ++u) {
-          const int64_t tt = t + u * 32;
-          if (tt < np) {
-            T w[W], xv[W];
-            CoarsePack<S>::cvt(a[u], w);
-            ldn<T, W>(x + tt * W, xv);
+    for (int c = 0; c < W; ++c) cs[c] = T(0);
 #pragma unroll
-            for (int c = 0; c < W; ++c) acc += w[c] * xv[c];
-          }
-        }
-      }
+    for (int p = 0; p < NP; ++p) {
+      const int row = p * RPP + warp * RPW + rg;
+      T w[W];
+      CoarsePack<S>::cvt(a[p], w);
+      T rs = T(0);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
-      if (lane == 0) ec[g] = acc;
+      for (int c = 0; c < W; ++c) rs += w[c] * xj[c];
+#pragma unroll
+      for (int o = 1; o < LPR; o <<= 1) rs += __shfl_xor_sync(kFull, rs, o);
+      if (cp == 0) srow[row] = rs;
+      const T xi = xs[(int64_t)I * kCoarseTile + row];
+#pragma unroll
+      for (int c = 0; c < W; ++c) cs[c] += w[c] * xi;
     }
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+      for (int c = 0; c < W; ++c) cs[c] += __shfl_xor_sync(kFull, cs[c], o);
+    if (rg == 0)
+#pragma unroll
+      for (int c = 0; c < W; ++c) scol[warp][cp * W + c] = cs[c];
+    __syncthreads();
+    if (threadIdx.x < kCoarseTile) {
+      const int64_t Tn = TL.seg_T[seg];
+      T* q = Q + TL.seg_q0[seg];
+      q[((int64_t)I * kCoarseTile + threadIdx.x) * Tn + J] = srow[threadIdx.x];
+      if (I != J) {
+        T v = T(0);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v += scol[w][threadIdx.x];
+        q[((int64_t)J * kCoarseTile + threadIdx.x) * Tn + I] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ec(g) = the sum of row g of Q (one warp per coarse row, lanes over the columns, fixed order)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_coarse_symv_sum(DCoarse C, DSymTiles TL, int epr,
+                                                            const T* __restrict__ Q,
+                                                            T* __restrict__ ec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ncoarse = C.nagg * epr;
+  for (int64_t g = gtid() >> 5; g < ncoarse; g += gstride() >> 5) {
+    const int seg = C.agg_seg[g / epr];
+    const int64_t loc = g - (int64_t)C.seg_agg0[seg] * epr;
+    const int64_t Tn = TL.seg_T[seg];
+    const T* q = Q + TL.seg_q0[seg] + loc * Tn;
+    T acc = T(0);
+    for (int64_t j = lane; j < Tn; j += 32) acc += q[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+    if (lane == 0) ec[g] = acc;
   }
 }
 
@@ -1954,18 +1995,17 @@ cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T*
 }
 
 template <typename T>
-cudaError_t launch_coarse_gemv(const Launch& L, const ItemList& GL, const DCoarse& C, int epr,
-                               const typename CoarseStore<T>::type* inv, const int64_t* inv_off,
-                               const int64_t* rc_off, const T* rc, T* ec) {
-  (*L.counter) += 1;
-  // rows are padded to whole 16-byte packs and blocks start at pack boundaries (inv_off)
+cudaError_t launch_coarse_symv(const Launch& L, const DCoarse& C, const DSymTiles& TL, int epr,
+                               const typename CoarseStore<T>::type* inv, const int64_t* rc_off,
+                               const T* rc, T* Q, T* ec) {
+  (*L.counter) += 2;
   if (!aligned16(inv) || !aligned16(rc)) return cudaErrorInvalidValue;
-  auto k = k_coarse_gemv<T, typename CoarseStore<T>::type>;
-  k<<<GSPM_GRID(L, (int64_t)GL.nitems * kBlock, k), kBlock, 0, L.stream>>>(GL, C, epr, inv,
-                                                                          inv_off, rc_off, rc, ec);
+  auto k1 = k_coarse_symv_tiles<T, typename CoarseStore<T>::type>;
+  k1<<<GSPM_GRID(L, TL.ntiles * kBlock, k1), kBlock, 0, L.stream>>>(TL, inv, rc_off, rc, Q);
+  auto k2 = k_coarse_symv_sum<T>;
+  k2<<<GSPM_GRID(L, C.nagg * epr * 32, k2), kBlock, 0, L.stream>>>(C, TL, epr, Q, ec);
   return cudaGetLastError();
 }
-
 template <typename T>
 cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
                          const T* dinv, const T* ec, T* z, CGState* st, int init, Red red) {
@@ -2176,9 +2216,9 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
                                          const double*, int, int);                                \
   template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*,           \
                                           const int64_t*, T*);                                    \
-  template cudaError_t launch_coarse_gemv<T>(const Launch&, const ItemList&, const DCoarse&, int,  \
+  template cudaError_t launch_coarse_symv<T>(const Launch&, const DCoarse&, const DSymTiles&, int, \
                                              const typename CoarseStore<T>::type*, const int64_t*, \
-                                             const int64_t*, const T*, T*);                       \
+                                             const T*, T*, T*);                                   \
   template cudaError_t launch_pcg_z<T>(const Launch&, const DSeg&, const DCoarse&, int, const T*, \
                                        const T*, const T*, T*, CGState*, int, Red);              \
   template cudaError_t launch_cg_init_gs<T>(const Launch&, const DSell&, const DSeg&, const T*,   \

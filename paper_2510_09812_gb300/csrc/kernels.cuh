@@ -181,28 +181,44 @@ cudaError_t launch_cg_pupdate(const Launch& L, const DSeg& G, int epr, int nr, i
 // rc = P^T r (per aggregate sums), ec = A_c^-1 rc (per segment dense block), then z and r.z;
 // the segment's last item stores rz (init) or beta = r.z / rz_old and rz.
 // rc layout: segment s's block starts at rc_off[s] and is zero-padded to coarse_ld(nc) values
-// (the coarse GEMV reads it in whole packs); ec is indexed by the global coarse index.
-// GL: work items of the coarse GEMV, runs of kBlock / 32 coarse rows of one segment (sl0 = first
-// row, sl1 = end).
+// (whole tiles); ec is indexed by the global coarse index.
 template <typename T>
 cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r,
                             const int64_t* rc_off, T* rc);
 // Storage of the dense coarse inverse: bfloat16 bits (uint16_t) under FP32 arithmetic, the
 // arithmetic type otherwise.  The inverse only applies the preconditioner: any fixed symmetric
-// positive definite rounding of it leaves the CG's solution unchanged.  Each row of a
-// segment's block of side nc is padded with zeros to a stride coarse_ld(nc) that keeps every
-// row 16-byte aligned; blocks start at multiples of that alignment (inv_off).
+// positive definite rounding of it leaves the CG's solution unchanged.  It is symmetric, so
+// only its upper triangle is stored, as kCoarseTile x kCoarseTile tiles (I <= J) of each
+// segment's block (zero-padded to whole tiles), row-major within a tile, tile rows one after
+// another: tile (I, J) of a segment with T tile rows is its tile number I T - I (I - 1) / 2 +
+// (J - I).
 template <typename T> struct CoarseStore { using type = T; };
 template <> struct CoarseStore<float> { using type = uint16_t; };
-template <typename T>
+constexpr int kCoarseTile = 64;
 inline int64_t coarse_ld(int64_t nc) {
-  constexpr int64_t w = 16 / sizeof(typename CoarseStore<T>::type);
-  return (nc + w - 1) / w * w;
+  return (nc + kCoarseTile - 1) / kCoarseTile * kCoarseTile;
 }
+// The stored tiles of all segments: tile t of the global list belongs to segment tseg[t], tile
+// row tI[t], column tJ[t]; segment s's tiles start at seg_tile0[s] and it has seg_T[s] tile rows.
+// The partials of segment s sit in Q at seg_q0[s], one row of seg_T[s] values per (padded)
+// coarse row of the segment.
+struct DSymTiles {
+  int64_t ntiles;
+  const int32_t* tseg;
+  const int32_t* tI;
+  const int32_t* tJ;
+  const int64_t* seg_tile0;
+  const int32_t* seg_T;
+  const int64_t* seg_q0;
+};
+// ec = A_c^-1 rc with the stored upper triangle, in two kernels: each tile (I, J) writes the
+// partial products A_IJ rc_J to Q(row I kCoarseTile + r, J) and, off the diagonal,
+// A_IJ^T rc_I to Q(row J kCoarseTile + c, I) (every stored value read once); then each coarse
+// row sums its row of Q in column order.  Q: scratch of sum over segments of T^2 kCoarseTile.
 template <typename T>
-cudaError_t launch_coarse_gemv(const Launch& L, const ItemList& GL, const DCoarse& C, int epr,
-                               const typename CoarseStore<T>::type* inv, const int64_t* inv_off,
-                               const int64_t* rc_off, const T* rc, T* ec);
+cudaError_t launch_coarse_symv(const Launch& L, const DCoarse& C, const DSymTiles& TL, int epr,
+                               const typename CoarseStore<T>::type* inv, const int64_t* rc_off,
+                               const T* rc, T* Q, T* ec);
 template <typename T>
 cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int epr, const T* r,
                          const T* dinv, const T* ec, T* z, CGState* st, int init, Red red);
