@@ -44,6 +44,15 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
+// Programmatic dependent launch (the CG loop kernels): a kernel launched with
+// launch_pdl first waits until the previous kernel of the stream has completed and its memory
+// is visible, then lets the next kernel be scheduled (its blocks wait the same way), so
+// launch latency overlaps the running kernel.  Outside such a launch both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // The last item of `seg` to arrive (its block partials already in red.partial[item]) sums the
 // segment's item partials in item order and returns true (totals in res[0..NC), valid in every
 // thread of that block).
@@ -632,6 +641,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
                                                     int64_t ld, const T* __restrict__ p,
                                                     T* __restrict__ q, CGState* st, Red red,
                                                     int pinned) {
+  pdl_enter();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
@@ -740,6 +750,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(DSeg G, ItemList IL, int e
                                                       const T* __restrict__ q, CGState* st,
                                                       int* nactive, Red red,
                                                       const T* __restrict__ dinv) {
+  pdl_enter();
   constexpr int W = Pack16<T>::W;
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
@@ -868,6 +879,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_pupdate(DSeg G, ItemList IL, int 
                                                        const T* __restrict__ r,
                                                        T* __restrict__ p, const CGState* st,
                                                        LoopCtl lc, const T* __restrict__ dinv) {
+  pdl_enter();
   constexpr int W = Pack16<T>::W;
   if (lc.count && blockIdx.x == 0 && threadIdx.x == 0) {
     const int c = *lc.count + 1;
@@ -978,6 +990,7 @@ template <typename T, int EPR>
 __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restrict__ r,
                                                      const int64_t* __restrict__ rc_off,
                                                      T* __restrict__ rc) {
+  pdl_enter();
   __shared__ T sm[EPR][kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t I = blockIdx.x; I < C.nagg; I += gridDim.x) {
@@ -1091,6 +1104,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_symv_tiles(DSymTiles TL,
                                                               const int64_t* __restrict__ rc_off,
                                                               const T* __restrict__ rc,
                                                               T* __restrict__ Q) {
+  pdl_enter();
   constexpr int W = CoarsePack<S>::W, LPR = kCoarseTile / W, RPW = 32 / LPR;
   constexpr int NW = kBlock / 32, RPP = NW * RPW, NP = kCoarseTile / RPP;
   static_assert(LPR <= 32 && NP >= 1, "tile layout");
@@ -1154,6 +1168,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_coarse_symv_sum(DCoarse C, DSymTiles TL, int epr,
                                                             const T* __restrict__ Q,
                                                             T* __restrict__ ec) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int64_t ncoarse = C.nagg * epr;
   for (int64_t g = gtid() >> 5; g < ncoarse; g += gstride() >> 5) {
@@ -1179,6 +1194,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_z(DSeg G, ItemList IL, DCoarse C
                                                   const T* __restrict__ ec,
                                                   T* __restrict__ z, CGState* st, int init,
                                                   Red red) {
+  pdl_enter();
   constexpr int N = 4 * EPR;
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
@@ -1780,6 +1796,28 @@ static ItemGrid item_grid(const Launch& L, const DSeg& G, const void* kernel) {
   return ItemGrid{grid_for(L, (int64_t)il.nitems * kBlock, kernel), il};
 }
 
+#define ST_CUDA(...)                      \
+  do {                                    \
+    const cudaError_t e_ = (__VA_ARGS__); \
+    if (e_ != cudaSuccess) return e_;     \
+  } while (0)
+
+// Launch of a CG loop kernel with programmatic stream serialisation (see pdl_enter)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), int grid, cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 #define GSPM_GRID(L, threads, kern) grid_for((L), (threads), reinterpret_cast<const void*>(kern))
 #define GSPM_IGRID(L, G, kern) item_grid((L), (G), reinterpret_cast<const void*>(kern))
 
@@ -1877,19 +1915,19 @@ static cudaError_t cg_spmv_variant(const Launch& L, const DSell& A, const DSeg& 
   if (B == 9) {
     auto k = k_cg_spmv<T, 9, 1, VAR>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
-    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
+    return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 1) {
     auto k = k_cg_spmv<T, 1, 1, VAR>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
-    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
+    return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 2) {
     auto k = k_cg_spmv<T, 1, 2, VAR>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
-    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
+    return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 3) {
     auto k = k_cg_spmv<T, 1, 3, VAR>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
-    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, ld, p, q, st, red, pinned);
+    return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1912,12 +1950,12 @@ cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const
 static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 template <typename T, int NR, bool VEC>
-static void cg_update_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, T* x, T* r,
+static cudaError_t cg_update_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, T* x, T* r,
                          const T* p, const T* q, CGState* st, int* nactive, Red red,
                          const T* dinv) {
   auto k = k_cg_update<T, NR, VEC>;
   const ItemGrid ig = GSPM_IGRID(L, G, k);
-  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, x, r, p, q, st, nactive, red, dinv);
+  return launch_pdl(k, ig.grid, L.stream, G, ig.list, epr, ld, x, r, p, q, st, nactive, red, dinv);
 }
 
 template <typename T, bool VEC>
@@ -1925,9 +1963,9 @@ static cudaError_t cg_update_vec(const Launch& L, const DSeg& G, int epr, int nr
                                  T* x, T* r, const T* p, const T* q, CGState* st, int* nactive,
                                  Red red, const T* dinv) {
   switch (nr) {
-    case 1: cg_update_nr<T, 1, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv); break;
-    case 2: cg_update_nr<T, 2, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv); break;
-    case 3: cg_update_nr<T, 3, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv); break;
+    case 1: ST_CUDA(cg_update_nr<T, 1, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv)); break;
+    case 2: ST_CUDA(cg_update_nr<T, 2, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv)); break;
+    case 3: ST_CUDA(cg_update_nr<T, 3, VEC>(L, G, epr, ld, x, r, p, q, st, nactive, red, dinv)); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1946,11 +1984,11 @@ cudaError_t launch_cg_update(const Launch& L, const DSeg& G, int epr, int nr, in
 }
 
 template <typename T, int NR, bool VEC>
-static void cg_pupdate_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, const T* r, T* p,
+static cudaError_t cg_pupdate_nr(const Launch& L, const DSeg& G, int epr, int64_t ld, const T* r, T* p,
                           const CGState* st, const LoopCtl& lc, const T* dinv) {
   auto k = k_cg_pupdate<T, NR, VEC>;
   const ItemGrid ig = GSPM_IGRID(L, G, k);
-  k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, epr, ld, r, p, st, lc, dinv);
+  return launch_pdl(k, ig.grid, L.stream, G, ig.list, epr, ld, r, p, st, lc, dinv);
 }
 
 template <typename T, bool VEC>
@@ -1958,9 +1996,9 @@ static cudaError_t cg_pupdate_vec(const Launch& L, const DSeg& G, int epr, int n
                                   const T* r, T* p, const CGState* st, const LoopCtl& lc,
                                   const T* dinv) {
   switch (nr) {
-    case 1: cg_pupdate_nr<T, 1, VEC>(L, G, epr, ld, r, p, st, lc, dinv); break;
-    case 2: cg_pupdate_nr<T, 2, VEC>(L, G, epr, ld, r, p, st, lc, dinv); break;
-    case 3: cg_pupdate_nr<T, 3, VEC>(L, G, epr, ld, r, p, st, lc, dinv); break;
+    case 1: ST_CUDA(cg_pupdate_nr<T, 1, VEC>(L, G, epr, ld, r, p, st, lc, dinv)); break;
+    case 2: ST_CUDA(cg_pupdate_nr<T, 2, VEC>(L, G, epr, ld, r, p, st, lc, dinv)); break;
+    case 3: ST_CUDA(cg_pupdate_nr<T, 3, VEC>(L, G, epr, ld, r, p, st, lc, dinv)); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1984,10 +2022,10 @@ cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T*
   (*L.counter) += 1;
   if (epr == 3) {
     auto k = k_restrict<T, 3>;
-    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc_off, rc);
+    ST_CUDA(launch_pdl(k, GSPM_GRID(L, C.nagg * kBlock, k), L.stream, C, r, rc_off, rc));
   } else if (epr == 1) {
     auto k = k_restrict<T, 1>;
-    k<<<GSPM_GRID(L, C.nagg * kBlock, k), kBlock, 0, L.stream>>>(C, r, rc_off, rc);
+    ST_CUDA(launch_pdl(k, GSPM_GRID(L, C.nagg * kBlock, k), L.stream, C, r, rc_off, rc));
   } else {
     return cudaErrorInvalidValue;
   }
@@ -2001,9 +2039,9 @@ cudaError_t launch_coarse_symv(const Launch& L, const DCoarse& C, const DSymTile
   (*L.counter) += 2;
   if (!aligned16(inv) || !aligned16(rc)) return cudaErrorInvalidValue;
   auto k1 = k_coarse_symv_tiles<T, typename CoarseStore<T>::type>;
-  k1<<<GSPM_GRID(L, TL.ntiles * kBlock, k1), kBlock, 0, L.stream>>>(TL, inv, rc_off, rc, Q);
+  ST_CUDA(launch_pdl(k1, GSPM_GRID(L, TL.ntiles * kBlock, k1), L.stream, TL, inv, rc_off, rc, Q));
   auto k2 = k_coarse_symv_sum<T>;
-  k2<<<GSPM_GRID(L, C.nagg * epr * 32, k2), kBlock, 0, L.stream>>>(C, TL, epr, Q, ec);
+  ST_CUDA(launch_pdl(k2, GSPM_GRID(L, C.nagg * epr * 32, k2), L.stream, C, TL, epr, Q, ec));
   return cudaGetLastError();
 }
 template <typename T>
@@ -2013,11 +2051,11 @@ cudaError_t launch_pcg_z(const Launch& L, const DSeg& G, const DCoarse& C, int e
   if (epr == 3) {
     auto k = k_pcg_z<T, 3>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
-    k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, C, r, dinv, ec, z, st, init, red);
+    ST_CUDA(launch_pdl(k, ig.grid, L.stream, G, ig.list, C, r, dinv, ec, z, st, init, red));
   } else if (epr == 1) {
     auto k = k_pcg_z<T, 1>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
-    k<<<ig.grid, kBlock, 0, L.stream>>>(G, ig.list, C, r, dinv, ec, z, st, init, red);
+    ST_CUDA(launch_pdl(k, ig.grid, L.stream, G, ig.list, C, r, dinv, ec, z, st, init, red));
   } else {
     return cudaErrorInvalidValue;
   }
