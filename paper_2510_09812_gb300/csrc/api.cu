@@ -1251,7 +1251,7 @@ class Engine final : public EngineBase {
     // the FP64 inverse (its column solves leave the two triangles a few ulps apart), rounded once
     // to the storage type
     using S16 = typename CoarseStore<T>::type;
-    constexpr int64_t TS = kCoarseTile;
+    constexpr int64_t TS = coarse_tile<T>();
     struct Tiles {
       std::vector<S16> data;
       std::vector<int32_t> tseg, tI, tJ, Tn;
@@ -1338,8 +1338,8 @@ class Engine final : public EngineBase {
       const int64_t a = hb_.coarse[sg].n_agg;
       rco3[sg] = r3;
       rco1[sg] = r1;
-      r3 += coarse_ld(3 * a);
-      r1 += coarse_ld(a);
+      r3 += coarse_ld<T>(3 * a);
+      r1 += coarse_ld<T>(a);
     }
     ST(mem_.alloc(&rc_, std::max(r3, r1)));
     CK(cudaMemset(rc_, 0, std::max(r3, r1) * sizeof(T)));

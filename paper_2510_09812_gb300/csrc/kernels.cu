@@ -1105,6 +1105,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_symv_tiles(DSymTiles TL,
                                                               const T* __restrict__ rc,
                                                               T* __restrict__ Q) {
   pdl_enter();
+  constexpr int kCoarseTile = coarse_tile<T>();
   constexpr int W = CoarsePack<S>::W, LPR = kCoarseTile / W, RPW = 32 / LPR;
   constexpr int NW = kBlock / 32, RPP = NW * RPW, NP = kCoarseTile / RPP;
   static_assert(LPR <= 32 && NP >= 1, "tile layout");

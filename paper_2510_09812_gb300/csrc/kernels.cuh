@@ -188,15 +188,20 @@ cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T*
 // Storage of the dense coarse inverse: bfloat16 bits (uint16_t) under FP32 arithmetic, the
 // arithmetic type otherwise.  The inverse only applies the preconditioner: any fixed symmetric
 // positive definite rounding of it leaves the CG's solution unchanged.  It is symmetric, so
-// only its upper triangle is stored, as kCoarseTile x kCoarseTile tiles (I <= J) of each
-// segment's block (zero-padded to whole tiles), row-major within a tile, tile rows one after
-// another: tile (I, J) of a segment with T tile rows is its tile number I T - I (I - 1) / 2 +
-// (J - I).
+// only its upper triangle is stored, as square tiles (I <= J) of each segment's block
+// (zero-padded to whole tiles), row-major within a tile, tile rows one after another: tile
+// (I, J) of a segment with T tile rows is its tile number I T - I (I - 1) / 2 + (J - I).  The
+// tile side (coarse_tile: 128 for BF16, 64 for FP64) makes a row of a tile 16 or 32 lanes of
+// 16-byte packs.
 template <typename T> struct CoarseStore { using type = T; };
 template <> struct CoarseStore<float> { using type = uint16_t; };
-constexpr int kCoarseTile = 64;
+template <typename T>
+__host__ __device__ constexpr int coarse_tile() {
+  return sizeof(typename CoarseStore<T>::type) == 2 ? 128 : 64;
+}
+template <typename T>
 inline int64_t coarse_ld(int64_t nc) {
-  return (nc + kCoarseTile - 1) / kCoarseTile * kCoarseTile;
+  return (nc + coarse_tile<T>() - 1) / coarse_tile<T>() * coarse_tile<T>();
 }
 // The stored tiles of all segments: tile t of the global list belongs to segment tseg[t], tile
 // row tI[t], column tJ[t]; segment s's tiles start at seg_tile0[s] and it has seg_T[s] tile rows.
@@ -212,9 +217,9 @@ struct DSymTiles {
   const int64_t* seg_q0;
 };
 // ec = A_c^-1 rc with the stored upper triangle, in two kernels: each tile (I, J) writes the
-// partial products A_IJ rc_J to Q(row I kCoarseTile + r, J) and, off the diagonal,
-// A_IJ^T rc_I to Q(row J kCoarseTile + c, I) (every stored value read once); then each coarse
-// row sums its row of Q in column order.  Q: scratch of sum over segments of T^2 kCoarseTile.
+// partial products A_IJ rc_J to Q(row I tile + r, J) and, off the diagonal, A_IJ^T rc_I to
+// Q(row J tile + c, I) (every stored value read once); then each coarse row sums its row of Q
+// in column order.  Q: scratch of sum over segments of T^2 tile values.
 template <typename T>
 cudaError_t launch_coarse_symv(const Launch& L, const DCoarse& C, const DSymTiles& TL, int epr,
                                const typename CoarseStore<T>::type* inv, const int64_t* rc_off,
