@@ -102,8 +102,13 @@ extern "C" {
                                          node zero subtracted): the same solution in exact
                                          arithmetic, with far fewer CG iterations, since
                                          pinning one node of a periodic body leaves an
-                                         eigenvalue of order 1/n.  Stopping test of either form:
-                                         ||r|| < rtol ||b||, with its own r and b               */
+                                         eigenvalue of order 1/n.  The singular form runs
+                                         projected off the constants (x0, r.r and every search
+                                         direction without their per-component means), which
+                                         keeps FP32 rounding of K 1 from steering the iteration
+                                         along the constants.  Stopping test of either form:
+                                         ||r|| < rtol ||b||, with its own r and b (the
+                                         projected r for the singular form)                   */
 
 /* ---- inputs ----------------------------------------------------------------------------- */
 typedef struct gspm_mesh_desc {
@@ -150,7 +155,7 @@ typedef struct gspm_options {
                          max(512, n / 4096), n the mesh's nodes); sets the coarse problem size
                          (3 n / coarse_nodes for K^mech), whose dense inverse is formed at load:
                          smaller aggregates cut CG iterations, cost load time (cubic in the
-                         coarse size) and coarse-GEMV traffic per iteration (quadratic)      */
+                         coarse size) and coarse-product traffic per iteration (quadratic)   */
   void* stream;       /* cudaStream_t for all work of the context; NULL = legacy default stream */
 } gspm_options;
 
