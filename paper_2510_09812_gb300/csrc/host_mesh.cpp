@@ -669,38 +669,118 @@ static inline double dot4(const double* a, const double* b, int64_t len) {
   return (s0 + s1) + (s2 + s3);
 }
 
-// In-place Cholesky of the SPD matrix A (n x n, row-major, lower factor) and its explicit
-// inverse; false if a pivot is not positive.
-static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* inv) {
-  for (int64_t j = 0; j < n; ++j) {
-    const double d = A[j * n + j] - dot4(&A[j * n], &A[j * n], j);
-    if (!(d > 0.0)) return false;
-    const double ljj = std::sqrt(d);
-    A[j * n + j] = ljj;
-#pragma omp parallel for schedule(static)
-    for (int64_t i = j + 1; i < n; ++i) A[i * n + j] = (A[i * n + j] - dot4(&A[i * n], &A[j * n], j)) / ljj;
+// acc[x][y] += sum_t a[x][t] b[y][t] for t < len: a 4 x 4 register tile of dot products of
+// rows, each loaded value serving four products
+static inline void tile4x4(const double* const a[4], const double* const b[4], int64_t len,
+                           double (&acc)[4][4]) {
+  for (int64_t t = 0; t < len; ++t) {
+    const double a0 = a[0][t], a1 = a[1][t], a2 = a[2][t], a3 = a[3][t];
+    const double b0 = b[0][t], b1 = b[1][t], b2 = b[2][t], b3 = b[3][t];
+    acc[0][0] += a0 * b0; acc[0][1] += a0 * b1; acc[0][2] += a0 * b2; acc[0][3] += a0 * b3;
+    acc[1][0] += a1 * b0; acc[1][1] += a1 * b1; acc[1][2] += a1 * b2; acc[1][3] += a1 * b3;
+    acc[2][0] += a2 * b0; acc[2][1] += a2 * b1; acc[2][2] += a2 * b2; acc[2][3] += a2 * b3;
+    acc[3][0] += a3 * b0; acc[3][1] += a3 * b1; acc[3][2] += a3 * b2; acc[3][3] += a3 * b3;
   }
-  // U = L^T row-major, so that both triangular sweeps read contiguous rows
-  std::vector<double> U(n * n, 0.0);
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t k = 0; k <= i; ++k) U[k * n + i] = A[i * n + k];
-  inv->assign(n * n, 0.0);
-#pragma omp parallel
-  {
-    std::vector<double> y(n);
-#pragma omp for schedule(dynamic, 16)
-    for (int64_t c = 0; c < n; ++c) {
-      // L y = e_c (y is zero above c), then L^T x = y from the bottom up to row c only: x is
-      // column c of the inverse, whose entries above c are those of later columns (symmetry)
-      for (int64_t i = 0; i < c; ++i) y[i] = 0.0;
-      for (int64_t i = c; i < n; ++i)
-        y[i] = ((i == c ? 1.0 : 0.0) - dot4(&A[i * n + c], &y[c], i - c)) / A[i * n + i];
-      double* x = inv->data() + c * n;
-      for (int64_t i = n - 1; i >= c; --i)
-        x[i] = (y[i] - dot4(&U[i * n + i + 1], &x[i + 1], n - 1 - i)) / U[i * n + i];
+}
+
+// Blocked right-looking Cholesky of the SPD matrix A (n x n, row-major, lower factor in place):
+// per block of kb columns, the diagonal block unblocked, the rows below it by forward
+// substitution, then the trailing lower triangle updated by the block's rank-kb product in
+// 4 x 4 tiles.
+static bool chol_blocked(std::vector<double>& A, int64_t n) {
+  constexpr int64_t NB = 128;
+  for (int64_t k = 0; k < n; k += NB) {
+    const int64_t kb = std::min(NB, n - k);
+    for (int64_t j = k; j < k + kb; ++j) {
+      const double d = A[j * n + j] - dot4(&A[j * n + k], &A[j * n + k], j - k);
+      if (!(d > 0.0)) return false;
+      const double ljj = std::sqrt(d);
+      A[j * n + j] = ljj;
+      for (int64_t i = j + 1; i < k + kb; ++i)
+        A[i * n + j] = (A[i * n + j] - dot4(&A[i * n + k], &A[j * n + k], j - k)) / ljj;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = k + kb; i < n; ++i)
+      for (int64_t j = k; j < k + kb; ++j)
+        A[i * n + j] = (A[i * n + j] - dot4(&A[i * n + k], &A[j * n + k], j - k)) / A[j * n + j];
+    const int64_t m0 = k + kb, nt = (n - m0 + 3) / 4;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t bi = 0; bi < nt; ++bi) {
+      const int64_t i0 = m0 + 4 * bi;
+      for (int64_t j0 = m0; j0 <= i0; j0 += 4) {
+        double acc[4][4] = {};
+        const double* a[4];
+        const double* b[4];
+        for (int x = 0; x < 4; ++x) {
+          a[x] = &A[std::min(i0 + x, n - 1) * n + k];
+          b[x] = &A[std::min(j0 + x, n - 1) * n + k];
+        }
+        tile4x4(a, b, kb, acc);
+        for (int x = 0; x < 4; ++x)
+          for (int y = 0; y < 4; ++y) {
+            const int64_t i = i0 + x, j = j0 + y;
+            if (i < n && j <= i) A[i * n + j] -= acc[x][y];
+          }
+      }
     }
   }
-  // rows hold the upper triangle (row c: entries c..n-1); mirror it
+  return true;
+}
+
+// Explicit inverse of the SPD matrix A (overwritten by its Cholesky factor L); false if a pivot
+// is not positive.  W = L^-1 is formed transposed (Wt row j = column j of W, zero left of the
+// diagonal) four rows at a time: Wt[j][i] = (delta_ij - sum_{k<i} L[i][k] Wt[j][k]) / L[i][i],
+// the part k < i0 of each 4 x 4 block of (j, i) as a register tile, the rest in order.  Then
+// A^-1 = W^T W: entry (a, b >= a) = sum_k Wt[a][k] Wt[b][k], again in 4 x 4 tiles, and the lower
+// triangle mirrored.
+static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* inv) {
+  if (!chol_blocked(A, n)) return false;
+  std::vector<double> Wt(n * n, 0.0);
+  const int64_t nb = (n + 3) / 4;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t bj = 0; bj < nb; ++bj) {
+    const int64_t j0 = 4 * bj;
+    for (int64_t i0 = j0; i0 < n; i0 += 4) {
+      double acc[4][4] = {};  // [x: row j0 + x of Wt][y: column i0 + y]
+      const double* a[4];
+      const double* b[4];
+      for (int x = 0; x < 4; ++x) {
+        a[x] = &Wt[std::min(j0 + x, n - 1) * n + j0];
+        b[x] = &A[std::min(i0 + x, n - 1) * n + j0];
+      }
+      tile4x4(a, b, i0 - j0, acc);
+      for (int y = 0; y < 4 && i0 + y < n; ++y) {
+        const int64_t i = i0 + y;
+        for (int x = 0; x < 4 && j0 + x < n; ++x) {
+          const int64_t j = j0 + x;
+          if (i < j) continue;
+          double s = acc[x][y];
+          for (int64_t k = i0; k < i; ++k) s += A[i * n + k] * Wt[j * n + k];
+          Wt[j * n + i] = ((i == j ? 1.0 : 0.0) - s) / A[i * n + i];
+        }
+      }
+    }
+  }
+  inv->assign(n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t ba = 0; ba < nb; ++ba) {
+    const int64_t a0 = 4 * ba;
+    for (int64_t b0 = a0; b0 < n; b0 += 4) {
+      double acc[4][4] = {};
+      const double* a[4];
+      const double* b[4];
+      for (int x = 0; x < 4; ++x) {
+        a[x] = &Wt[std::min(a0 + x, n - 1) * n + b0];
+        b[x] = &Wt[std::min(b0 + x, n - 1) * n + b0];
+      }
+      tile4x4(a, b, n - b0, acc);
+      for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y) {
+          const int64_t r = a0 + x, c = b0 + y;
+          if (r < n && c < n && c >= r) (*inv)[r * n + c] = acc[x][y];
+        }
+    }
+  }
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < n; ++i)
     for (int64_t c = 0; c < i; ++c) (*inv)[i * n + c] = (*inv)[c * n + i];
