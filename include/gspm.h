@@ -86,7 +86,7 @@ extern "C" {
                                          (Sec. 3.1).  Default (singular form only): CG with the
                                          two-level preconditioner z = D^-1 r + P A_c^-1 P^T r,
                                          D = diag(K), P = plain aggregation of the nodes into
-                                         coordinate bins of max(512, n/4096) nodes (the same
+                                         coordinate bins of max(512, n/6000) nodes (the same
                                          for each component), A_c = P^T K P made definite on
                                          the constants and inverted densely at load.  The
                                          stopping test stays ||r|| < rtol ||b||, so the
@@ -152,7 +152,7 @@ typedef struct gspm_options {
   int max_iter;       /* per CG solve; exceeding it returns GSPM_ENOCONV                       */
   unsigned flags;     /* GSPM_FLAG_*                                                           */
   int64_t coarse_nodes; /* nodes per aggregate of the two-level preconditioner (0: the default
-                         max(512, n / 4096), n the mesh's nodes); sets the coarse problem size
+                         max(512, n / 6000), n the mesh's nodes); sets the coarse problem size
                          (3 n / coarse_nodes for K^mech), whose dense inverse is formed at load:
                          smaller aggregates cut CG iterations, cost load time (cubic in the
                          coarse size) and coarse-product traffic per iteration (quadratic)   */

@@ -175,7 +175,7 @@ double tet_geometry(const double* x0, const double* x1, const double* x2, const 
 }  // namespace
 
 int64_t coarse_nodes_of(int64_t option, int64_t n) {
-  return option > 0 ? option : std::max<int64_t>(512, (n + 4095) / 4096);
+  return option > 0 ? option : std::max<int64_t>(512, (n + 5999) / 6000);
 }
 
 void coarse_bins(const HostMesh& hm, int64_t nodes_per_agg, int nb[3],

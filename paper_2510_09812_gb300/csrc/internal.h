@@ -56,7 +56,7 @@ struct HostMesh {
 // aggregates of coarse_nodes_of(coarse_nodes, n) nodes)
 int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes, HostMesh* hm);
 
-// Aggregate size: the option when positive, else max(512, n / 4096)
+// Aggregate size: the option when positive, else max(512, n / 6000)
 int64_t coarse_nodes_of(int64_t option, int64_t n);
 // Coordinate bins of about nodes_per_agg nodes: edge H = (V nodes_per_agg / n)^(1/3), nb[a] =
 // round(L_a / H) bins per axis; bin_of[i] (x fastest) for every unique node i, from its
