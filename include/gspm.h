@@ -69,7 +69,10 @@ extern "C" {
                               aggregate is then a contiguous range of rows, which the
                               restriction reads in order                                       */
 
-#define GSPM_FLAG_HOST_ONLY 1u        /* build host structures only; no CUDA call is made      */
+#define GSPM_FLAG_HOST_ONLY 1u        /* build host structures only (mesh, node graph,
+                                         assembly and, unless PINNED_CG or PLAIN_CG, the
+                                         two-level preconditioner's coarse operators and their
+                                         inverses); no CUDA call is made                      */
 #define GSPM_FLAG_ROW2_PRINTED 2u     /* Algorithm B.1 second row exactly as printed (m^n_1,
                                          g^n_1) instead of the Gauss-Seidel sweep (m*_1, g*_1)  */
 #define GSPM_FLAG_NO_AUTOTUNE 4u      /* skip the SpMV schedule autotuner (schedule 0)          */
@@ -206,6 +209,11 @@ typedef struct gspm_step_stats {
 #define GSPM_EXPORT_AGGREGATES 6        /* int32 [n_unique] preconditioner aggregate per node   */
 #define GSPM_EXPORT_COARSE_K_MS 7       /* double [n_agg^2] P^T K^ms P (unpinned K), row-major  */
 #define GSPM_EXPORT_COARSE_K_MECH 8     /* double [(3 n_agg)^2] P^T K^mech P, index 3 I + a     */
+#define GSPM_EXPORT_COARSE_INV_MS 9     /* double [n_agg^2] inverse of P^T K^ms P + rho 1 1^T    */
+#define GSPM_EXPORT_COARSE_INV_MECH 10  /* double [(3 n_agg)^2] inverse of P^T K^mech P plus rho
+                                           on each component's constants (rho = trace / (3 n_agg)
+                                           / n_agg); the FP64 inverses before rounding to the
+                                           device storage, kept by host-only contexts only     */
 
 /* fields readable / writable with gspm_get_field / gspm_set_field (unique-node order) */
 #define GSPM_FIELD_M 0       /* [n][3] magnetisation m (non-magnetic nodes forced to 0)       */

@@ -1717,14 +1717,15 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
       }
       return st;
     }
-    host_sell_build(c->hm[k], &hs[k]);
-    if (!c->host_only) host_assemble(c->hm[k], hs[k], c->P, &ops[k]);
   }
   // two-level preconditioner of the K^ms / K^mech solves (singular form only): aggregates of
-  // coarse_nodes nodes, by default max(512, n / 2048)
+  // coarse_nodes_of(coarse_nodes, n) nodes; host-only contexts build it too (for export)
   std::vector<HostCoarse> coarse;
-  const bool two_level = !c->host_only &&
-                         !(opt->flags & (GSPM_FLAG_PINNED_CG | GSPM_FLAG_PLAIN_CG));
+  const bool two_level = !(opt->flags & (GSPM_FLAG_PINNED_CG | GSPM_FLAG_PLAIN_CG));
+  for (int k = 0; k < nmesh; ++k) {
+    host_sell_build(c->hm[k], &hs[k]);
+    if (!c->host_only || two_level) host_assemble(c->hm[k], hs[k], c->P, &ops[k]);
+  }
   if (two_level) {
     coarse.resize(nmesh);
     for (int k = 0; k < nmesh; ++k) {
@@ -1737,6 +1738,7 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
     c->hb.sell = std::move(hs[0]);
     c->hb.n_nodes = 0;
     for (auto& h : c->hm) c->hb.n_nodes += h.n;
+    c->hb.coarse = std::move(coarse);
   } else {
     host_batch_build(c->hm, hs, ops, &c->hb);
     c->hb.coarse = std::move(coarse);
@@ -1862,7 +1864,9 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
     case GSPM_EXPORT_LUMPED_MASS: return put(hm.ML.data(), hm.n, 8);
     case GSPM_EXPORT_AGGREGATES:
     case GSPM_EXPORT_COARSE_K_MS:
-    case GSPM_EXPORT_COARSE_K_MECH: {
+    case GSPM_EXPORT_COARSE_K_MECH:
+    case GSPM_EXPORT_COARSE_INV_MS:
+    case GSPM_EXPORT_COARSE_INV_MECH: {
       if (ctx->hb.coarse.empty()) {
         set_error("mesh_export: the context has no two-level preconditioner");
         return GSPM_ESTATE;
@@ -1871,6 +1875,14 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
       if (what == GSPM_EXPORT_COARSE_K_MS) return put(hc.Kc_ms.data(), (int64_t)hc.Kc_ms.size(), 8);
       if (what == GSPM_EXPORT_COARSE_K_MECH)
         return put(hc.Kc_mech.data(), (int64_t)hc.Kc_mech.size(), 8);
+      if (what == GSPM_EXPORT_COARSE_INV_MS || what == GSPM_EXPORT_COARSE_INV_MECH) {
+        const std::vector<double>& v = what == GSPM_EXPORT_COARSE_INV_MS ? hc.inv_ms : hc.inv_mech;
+        if (v.empty()) {
+          set_error("mesh_export: coarse inverses are kept by host-only contexts only");
+          return GSPM_ESTATE;
+        }
+        return put(v.data(), (int64_t)v.size(), 8);
+      }
       std::vector<int32_t> a(hm.n);
       for (int64_t i = 0; i < hm.n; ++i) a[hm.perm[i]] = hc.agg[i];
       return put(a.data(), hm.n, 4);

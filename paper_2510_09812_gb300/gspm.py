@@ -20,8 +20,9 @@ PREC_F64, PREC_MIXED = 0, 1
 ORDER_NONE, ORDER_RCM, ORDER_AGGREGATE = 0, 1, 2
 FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE, FLAG_GRAPH, FLAG_PINNED_CG = 1, 2, 4, 8, 16
 FLAG_RESOLVE_AT_MSTAR, FLAG_PLAIN_CG = 32, 64
-EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC, \
-    EXPORT_LUMPED_MASS, EXPORT_AGGREGATES, EXPORT_COARSE_K_MS, EXPORT_COARSE_K_MECH = range(9)
+(EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC,
+ EXPORT_LUMPED_MASS, EXPORT_AGGREGATES, EXPORT_COARSE_K_MS, EXPORT_COARSE_K_MECH,
+ EXPORT_COARSE_INV_MS, EXPORT_COARSE_INV_MECH) = range(11)
 FIELD_M, FIELD_U, FIELD_DISP, FIELD_HD, FIELD_STRAIN, FIELD_H, FIELD_DISP_PREV = range(7)
 X0_PREV, X0_ZERO, X0_EXTRAPOLATE, X0_LEARNED = range(4)
 MPNN_PARAMS = 26051
@@ -271,7 +272,9 @@ class Context:
                        EXPORT_LUMPED_MASS: (inf["n_unique"], np.float64),
                        EXPORT_AGGREGATES: (inf["n_unique"], np.int32),
                        EXPORT_COARSE_K_MS: (inf["n_aggregates"] ** 2, np.float64),
-                       EXPORT_COARSE_K_MECH: (9 * inf["n_aggregates"] ** 2, np.float64)}[what]
+                       EXPORT_COARSE_K_MECH: (9 * inf["n_aggregates"] ** 2, np.float64),
+                       EXPORT_COARSE_INV_MS: (inf["n_aggregates"] ** 2, np.float64),
+                       EXPORT_COARSE_INV_MECH: (9 * inf["n_aggregates"] ** 2, np.float64)}[what]
         out = np.empty(size, dtype=dtype)
         _check(lib.gspm_mesh_export(self._h, what, C.c_void_p(out.ctypes.data), size),
                "gspm_mesh_export")

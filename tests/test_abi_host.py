@@ -39,9 +39,9 @@ MESHES = [
 ]
 
 
-def _aggregate_order(mesh, wm, npa):
-    """Nodes sorted by coordinate bin of about npa nodes (x-fastest bin index, ties by index),
-    bins from the wrapped coordinates of each node's first stored copy."""
+def _bins(mesh, wm, npa):
+    """Coordinate bin (x-fastest index) of every unique node for bins of about npa nodes, from
+    the wrapped coordinates of each node's first stored copy."""
     first = np.full(wm.n, -1)
     first[wm.unique_of_stored[::-1]] = np.arange(wm.unique_of_stored.size)[::-1]
     xw = mesh.coords[first]
@@ -50,8 +50,12 @@ def _aggregate_order(mesh, wm, npa):
     H = np.cbrt(np.prod(L) * npa / wm.n)
     nb = np.maximum(1, np.floor(L / H + 0.5)).astype(np.int64)
     t = np.clip(np.floor((xw - lo) / L * nb).astype(np.int64), 0, nb - 1)
-    b = t[:, 0] + nb[0] * (t[:, 1] + nb[1] * t[:, 2])
-    return np.argsort(b, kind="stable")
+    return t[:, 0] + nb[0] * (t[:, 1] + nb[1] * t[:, 2])
+
+
+def _aggregate_order(mesh, wm, npa):
+    """Nodes sorted by coordinate bin (ties by index)."""
+    return np.argsort(_bins(mesh, wm, npa), kind="stable")
 
 
 @pytest.mark.parametrize("spec", MESHES)
@@ -132,3 +136,41 @@ def test_rotation_must_be_proper(gspm_lib):
     c, s_ = np.cos(0.3), np.sin(0.3)
     mat["R"] = [c, -s_, 0.0, s_, c, 0.0, 0.0, 0.0, 1.0]
     gspm_lib.Context(mesh, mat, 1e-12, 0.5, host_only=True).close()
+
+
+@pytest.mark.parametrize("ordering", ["aggregate", "none"])
+def test_host_coarse_operators_and_inverses(gspm_lib, ordering):
+    """Host-only contexts build the two-level preconditioner's coarse space: the aggregates are
+    the non-empty coordinate bins in bin order, the coarse operators are the Galerkin products
+    P^T K P of the oracle's matrices (same sums, other order), and the kept FP64 inverses invert
+    those products plus rho = trace / n_c / n_agg on each component's constants."""
+    import scipy.sparse as sp
+    from oracle.gspm import System
+    spec = MESHES[1]
+    mesh = synth.kuhn_box(spec["cells"], spec["box"], jitter=spec["jitter"], seed=spec["seed"],
+                          defects=spec["defects"])
+    npa = 16
+    g = gspm_lib
+    ctx = g.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, ordering=ordering,
+                    host_only=True, coarse_nodes=npa)
+    wm = WrappedMesh.from_synth(mesh)
+    na = ctx.info()["n_aggregates"]
+    agg = ctx.export(g.EXPORT_AGGREGATES)
+    _, expect = np.unique(_bins(mesh, wm, npa), return_inverse=True)
+    assert na > 8 and np.array_equal(agg, expect)
+    s = System(wm, synth.fe_like_material(), 1e-12, 0.5)
+    P = sp.csr_matrix((np.ones(wm.n), (np.arange(wm.n), agg)), shape=(wm.n, na))
+    P3 = sp.kron(P, sp.identity(3)).tocsr()
+    for Kraw, Pm, comps, ek, ei in ((s.K_ms_raw, P, 1, g.EXPORT_COARSE_K_MS, g.EXPORT_COARSE_INV_MS),
+                                    (s.K_mech_raw, P3, 3, g.EXPORT_COARSE_K_MECH,
+                                     g.EXPORT_COARSE_INV_MECH)):
+        nc = comps * na
+        Kc = (Pm.T @ Kraw @ Pm).toarray()
+        got = ctx.export(ek).reshape(nc, nc)
+        assert np.abs(got - Kc).max() < 1e-12 * np.abs(Kc).max()
+        rho = np.trace(Kc) / nc / na
+        same = (np.arange(nc)[:, None] % comps) == (np.arange(nc)[None, :] % comps)
+        A = Kc + rho * same
+        inv = ctx.export(ei).reshape(nc, nc)
+        assert np.abs(inv - inv.T).max() < 1e-12 * np.abs(inv).max()
+        assert np.abs(A @ inv - np.eye(nc)).max() < 1e-10
