@@ -670,17 +670,35 @@ static inline double dot4(const double* a, const double* b, int64_t len) {
 }
 
 // acc[x][y] += sum_t a[x][t] b[y][t] for t < len: a 4 x 4 register tile of dot products of
-// rows, each loaded value serving four products
+// rows, each loaded value serving four products, two consecutive t per vector lane pair (GCC
+// vector extension: SSE2 or NEON, the same pairwise order on either), odd tail in order
+typedef double Dbl2 __attribute__((vector_size(16)));
+static inline Dbl2 load2(const double* p) {
+  Dbl2 v;
+  std::memcpy(&v, p, sizeof(v));
+  return v;
+}
 static inline void tile4x4(const double* const a[4], const double* const b[4], int64_t len,
                            double (&acc)[4][4]) {
-  for (int64_t t = 0; t < len; ++t) {
-    const double a0 = a[0][t], a1 = a[1][t], a2 = a[2][t], a3 = a[3][t];
-    const double b0 = b[0][t], b1 = b[1][t], b2 = b[2][t], b3 = b[3][t];
-    acc[0][0] += a0 * b0; acc[0][1] += a0 * b1; acc[0][2] += a0 * b2; acc[0][3] += a0 * b3;
-    acc[1][0] += a1 * b0; acc[1][1] += a1 * b1; acc[1][2] += a1 * b2; acc[1][3] += a1 * b3;
-    acc[2][0] += a2 * b0; acc[2][1] += a2 * b1; acc[2][2] += a2 * b2; acc[2][3] += a2 * b3;
-    acc[3][0] += a3 * b0; acc[3][1] += a3 * b1; acc[3][2] += a3 * b2; acc[3][3] += a3 * b3;
+  Dbl2 s[4][4];
+  for (int x = 0; x < 4; ++x)
+    for (int y = 0; y < 4; ++y) s[x][y] = Dbl2{0.0, 0.0};
+  int64_t t = 0;
+  for (; t + 2 <= len; t += 2) {
+    const Dbl2 a0 = load2(a[0] + t), a1 = load2(a[1] + t), a2 = load2(a[2] + t),
+               a3 = load2(a[3] + t);
+    const Dbl2 b0 = load2(b[0] + t), b1 = load2(b[1] + t), b2 = load2(b[2] + t),
+               b3 = load2(b[3] + t);
+    s[0][0] += a0 * b0; s[0][1] += a0 * b1; s[0][2] += a0 * b2; s[0][3] += a0 * b3;
+    s[1][0] += a1 * b0; s[1][1] += a1 * b1; s[1][2] += a1 * b2; s[1][3] += a1 * b3;
+    s[2][0] += a2 * b0; s[2][1] += a2 * b1; s[2][2] += a2 * b2; s[2][3] += a2 * b3;
+    s[3][0] += a3 * b0; s[3][1] += a3 * b1; s[3][2] += a3 * b2; s[3][3] += a3 * b3;
   }
+  for (int x = 0; x < 4; ++x)
+    for (int y = 0; y < 4; ++y) acc[x][y] += s[x][y][0] + s[x][y][1];
+  for (; t < len; ++t)
+    for (int x = 0; x < 4; ++x)
+      for (int y = 0; y < 4; ++y) acc[x][y] += a[x][t] * b[y][t];
 }
 
 // Blocked right-looking Cholesky of the SPD matrix A (n x n, row-major, lower factor in place):
