@@ -1427,7 +1427,7 @@ class Engine final : public EngineBase {
 
   int init_segments() {
     const int S = nseg_;
-    int32_t *d_sos, *d_si0, *d_sni;
+    int32_t* d_sos;
     int64_t *d_r0, *d_nr, *d_pin;
     unsigned* d_cnt;
     ST(mem_.alloc(&d_sos, nslices_));
