@@ -4,9 +4,12 @@ One "step" = one full GSPM time step (volume averages, both RHS assemblies, magn
 mechanical CG, strain/field recovery, seven GSPM CG solves, projection) through the C ABI.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --contract [--contract-cells 128,128,32] [--contract-steps 1000]
 
 Prints one JSON line (rank 0).  N > 1 (torchrun) runs independent replicas of the single-mesh
-step, one per GPU (the single-mesh path has no independent units to shard).
+step, one per GPU (the single-mesh path has no independent units to shard).  --contract runs the
+mixed-precision contract instead: the sphere-inclusion workload stepped in mixed precision and in
+FP64 from the same state, with the angle and field errors between the two trajectories.
 """
 from __future__ import annotations
 
@@ -18,7 +21,6 @@ import re
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -29,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "GSPM steps/s at 3M nodes, mixed+learned vs plain FP64 on 1 GB300; % HBM peak"
 WEIGHTS = os.path.join(ROOT, "paper_2510_09812_gb300", "weights", "warmstart_mpnn.npy")
 FALLBACK_HBM = 6800.0
+FULL_CELLS = (228, 228, 57)
+ORACLE_CELLS = (40, 40, 10)
+X0_NAMES = ("prev", "zero", "extrapolate", "learned")
 
 
 def _peaks():
@@ -112,34 +117,37 @@ def _kernel_src_hash():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on this kernel
-    source; else None."""
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` at the 3M-node mesh from a committed ncu summary taken on
+    the current kernel source (a line `dram_bytes_per_launch_full[<kernel>]: <bytes>` next to
+    `kernels_sha256: <hash>`), else None."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
+    pat = re.compile(r"dram_bytes_per_launch_full\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)")
     for fn in sorted(os.listdir(d)):
-        if not fn.startswith(kernel) or workload not in fn:
-            continue
         txt = open(os.path.join(d, fn)).read()
         h = re.search(r"kernels_sha256:\s*([0-9a-f]+)", txt)
-        b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+        b = pat.search(txt)
         if h and b and h.group(1) == _kernel_src_hash():
             return float(b.group(1))
     return None
 
 
-def cpu_oracle_sample(wall_budget=25.0, steps=None, warmup=1):
-    """Time the CPU oracle (as it stands) on a bounded sample of the workload: a mesh built
-    with the same recipe (h, jitter, void + cuboids generator) but 40x40x10 cubes.  Returns
-    (steps/s scaled to the full mesh by node count, seconds per sample step, description)."""
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline
+# ------------------------------------------------------------------------------------------
+
+def cpu_oracle_sample(steps=None, warmup=1, wall_budget=20.0, cells=ORACLE_CELLS):
+    """Time the CPU oracle (as it stands) on the benchmark recipe at `cells` cubes (same h,
+    jitter and void + cuboids generator): whole steps, then a fixed number of its own CG
+    iterations on each system to separate the iteration cost from the rest of the step."""
     from paper_2510_09812_gb300 import synth
     from oracle.gspm import System
     from oracle.mesh import WrappedMesh
+    from oracle.solvers import cg
     h = 1024.0 / 228.0
-    cells = (40, 40, 10)
     cfg = synth.void_cuboids_box(n_cells=cells, box=tuple(v * h for v in cells))
-    full_n = 228 * 228 * 57
     wm = WrappedMesh.from_synth(cfg["mesh"])
     s = System(wm, cfg["material"], cfg["dt"], cfg["alpha"])
     m = np.array(cfg["m0"])
@@ -147,34 +155,157 @@ def cpu_oracle_sample(wall_budget=25.0, steps=None, warmup=1):
     U, u = np.zeros(wm.n), np.zeros((wm.n, 3))
     for _ in range(warmup):
         m, U, u, _ = s.step(m, U, u, cfg["H"])
+    it = {"ms": 0, "mech": 0, "gs": 0}
     t0 = time.perf_counter()
     k = 0
     while True:
-        m, U, u, _ = s.step(m, U, u, cfg["H"])
+        m, U, u, info = s.step(m, U, u, cfg["H"])
+        it["ms"] += info["it_ms"]
+        it["mech"] += info["it_mech"]
+        it["gs"] += int(np.sum(info["it_gs"]))
         k += 1
         el = time.perf_counter() - t0
         if (steps is not None and k >= steps) or (steps is None and (el > wall_budget or k >= 20)):
             break
     per = el / k
-    desc = (f"oracle GSPM steps on the same recipe at 40x40x10 cubes ({wm.n} nodes, "
-            f"{cfg['mesh'].n_tets} tets), {k} timed after {warmup} warm-up; per-step time "
-            f"scaled by node count {wm.n}/{full_n} to the 3M-node mesh")
-    return (1.0 / per) * (wm.n / full_n), per, desc, k
+    # seconds per CG iteration of each system (the oracle's CG with a zero tolerance runs the
+    # requested number of iterations)
+    rng = np.random.default_rng(0)
+    t_it = {}
+    for name, A in (("ms", s.K_ms), ("mech", s.K_mech), ("gs", s.A_eps)):
+        b = rng.standard_normal(A.shape[0])
+        best = float("inf")
+        for _ in range(3):
+            t1 = time.perf_counter()
+            cg(A, b, np.zeros_like(b), 0.0, 20)
+            best = min(best, (time.perf_counter() - t1) / 20)
+        t_it[name] = best
+    return {"nodes": int(wm.n), "tets": int(cfg["mesh"].n_tets), "cells": list(cells),
+            "steps": k, "warmup": warmup, "s_per_step": per,
+            "it_per_step": {key: v / k for key, v in it.items()}, "s_per_iteration": t_it}
 
 
-def cpu_oracle_sample_1core(steps=None, warmup=1):
-    """cpu_oracle_sample in a fresh child process with one BLAS / OpenMP thread, so that the
-    sample runs on exactly one core."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def cpu_oracle_child(steps=None, warmup=1, threads=1, cells=ORACLE_CELLS):
+    """cpu_oracle_sample in a fresh child process with `threads` BLAS / OpenMP threads."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads), CUDA_VISIBLE_DEVICES="")
     code = ("import json, sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.cpu_oracle_sample(steps=%r, warmup=%r)))"
-            % (ROOT, steps, warmup))
-    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, check=True,
-                         capture_output=True, text=True).stdout
-    rate, per, desc, k = json.loads(out.strip().splitlines()[-1])
-    return rate, per, desc, k
+            "print(json.dumps(bench.cpu_oracle_sample(steps=%r, warmup=%r, cells=%r)))"
+            % (ROOT, steps, warmup, tuple(cells)))
+    return subprocess.Popen([sys.executable, "-c", code], env=env, cwd=ROOT,
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
 
+
+def _child_result(p):
+    out, err = p.communicate()
+    if p.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + err[-2000:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def oracle_full_size_model(sample, full_nodes, full_cells, it_full=None):
+    """Oracle seconds per step at the full mesh from a sample: the work outside the CG loops
+    scales with the nodes; a CG iteration costs the sample's measured time per iteration scaled
+    by the nodes; the iteration counts of the plain CG on K^ms and K^mech grow with the mesh's
+    linear size in cells (sqrt of the condition number of a Laplacian-type operator), those of
+    the GSPM solves (M + c eps K) do not.  it_full: measured full-size counts of the same
+    algorithm (pinned systems, plain CG), used instead of the growth law when given."""
+    scale = full_nodes / sample["nodes"]
+    ips, spi = sample["it_per_step"], sample["s_per_iteration"]
+    t_cg = sum(ips[k] * spi[k] for k in ("ms", "mech", "gs"))
+    other = max(sample["s_per_step"] - t_cg, 0.0)
+    growth = max(full_cells) / max(sample["cells"])
+    its = dict(it_full) if it_full else {"ms": ips["ms"] * growth, "mech": ips["mech"] * growth,
+                                         "gs": ips["gs"]}
+    t = other * scale + sum(its[k] * spi[k] * scale for k in ("ms", "mech", "gs"))
+    return t, its, ("measured at full size (same algorithm on the GPU)" if it_full else
+                    f"sample counts x {growth:.2f} (linear mesh size) for K^ms and K^mech")
+
+
+def cpu_baseline_block(sample, full_nodes, it_full=None, cores=1, kind="oracle"):
+    t, its, how = oracle_full_size_model(sample, full_nodes, FULL_CELLS, it_full)
+    return {"value": 1.0 / t, "unit": "steps/s", "cores": cores, "kind": kind,
+            "sample": (f"oracle (NumPy/SciPy) GSPM steps on the same recipe at "
+                       f"{'x'.join(map(str, sample['cells']))} cubes ({sample['nodes']} nodes), "
+                       f"{sample['steps']} timed after {sample['warmup']} warm-up, plus 3 x 20 CG "
+                       f"iterations per system (best); full-size step time = non-CG time x nodes ratio "
+                       f"+ CG iterations per step ({how}) x time per iteration x nodes ratio"),
+            "measured_at_sample": {"nodes": sample["nodes"],
+                                   "steps_per_s": 1.0 / sample["s_per_step"],
+                                   "node_updates_per_s": sample["nodes"] / sample["s_per_step"],
+                                   "cg_iterations_per_step": sample["it_per_step"],
+                                   "s_per_cg_iteration": sample["s_per_iteration"]},
+            "cg_iterations_per_step_full": its}
+
+
+def cpu_all_cores(cells=ORACLE_CELLS, steps=3):
+    """The oracle sample run as independent single-thread replicas, one per host core: the
+    oracle's sparse products run on one thread, so this is the host's whole-CPU throughput of
+    the oracle as it stands (node updates/s summed over the replicas)."""
+    ncores = os.cpu_count() or 1
+    procs = [cpu_oracle_child(steps=steps, warmup=1, threads=1, cells=cells)
+             for _ in range(ncores)]
+    res = [_child_result(p) for p in procs]
+    nu = sum(r["nodes"] / r["s_per_step"] for r in res)
+    return {"cores": ncores, "replicas": ncores, "node_updates_per_s": nu,
+            "steps_per_s_each_mean": float(np.mean([1.0 / r["s_per_step"] for r in res])),
+            "nodes": res[0]["nodes"], "steps": steps}
+
+
+# ------------------------------------------------------------------------------------------
+# helpers on contexts
+# ------------------------------------------------------------------------------------------
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _snapshot(gspm, torch, ctx, fields=None):
+    n = ctx.n
+    fields = fields or (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP, gspm.FIELD_DISP_PREV)
+    snap = {f: torch.empty((n, gspm.FIELD_NCOMP[f]) if gspm.FIELD_NCOMP[f] > 1 else (n,),
+                           dtype=torch.float64, device="cuda") for f in fields}
+    for f, t in snap.items():
+        ctx.get_field(f, t)
+    torch.cuda.synchronize()
+    return snap
+
+
+def _restore(torch, ctx, snap):
+    for f, t in snap.items():
+        ctx.set_field(f, t)
+    torch.cuda.synchronize()
+
+
+def _fields(gspm, ctx):
+    return {name: ctx.get_field(f) for name, f in (("m", gspm.FIELD_M), ("U", gspm.FIELD_U),
+                                                    ("u", gspm.FIELD_DISP), ("E", gspm.FIELD_STRAIN),
+                                                    ("h_d", gspm.FIELD_HD), ("h", gspm.FIELD_H))}
+
+
+def _max_angle(a, b):
+    na, nb = np.linalg.norm(a, axis=1), np.linalg.norm(b, axis=1)
+    ok = (na > 0.5) & (nb > 0.5)
+    c = np.clip((a[ok] * b[ok]).sum(1) / (na[ok] * nb[ok]), -1.0, 1.0)
+    return float(np.arccos(c).max()) if ok.any() else 0.0
+
+
+def field_errors(test, ref):
+    """Max angle between the m fields (rad) and, for every other field, max |test - ref| / max
+    |ref| (U and u are both zero at the pinned node, so they compare directly)."""
+    out = {"m_max_angle_rad": _max_angle(test["m"], ref["m"])}
+    for k in ("U", "u", "E", "h_d", "h"):
+        d = np.abs(np.asarray(test[k]) - np.asarray(ref[k])).max()
+        out[f"{k}_rel_err"] = float(d / max(np.abs(ref[k]).max(), 1e-300))
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+# secondary workloads
+# ------------------------------------------------------------------------------------------
 
 def run_batch(gspm, torch, args, barrier):
     """64 independent meshes of log-uniform size 2k-200k nodes, each with its own inclusion and
@@ -199,20 +330,14 @@ def run_batch(gspm, torch, args, barrier):
     ctx.set_field(gspm.FIELD_M, m_all)
     info = ctx.info()
     ctx.batch_step(2, H, stats=False)
-    n = info["n_unique"]
-    snap = {f: torch.empty((n, gspm.FIELD_NCOMP[f]) if gspm.FIELD_NCOMP[f] > 1 else (n,),
-                           dtype=torch.float64, device="cuda")
-            for f in (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP)}
-    for f, t in snap.items():
-        ctx.get_field(f, t)
-    kb = max(1, min(args.steps, 4))
+    snap = _snapshot(gspm, torch, ctx, (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP))
+    kb = max(1, args.batch_steps)
 
     def timed_batch(graph):
         # the graph is captured by an untimed step; every pass starts from the same state
         ctx.set_graph(graph)
         ctx.batch_step(1, H, stats=False)
-        for f, t in snap.items():
-            ctx.set_field(f, t)
+        _restore(torch, ctx, snap)
         l0 = ctx.launch_count()
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -303,31 +428,107 @@ def run_small(gspm, torch, barrier, steps=200):
     return out
 
 
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
+# ------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ------------------------------------------------------------------------------------------
 
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    per_steps = []
-    rate, per, desc, k = cpu_oracle_sample_1core(steps=args.steps, warmup=args.warmup)
+    # each requested step is one oracle step of the bounded sample (a fixed mesh of the recipe)
+    sample = _child_result(cpu_oracle_child(steps=args.steps, warmup=args.warmup))
+    n_full = FULL_CELLS[0] * FULL_CELLS[1] * FULL_CELLS[2]
+    cpu = cpu_baseline_block(sample, n_full)
+    rate = cpu["value"]
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "void_cuboids_1024x1024x256nm_2963088n", "precision": "f64",
-                       "solver": "CPU oracle (NumPy/SciPy, single thread)"},
-            "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                       "solver": "CPU oracle (NumPy/SciPy, one thread): pinned systems, plain CG"},
+            "cpu_baseline": cpu,
             "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------------------------------
+# mixed-precision contract run (separate invocation)
+# ------------------------------------------------------------------------------------------
+
+def run_contract(args):
+    """The sphere-inclusion workload (512x512x128 nm, 0.5M nodes, dt 5 ps) stepped in mixed
+    precision and in FP64 (same solver form, graph replay) from the same initial state for
+    --contract-steps steps: max angle of m and the relative errors of U, u, E, h~_d and h after
+    the run and at checkpoints, true residuals of the last solves, and both step rates.  Two
+    starts: the workload's own (m = e1 in 200 A/m along e1, a near-equilibrium state) and a
+    seeded random m (relaxation with large motion)."""
+    import torch
+    from paper_2510_09812_gb300 import build
+    from paper_2510_09812_gb300 import gspm, synth
+    build.build()
+    torch.cuda.set_device(0)
+    cells = tuple(int(v) for v in args.contract_cells.split(","))
+    box = tuple(4.0 * c for c in cells)
+    cfg = synth.sphere_inclusion_box(n_cells=cells, box=box, radius=60.0 * cells[2] / 32)
+    K = args.contract_steps
+    checkpoints = sorted({c for c in (1, 10, 100, K // 2, K) if 0 < c <= K})
+    starts = {"uniform_e1_200Apm": (cfg["m0"], cfg["H"]),
+              "random_m_zero_field": (synth.random_unit_m(cfg["mesh"].n_unique, 11), np.zeros(3))}
+    out = {"workload": cfg["name"], "nodes": cfg["mesh"].n_unique, "dt_s": cfg["dt"],
+           "alpha": cfg["alpha"], "steps": K, "rtol": 1e-7, "starts": {}}
+    ctxs = {}
+    for prec in ("mixed", "f64"):
+        t0 = time.perf_counter()
+        ctxs[prec] = gspm.Context(cfg["mesh"], cfg["material"], cfg["dt"], cfg["alpha"],
+                                  precision=prec, rtol_gs=1e-7, rtol_ms=1e-7, rtol_mech=1e-7,
+                                  graph=True)
+        ctxs[prec].set_true_residual(True)
+        out[f"load_s_{prec}"] = round(time.perf_counter() - t0, 1)
+    for name, (m0, H) in starts.items():
+        res = {"checkpoints": {}}
+        fields = {}
+        for prec, ctx in ctxs.items():
+            ctx.set_field(gspm.FIELD_M, m0)
+            ctx.set_field(gspm.FIELD_U, np.zeros(ctx.n))
+            ctx.set_field(gspm.FIELD_DISP, np.zeros((ctx.n, 3)))
+            ctx.set_field(gspm.FIELD_DISP_PREV, np.zeros((ctx.n, 3)))
+            done, ms, its = 0, 0.0, {"it_ms": 0, "it_mech": 0, "it_gs": 0}
+            fields[prec] = {}
+            for c in checkpoints:
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                st = ctx.step(c - done, H)
+                ev1.record()
+                torch.cuda.synchronize()
+                ms += ev0.elapsed_time(ev1)
+                for key in its:
+                    its[key] += st[key]
+                done = c
+                fields[prec][c] = _fields(gspm, ctx)
+                if c == checkpoints[-1]:
+                    res[prec] = {"steps_per_s": K / (ms / 1000.0),
+                                 "cg_iterations_per_step": {k: v / K for k, v in its.items()},
+                                 "last_step": {"res_ms": st["res_ms_last"],
+                                               "res_mech": st["res_mech_last"],
+                                               "true_res_ms": st["true_res_ms_last"],
+                                               "true_res_mech": st["true_res_mech_last"],
+                                               "dm": st["dm_last"], "noconv": st["noconv"]}}
+        for c in checkpoints:
+            res["checkpoints"][str(c)] = field_errors(fields["mixed"][c], fields["f64"][c])
+        res["final"] = res["checkpoints"][str(K)]
+        res["within_1e-4_rad"] = res["final"]["m_max_angle_rad"] < 1e-4
+        out["starts"][name] = res
+    for c in ctxs.values():
+        c.close()
+    print(json.dumps({"contract": out}), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# the headline
+# ------------------------------------------------------------------------------------------
 
 def run_ours(args):
     import torch
@@ -339,6 +540,7 @@ def run_ours(args):
     from paper_2510_09812_gb300 import build
     build.build()
     from paper_2510_09812_gb300 import gspm
+    from paper_2510_09812_gb300.shard import max_over_ranks
 
     cfg = _workload(args)
     mesh = cfg["mesh"]
@@ -351,14 +553,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    weights = None
-    if os.path.exists(WEIGHTS):
-        weights = np.load(WEIGHTS)
-    x0_names = {"prev": gspm.X0_PREV, "zero": gspm.X0_ZERO, "extrapolate": gspm.X0_EXTRAPOLATE,
-                "learned": gspm.X0_LEARNED}
-    # default: the previous step's displacement (the paper's warm start); with the CG projected
-    # off the constants the three classical guesses need about the same iterations on this
-    # workload (248 / 247 / 254 per step for previous / extrapolated / zero)
+    weights = np.load(WEIGHTS) if os.path.exists(WEIGHTS) else None
+    x0_code = {"prev": gspm.X0_PREV, "zero": gspm.X0_ZERO, "extrapolate": gspm.X0_EXTRAPOLATE,
+               "learned": gspm.X0_LEARNED}
     x0 = args.x0 if args.x0 != "auto" else ("learned" if weights is not None else "prev")
     if x0 == "learned" and weights is None:
         raise SystemExit(f"--x0 learned needs trained weights at {WEIGHTS}")
@@ -371,169 +568,241 @@ def run_ours(args):
         ctx.set_field(gspm.FIELD_M, cfg["m0"])
         if weights is not None:
             ctx.mpnn_set_params(weights)
-        ctx.set_x0_mode(x0_names[mode])
+        ctx.set_x0_mode(x0_code[mode])
         return ctx, time.perf_counter() - t0
 
-    def timed_steps(ctx, k, profile=("spmv_mech",)):
-        ctx.profile_enable(profile)
-        st_tot = {"it_mech": 0, "it_ms": 0, "it_gs": 0}
+    def timed(ctx, k, profile=(), clocks=False):
+        """k steps in one gspm_step call between CUDA events (with per-class events when
+        `profile` names kernel classes)."""
+        if profile:
+            ctx.profile_enable(profile)
         l0 = ctx.launch_count()
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local, enabled=not args.no_clocks) as clk:
+        with ClockSampler(local, enabled=clocks and not args.no_clocks) as clk:
             ev0.record()
-            for _ in range(k):
-                st = ctx.step(1, H)
-                for key in st_tot:
-                    st_tot[key] += st[key]
+            st = ctx.step(k, H)
             ev1.record()
             barrier()
         ms = ev0.elapsed_time(ev1)
         launches = ctx.launch_count() - l0
         prof = {c: ctx.profile_read(c) for c in profile}
-        ctx.profile_enable(())
-        return ms, st_tot, launches, prof, clk.summary()
+        if profile:
+            ctx.profile_enable(())
+        return ms, st, launches, prof, clk.summary()
+
+    def its(st, k):
+        return {"it_ms": st["it_ms"] / k, "it_mech": st["it_mech"] / k, "it_gs": st["it_gs"] / k}
 
     precision = args.precision
     ctx, t_load = make(precision, x0, pinned=args.pinned_cg, plain=args.plain_cg)
     info = ctx.info()
     n = info["n_unique"]
     for _ in range(args.warmup):
-        ctx.step(1, H)
-    # snapshot of the state after warm-up: every measured pass starts from it, so the timed
-    # region, the kernel breakdown and the end-to-end pass do identical work
-    snap = {f: torch.empty((n, gspm.FIELD_NCOMP[f]) if gspm.FIELD_NCOMP[f] > 1 else (n,),
-                           dtype=torch.float64, device="cuda")
-            for f in (gspm.FIELD_M, gspm.FIELD_U, gspm.FIELD_DISP, gspm.FIELD_DISP_PREV)}
-    for f, t in snap.items():
-        ctx.get_field(f, t)
+        ctx.step(1, H, stats=False)
+    # every measured pass starts from the state after warm-up, so all passes do identical work
+    snap = _snapshot(gspm, torch, ctx)
+    K = args.steps
 
-    def restore():
-        for f, t in snap.items():
-            ctx.set_field(f, t)
-        torch.cuda.synchronize()
-
-    ms, st, launches, prof, clocks = timed_steps(ctx, args.steps)
-    from paper_2510_09812_gb300.shard import max_over_ranks
+    # headline: graph replay (each step one CUDA graph launch, CG loops as device-side WHILE
+    # nodes), K steps in one call; the graph is captured by an untimed step first
+    if not args.direct:
+        ctx.set_graph(True)
+        ctx.step(1, H, stats=False)
+    _restore(torch, ctx, snap)
+    ms, st, launches, _, clocks = timed(ctx, K, clocks=True)
     t_max = max_over_ranks(ms, torch.device("cuda", local))
-    value = ws * args.steps / (t_max / 1000.0)
+    value = ws * K / (t_max / 1000.0)
+    headline_mode = "direct launches" if args.direct else "CUDA graph replay"
 
-    # roofline of the dominant kernel: 3x3-block SELL SpMV of the mechanical CG
+    # the same steps with direct launches (host-sequenced CG loops)
+    other_mode = None
+    if not args.direct:
+        ctx.set_graph(False)
+        _restore(torch, ctx, snap)
+        ms_d, st_d, l_d, _, _ = timed(ctx, K)
+        other_mode = {"mode": "direct launches", "value": ws * K / (ms_d / 1000.0),
+                      "ms_per_step": ms_d / K, "gpu_launches": l_d,
+                      "same_iterations": st_d["it_mech"] == st["it_mech"]
+                      and st_d["it_ms"] == st["it_ms"] and st_d["it_gs"] == st["it_gs"]}
+    ctx.set_graph(False)
+
+    # kernel pass (separate, from the same state): CUDA events around every launch of the
+    # mechanical SpMV and of the four assembly / recovery row kernels
     w = 4 if precision == "mixed" else 8
-    bytes_per_iter = (info["sell_entries"] * (9 * w + 4) + ((n + 31) // 32) * 12 + n * 3 * w * 2)
-    t_spmv, n_spmv = prof["spmv_mech"]
-    achieved = bytes_per_iter * st["it_mech"] / (t_spmv / 1000.0) / 1e9 if t_spmv > 0 else None
-    wl = cfg["name"]
-    traffic = _traffic("spmv_mech", "void_cuboids_3M") if args.cells is None else None
+    E, S = info["sell_entries"], (n + 31) // 32
+    kern = {  # algorithmic bytes per launch: values + columns + slice headers + vectors
+        "spmv_mech": ("k_cg_spmv<B=9> (3x3-block SELL SpMV + p.q)", E * (9 * w + 4) + S * 12 + 6 * n * w),
+        "rhs_ms": ("k_fdiv (b^ms = F^ms m)", E * (3 * w + 4) + S * 12 + 3 * n * w + n * w),
+        "grad_ms": ("k_fgrad (h~_d = -grad U)", E * (3 * w + 4) + S * 12 + n * w + 8 * n + 3 * n * w),
+        "rhs_mech": ("k_gdiv (b^mech = F^mech E0)", E * (3 * w + 4) + S * 12 + 6 * n * w + 3 * n * w),
+        "strain": ("k_fstrain (E = E_bar + sym grad u)", E * (3 * w + 4) + S * 12 + 3 * n * w + 8 * n + 6 * n * w),
+    }
+    _restore(torch, ctx, snap)
+    kp = max(1, min(K, 5))
+    _, st_k, _, prof, _ = timed(ctx, kp, tuple(kern))
+    rooflines = {}
+    for c, (desc, nbytes) in kern.items():
+        t_ms, cnt = prof[c]
+        gbs = nbytes * cnt / (t_ms / 1000.0) / 1e9 if t_ms > 0 else None
+        rooflines[c] = {"kernel": desc, "bytes_per_launch": int(nbytes), "launches": cnt,
+                        "us_per_launch": 1000.0 * t_ms / cnt if cnt else None,
+                        "achieved_gbs": gbs, "frac": gbs / peak if gbs else None,
+                        "traffic": _traffic(c) if args.cells is None else None}
+    sp = rooflines["spmv_mech"]
+    roofline = {"bound": "hbm", "kernel": sp["kernel"], "achieved": sp["achieved_gbs"],
+                "peak": peak, "unit": "GB/s", "frac": sp["frac"], "traffic": sp["traffic"],
+                "peak_kind": peak_kind, "bytes_per_launch": sp["bytes_per_launch"],
+                "launches_timed": sp["launches"], "timed_in": f"separate pass of {kp} steps"}
 
-    # per-class breakdown (separate, untimed pass from the same state)
-    classes = ["spmv_mech", "spmv_gs", "spmv_ms", "cg_vec", "cg_init", "rowops", "pointwise"]
-    kb = max(1, min(2, args.steps))
-    restore()
-    bms, bst, _, bprof, _ = timed_steps(ctx, kb, classes)
+    # per-class breakdown (separate pass from the same state)
+    classes = ["spmv_mech", "spmv_gs", "spmv_ms", "cg_vec", "cg_init", "rhs_ms", "grad_ms",
+               "rhs_mech", "strain", "pointwise", "learned"]
+    kb = max(1, min(2, K))
+    _restore(torch, ctx, snap)
+    bms, _, _, bprof, _ = timed(ctx, kb, classes)
     breakdown = {c: round(bprof[c][0] / kb, 3) for c in classes}
     breakdown["total_ms_per_step"] = round(bms / kb, 3)
 
     # end to end through the C ABI with pinned host buffers, from the same state: every step
-    # copies m host->device, steps, and copies m device->host (the next step's input)
-    restore()
+    # copies m host->device, steps (graph replay), and copies m device->host
+    if not args.direct:
+        ctx.set_graph(True)
+    _restore(torch, ctx, snap)
     mh = snap[gspm.FIELD_M].cpu().pin_memory()
     mo = torch.empty_like(mh).pin_memory()
-    ke = args.steps
     barrier()
     t0 = time.perf_counter()
-    for _ in range(ke):
+    for _ in range(K):
         ctx.set_field(gspm.FIELD_M, mh)
         ctx.step(1, H, stats=False)
         ctx.get_field(gspm.FIELD_M, mo)
         mh, mo = mo, mh
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": ws * ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": n * 3 * 8,
+    e2e = {"value": ws * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": n * 3 * 8,
            "d2h_bytes_per_step": n * 3 * 8}
+    ctx.set_graph(False)
 
-    # mechanical-CG initial guesses compared over the same steps from the same state
+    # precision: the FP64 path in the same solver form (graph replay), timed from the same
+    # state, then both precisions stepped from that state with true residuals on: max angle of m
+    # and the relative errors of every exported field after the same steps
+    precision_cmp, f64_form = None, None
+    if precision == "mixed" and not args.skip_plain:
+        ctx64, t_load64 = make("f64", x0, pinned=args.pinned_cg, plain=args.plain_cg)
+        ctx64.set_graph(True)
+        ctx64.step(1, H, stats=False)
+        _restore(torch, ctx64, snap)
+        k64 = max(1, min(K, 10))
+        ms64, st64, _, _, _ = timed(ctx64, k64)
+        f64_form = {"value": k64 / (ms64 / 1000.0), "unit": "steps/s", "steps": k64,
+                    "ms_per_step": ms64 / k64, "cg_iterations_per_step": its(st64, k64),
+                    "mesh_load_s": round(t_load64, 2), "mode": "CUDA graph replay"}
+        kc = max(1, min(K, 10))
+        res = {}
+        for name, c in (("mixed", ctx), ("f64", ctx64)):
+            c.set_graph(False)
+            c.set_true_residual(True)
+            _restore(torch, c, snap)
+            stc = c.step(kc, H)
+            res[name] = (_fields(gspm, c), stc)
+            c.set_true_residual(False)
+        precision_cmp = {"steps": kc, "from": "state after warm-up (FP32-representable)",
+                         "errors_mixed_vs_f64": field_errors(res["mixed"][0], res["f64"][0]),
+                         "residuals_last_step": {
+                             p: {"recursive_ms": s_["res_ms_last"], "true_ms": s_["true_res_ms_last"],
+                                 "recursive_mech": s_["res_mech_last"],
+                                 "true_mech": s_["true_res_mech_last"]}
+                             for p, (_, s_) in res.items()},
+                         "iterations": {p: its(s_, kc) for p, (_, s_) in res.items()}}
+        ctx64.close()
+
+    # mechanical-CG initial guesses compared over the same steps from the same state, with the
+    # mechanical CG run to 1e-8 (the tolerance of the learned warm-start evaluation)
     x0_cmp = {}
+    modes = ["prev", "extrapolate", "zero"] + (["learned"] if weights is not None else [])
     if not args.skip_x0:
-        modes = ["prev", "extrapolate", "zero"] + (["learned"] if weights is not None else [])
-        kx = max(1, min(args.steps, 3))
+        kx = max(1, min(K, 3))
+        ctx.set_rtol(rtol_mech=1e-8)
+        form = {}
         for mode in modes:
-            restore()
-            ctx.set_x0_mode(x0_names[mode])
-            ms_x, st_x, _, _, _ = timed_steps(ctx, kx, ())
-            x0_cmp[mode] = {"it_mech_per_step": st_x["it_mech"] / kx,
-                            "ms_per_step": round(ms_x / kx, 2)}
-        ctx.set_x0_mode(x0_names[x0])
-
-    # graph replay of the same steps from the same state (no per-kernel events inside a graph,
-    # so the roofline above comes from the direct pass)
-    graph = None
-    if not args.skip_graph:
-        restore()
-        ctx.set_graph(True)
-        ctx.step(1, H, stats=False)  # capture
-        restore()
-        ms_g, st_g, l_g, _, _ = timed_steps(ctx, args.steps, ())
-        graph = {"value": ws * args.steps / (ms_g / 1000.0), "unit": "steps/s",
-                 "ms_per_step": ms_g / args.steps, "gpu_launches": l_g,
-                 "same_iterations_as_direct": st_g == st}
-        ctx.set_graph(False)
+            _restore(torch, ctx, snap)
+            ctx.set_x0_mode(x0_code[mode])
+            ms_x, st_x, _, prof_x, _ = timed(ctx, kx, ("learned",))
+            form[mode] = {"it_mech_per_step": st_x["it_mech"] / kx,
+                          "ms_per_step": round(ms_x / kx, 2),
+                          "learned_ms_per_step": round(prof_x["learned"][0] / kx, 3)}
+        x0_cmp["two_level_pcg"] = form
+        ctx.set_rtol(rtol_mech=1e-7)
+        ctx.set_x0_mode(x0_code[x0])
     ctx.close()
 
     small = None
     if not args.skip_graph and ws == 1:
         small = run_small(gspm, torch, barrier)
 
-    # batched uneven meshes (64 meshes, 2k-200k nodes) in one context
     batched = None
     if not args.skip_batch:
         batched = run_batch(gspm, torch, args, barrier)
 
-    # other CG forms in the headline precision, same steps from the same start: the pinned
-    # systems of Sec. 2.5 (plain CG, as the paper) and the singular systems without the
-    # two-level preconditioner
-    forms = {}
+    # the other CG forms in the headline precision, same steps from the same state: the pinned
+    # systems of Sec. 2.5 with plain CG (the paper's form) and the singular systems with plain
+    # CG; then the paper's form in FP64 (the plain FP64 GPU form the metric names)
+    forms, plain = {}, None
+    it_full_oracle_form = None
     if not args.skip_plain:
         for name, kw in (("pinned_plain_cg", dict(pinned=True)),
                          ("singular_plain_cg", dict(plain=True))):
             ctxp, _ = make(precision, x0, **kw)
-            for _ in range(args.warmup):
-                ctxp.step(1, H)
-            kp = max(1, min(args.steps, 3))
-            ms_p, st_p, _, _, _ = timed_steps(ctxp, kp, ())
-            forms[name] = {"steps": kp, "ms_per_step": round(ms_p / kp, 2),
-                           "it_mech_per_step": st_p["it_mech"] / kp,
-                           "it_ms_per_step": st_p["it_ms"] / kp}
+            _restore(torch, ctxp, snap)
+            kp2 = max(1, min(K, 3))
+            ms_p, st_p, _, _, _ = timed(ctxp, kp2)
+            forms[name] = {"steps": kp2, "ms_per_step": round(ms_p / kp2, 2),
+                           "steps_per_s": kp2 / (ms_p / 1000.0),
+                           "cg_iterations_per_step": its(st_p, kp2)}
+            if name == "pinned_plain_cg" and not args.skip_x0:
+                ctxp.set_rtol(rtol_mech=1e-8)
+                form = {}
+                for mode in modes:
+                    _restore(torch, ctxp, snap)
+                    ctxp.set_x0_mode(x0_code[mode])
+                    ms_x, st_x, _, _, _ = timed(ctxp, 1)
+                    form[mode] = {"it_mech_per_step": st_x["it_mech"], "ms_per_step": round(ms_x, 2)}
+                x0_cmp["pinned_plain_cg"] = form
             ctxp.close()
-
-    # plain FP64 GPU form on the same GPU (the comparison the metric names): the paper's
-    # formulation (pinned systems, FP64 throughout, previous solution as initial guess)
-    plain = None
-    if precision != "f64" and not args.skip_plain:
-        ctx64, t_load64 = make("f64", pinned=True)
-        for _ in range(args.warmup):
-            ctx64.step(1, H)
-        k64 = max(1, args.steps // 2)
-        ms64, st64, l64, prof64, _ = timed_steps(ctx64, k64)
-        t64, _ = prof64["spmv_mech"]
-        b64 = (info["sell_entries"] * (9 * 8 + 4) + ((n + 31) // 32) * 12 + n * 3 * 8 * 2)
-        plain = {"value": k64 / (ms64 / 1000.0), "unit": "steps/s", "steps": k64,
-                 "ms_per_step": ms64 / k64, "it_mech_per_step": st64["it_mech"] / k64,
-                 "spmv_mech_gbs": b64 * st64["it_mech"] / (t64 / 1000.0) / 1e9 if t64 else None}
-        ctx64.close()
+        if precision != "f64":
+            ctx64, _ = make("f64", x0, pinned=True)
+            _restore(torch, ctx64, snap)
+            k64 = max(1, min(K, 5))
+            ms64, st64, _, _, _ = timed(ctx64, k64)
+            plain = {"form": "pinned systems (Sec. 2.5), plain CG, FP64 throughout",
+                     "value": k64 / (ms64 / 1000.0), "unit": "steps/s", "steps": k64,
+                     "ms_per_step": ms64 / k64, "cg_iterations_per_step": its(st64, k64)}
+            it_full_oracle_form = {"ms": st64["it_ms"] / k64, "mech": st64["it_mech"] / k64,
+                                   "gs": st64["it_gs"] / k64}
+            ctx64.close()
 
     if rank != 0:
         return
-    cpu = None
+    cpu, cpu_all = None, None
     if ws == 1 and not args.skip_cpu:
-        rate, per, desc, k = cpu_oracle_sample_1core()
-        cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc}
+        sample = _child_result(cpu_oracle_child())
+        cpu = cpu_baseline_block(sample, n)
+        if it_full_oracle_form:
+            t, _, _ = oracle_full_size_model(sample, n, FULL_CELLS, it_full_oracle_form)
+            cpu["steps_per_s_with_full_size_iterations"] = 1.0 / t
+        if not args.skip_cpu_all:
+            cpu_all = cpu_all_cores()
+    headline_form = (f"{precision}, consistent singular systems with two-level PCG"
+                     if not (args.pinned_cg or args.plain_cg) else precision) + \
+                    f", x0 = {x0}" + ("" if x0 == "learned" else
+                                      " (no trained warm-start weights in use)")
     line = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": wl, "nodes": n, "tets": info["n_tets"],
+        "config": {"workload": cfg["name"], "nodes": n, "tets": info["n_tets"],
                    "magnetic_nodes": info["n_magnetic_nodes"], "precision": precision,
                    "ordering": (args.ordering if args.ordering != "auto" else
                                 ("none" if (args.plain_cg or args.pinned_cg) else "aggregate")),
@@ -542,27 +811,28 @@ def run_ours(args):
                    "l2": f"inputs > L2: {info['device_bytes'] / 1e9:.2f} GB resident, "
                          "no flush needed",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "mesh_load_s": round(t_load, 2)},
+                   "mesh_load_s": round(t_load, 2), "mode": headline_mode},
+        "headline_form": headline_form,
         "node_updates_per_s": value * info["n_magnetic_nodes"],
-        "cg_iterations_per_step": {k: v / args.steps for k, v in st.items()},
-        "roofline": {"bound": "hbm", "kernel": "spmv_mech (SELL-32 3x3-block SpMV + p.q)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": traffic,
-                     "peak_kind": peak_kind, "bytes_per_launch": bytes_per_iter,
-                     "launches_timed": n_spmv, "iterations_timed": st["it_mech"]},
+        "cg_iterations_per_step": its(st, K),
+        "roofline": roofline,
+        "assembly_rooflines": {k: v for k, v in rooflines.items() if k != "spmv_mech"},
         "breakdown_ms_per_step": breakdown,
+        "other_launch_mode": other_mode,
         "cg_form": "pinned (Sec. 2.5), plain CG" if args.pinned_cg else
                    ("consistent singular system, plain CG" if args.plain_cg else
                     "consistent singular system, two-level preconditioned CG"),
         "n_aggregates": info["n_aggregates"],
+        "f64_same_form": f64_form,
+        "precision_comparison": precision_cmp,
         "other_cg_forms_same_start": forms,
         "plain_f64": plain,
-        "graph_replay": graph,
         "small_mesh_direct_vs_graph": small,
         "batched": batched,
         "x0": x0,
-        "x0_comparison": x0_cmp,
+        "x0_comparison_rtol_mech_1e-8": x0_cmp,
         "cpu_baseline": cpu,
+        "cpu_all_cores": cpu_all,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -579,6 +849,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--ordering", default="auto", choices=["auto", "none", "rcm", "aggregate"])
     ap.add_argument("--cells", default=None, help="smaller mesh of the same recipe, e.g. 64,64,16")
+    ap.add_argument("--direct", action="store_true",
+                    help="headline with direct launches instead of graph replay")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-graph", action="store_true")
     ap.add_argument("--pinned-cg", action="store_true",
@@ -590,17 +862,25 @@ def main():
     ap.add_argument("--plain-cg", action="store_true",
                     help="no two-level preconditioner for the K^ms / K^mech solves")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-cpu-all", action="store_true")
     ap.add_argument("--skip-x0", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--batch-meshes", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampler (profiling)")
     ap.add_argument("--x0", default="auto", choices=["auto", "prev", "zero", "extrapolate", "learned"],
                     help="initial guess of the mechanical CG (auto: learned when trained weights "
                          "exist, else the previous solution)")
+    ap.add_argument("--contract", action="store_true",
+                    help="run the mixed-precision contract (mixed vs FP64 trajectories) instead")
+    ap.add_argument("--contract-cells", default="128,128,32")
+    ap.add_argument("--contract-steps", type=int, default=1000)
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
+    if args.warmup < 3 and args.impl == "ours" and not args.contract:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.contract:
+        run_contract(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -184,6 +184,11 @@ typedef struct gspm_mesh_info {
   double spmv_ms_block[GSPM_SPMV_SCHEDULES]; /* ms per launch of each schedule (0 = not tuned) */
   double spmv_ms_scalar[GSPM_SPMV_SCHEDULES];
   int64_t n_aggregates;    /* aggregates of the two-level preconditioner, all meshes (0: none) */
+  double coarse_shift_ms, coarse_shift_mech;
+                           /* diagonal shift added to the coarse inverses before their rounding
+                              to the device storage to keep them positive definite (largest over
+                              the meshes; 0 when the rounded inverse is positive definite as it
+                              is, see gspm_coarse_round)                                      */
 } gspm_mesh_info;
 
 typedef struct gspm_step_stats {
@@ -197,6 +202,12 @@ typedef struct gspm_step_stats {
   double dm_last;          /* <|m^{n+1} - m^n|> over magnetic nodes, last step                 */
   double m_bar[3];         /* volume average of m over Omega_c before the last step            */
   int noconv;              /* number of solves that hit max_iter                               */
+  double true_res_ms_last, true_res_mech_last;
+                           /* true relative residuals ||b - K x|| / ||b|| of the last K^ms and
+                              K^mech solves, recomputed from b and the final x after the solve
+                              (rows other than the pinned one, K x accumulated in FP64 against the
+                              operator as stored: FP32 under GSPM_PREC_MIXED); -1 unless enabled
+                              with gspm_set_true_residual                                       */
 } gspm_step_stats;
 
 /* mesh export selectors (host copies of host-side structures; see gspm_mesh_export) */
@@ -214,6 +225,11 @@ typedef struct gspm_step_stats {
                                            on each component's constants (rho = trace / (3 n_agg)
                                            / n_agg); the FP64 inverses before rounding to the
                                            device storage, kept by host-only contexts only     */
+#define GSPM_EXPORT_COARSE_STORED_MS 11   /* double [n_agg^2] the K^ms coarse inverse as the device
+                                           stores it (gspm_coarse_round of the inverse: BF16
+                                           values under GSPM_PREC_MIXED), widened to FP64;
+                                           host-only contexts only                             */
+#define GSPM_EXPORT_COARSE_STORED_MECH 12 /* double [(3 n_agg)^2] the same for K^mech          */
 
 /* fields readable / writable with gspm_get_field / gspm_set_field (unique-node order) */
 #define GSPM_FIELD_M 0       /* [n][3] magnetisation m (non-magnetic nodes forced to 0)       */
@@ -338,6 +354,19 @@ GSPM_API int gspm_apply(struct gspm_ctx* ctx, int op, const double* x, double* y
 /* Number of CUDA kernels the context has launched since creation (host-side counter). */
 GSPM_API int64_t gspm_launch_count(const struct gspm_ctx* ctx);
 
+/* Storage rule of the two-level preconditioner's dense coarse inverse (host code, no GPU): the
+ * symmetric part of A ([n][n] row-major, symmetric positive definite) rounded entry by entry to
+ * bfloat16 (bf16 = 1: round to nearest even of the FP32 value; mixed precision) or kept in FP64
+ * (bf16 = 0), into out [n][n] as FP64 values.  The rounded matrix is accepted only if a Cholesky
+ * factorisation of it (in FP64) succeeds, so the preconditioner stays symmetric positive
+ * definite and the CG's r.z stays positive; otherwise a diagonal shift s is added before
+ * rounding (2^-8 max_i A_ii, doubled until accepted, at most max_i A_ii) and returned in *shift
+ * (0 if none was needed; may be NULL).  mesh_load applies this rule to every coarse inverse.
+ * The paper has no coarse level; this is part of the build's preconditioner (its Sec. 5 names
+ * preconditioning as the next step).  Errors: GSPM_EINVAL (null pointer, n < 1, bf16 not 0/1),
+ * GSPM_EMESH (no shift up to max_i A_ii is accepted: A is not positive definite). */
+GSPM_API int gspm_coarse_round(const double* A, int64_t n, int bf16, double* out, double* shift);
+
 /* ---- allocation-free variant ------------------------------------------------------------ */
 
 /* Volume average without any device allocation, for callers that cannot call cudaMalloc (for
@@ -395,6 +424,20 @@ GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights,
  * GSPM_ECUDA if capture or instantiation fails (the step is then not run). */
 GSPM_API int gspm_set_graph(struct gspm_ctx* ctx, int on);
 
+/* Recompute the true residual ||b - K x|| / ||b|| of every K^ms and K^mech solve after it ends
+ * (on != 0) and report the last ones in gspm_step_stats; off (0) by default.  The CG stopping test
+ * (Sec. 2.5, relative residual 1e-7 in Sec. 3.1) uses the residual that the CG recursion
+ * carries, which drifts from b - K x in finite precision; this call measures the drift.  It adds
+ * one FP64-accumulated product with K per solve.  In graph mode the next step captures the graph
+ * again.  Errors: GSPM_ESTATE for host-only contexts. */
+GSPM_API int gspm_set_true_residual(struct gspm_ctx* ctx, int on);
+
+/* Change the relative residual targets of the GSPM, K^ms and K^mech solves (gspm_options.rtol_*;
+ * Sec. 3.1 uses 1e-7) for the following steps; a value <= 0 keeps that tolerance.  In graph mode
+ * the next step captures the graph again.  Errors: GSPM_EINVAL for a tolerance >= 1,
+ * GSPM_ESTATE for host-only contexts. */
+GSPM_API int gspm_set_rtol(struct gspm_ctx* ctx, double rtol_gs, double rtol_ms, double rtol_mech);
+
 /* Select the mechanical CG's initial guess for gspm_step (GSPM_X0_*); GSPM_X0_LEARNED needs
  * parameters (GSPM_ESTATE otherwise). */
 GSPM_API int gspm_set_x0_mode(struct gspm_ctx* ctx, int mode);
@@ -434,10 +477,13 @@ GSPM_API int gspm_mpnn_train(struct gspm_ctx* ctx, int iterations, double lr, ui
 #define GSPM_KCLASS_SPMV_MS 2    /* scalar SpMV + p.q of the magnetostatic CG (K^ms)          */
 #define GSPM_KCLASS_CG_VEC 3     /* CG vector updates (x, r with r.r; p)                       */
 #define GSPM_KCLASS_CG_INIT 4    /* CG start-up (residual, norms)                              */
-#define GSPM_KCLASS_ROWOPS 5     /* F^ms / G row kernels: RHS assembly, h~_d and strain        */
+#define GSPM_KCLASS_RHS_MS 5     /* demagnetisation right-hand side b^ms = F^ms m (Eq. RHS_b)   */
 #define GSPM_KCLASS_POINTWISE 6  /* E0, h(m), GSPM stages, projection, volume averages         */
 #define GSPM_KCLASS_LEARNED 7    /* learned warm start inference (features, 4 layers, output)  */
-#define GSPM_KCLASS_COUNT 8
+#define GSPM_KCLASS_GRAD_MS 8    /* h~_d = -grad U through F^ms and the lumped mass (Sec. 2.3) */
+#define GSPM_KCLASS_RHS_MECH 9   /* mechanical right-hand side F^mech E0 (Eq. RHS_b)           */
+#define GSPM_KCLASS_STRAIN 10    /* strain E = E_bar + sym grad u (Sec. 2.3)                   */
+#define GSPM_KCLASS_COUNT 11
 
 /* Record CUDA events on the context's stream around every subsequent launch of the classes in
  * class_mask (bit k = class k); 0 stops recording.  Each call clears the accumulated times. */

@@ -59,13 +59,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for s in CUDA_SOURCES:
         o = os.path.join(BUILD, s + ".o")
         objs.append(o)
-        jobs.append([nvcc, *ARCH, "-lineinfo", *common, "-Xcompiler", "-fPIC,-fopenmp",
+        jobs.append([nvcc, *ARCH, "-lineinfo", *common,
+                     "-Xcompiler", "-fPIC,-fopenmp,-ffp-contract=off",
                      "-Xptxas", "-warn-spills", "-c", os.path.join(CSRC, s), "-o", o])
     for s in CXX_SOURCES:
         o = os.path.join(BUILD, s + ".o")
         objs.append(o)
+        # no FMA contraction: the host's dense coarse factorisation and inverse then round alike
+        # on x86-64 and aarch64 (GCC contracts a * b + c by default on aarch64 only)
         jobs.append(["g++", *common, f"-I{_cuda_home(nvcc)}/include", "-fPIC", "-fopenmp",
-                     "-Wall", "-c", os.path.join(CSRC, s), "-o", o])
+                     "-ffp-contract=off", "-Wall", "-c", os.path.join(CSRC, s), "-o", o])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
              for j in jobs]
     failed = []

@@ -121,6 +121,8 @@ class EngineBase {
   virtual int profile_read(int cls, double* ms, int64_t* launches) = 0;
   virtual int set_x0_mode(int mode) = 0;
   virtual int set_graph(int on) = 0;
+  virtual int set_true_residual(int on) = 0;
+  virtual int set_rtol(double gs, double ms, double mech) = 0;
   virtual int mpnn_params(float* out, const float* in, int64_t count) = 0;
   virtual int mpnn_predict(const double* m, const double* up, const double* up2, double* out,
                            int what, int where) = 0;
@@ -203,10 +205,16 @@ class Engine final : public EngineBase {
       ST(upload(&dgs_eps_, de));
       ST(upload(&dgs_aeps_, da));
     }
-    ST(mem_.alloc(&invML_, n));
-    ST(mem_.alloc(&w_, n));
-    ST(mem_.alloc(&mag_, n));
-    ST(mem_.alloc(&perm_, n));
+    // per-row arrays are padded to whole slices (ld rows; zero, or -1 for perm, on the padding)
+    // so that every kernel may address the rows of its last slice
+    ST(mem_.alloc(&invML_, ld));
+    ST(mem_.alloc(&w_, ld));
+    ST(mem_.alloc(&mag_, ld));
+    ST(mem_.alloc(&perm_, ld));
+    CK(cudaMemset(invML_, 0, ld * sizeof(double)));
+    CK(cudaMemset(w_, 0, ld * sizeof(double)));
+    CK(cudaMemset(mag_, 0, ld));
+    CK(cudaMemset(perm_, 0xff, ld * sizeof(int64_t)));
     CK(cudaMemcpy(invML_, ops.invML.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(w_, ops.w.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(mag_, ops.mag.data(), n, cudaMemcpyHostToDevice));
@@ -218,13 +226,25 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&hd_, 3 * ld));
     ST(mem_.alloc(&E_, 6 * ld));
     ST(mem_.alloc(&E0_, 6 * ld));
-    ST(mem_.alloc(&sig0_, 6 * n));
+    ST(mem_.alloc(&sig0_, 6 * ld));
     ST(mem_.alloc(&U_, ld));
-    ST(mem_.alloc(&u_, 3 * n));
-    ST(mem_.alloc(&u2_, 3 * n));
-    ST(mem_.alloc(&utmp_, 3 * n));
-    ST(mem_.alloc(&uin_, 3 * n));
-    ST(mem_.alloc(&uin2_, 3 * n));
+    ST(mem_.alloc(&u_, 3 * ld));
+    ST(mem_.alloc(&u2_, 3 * ld));
+    if (std::is_same<T, float>::value) {
+      // low parts of the refined K^ms / K^mech solutions and the correction solves' iterate
+      ST(mem_.alloc(&Ulo_, ld));
+      ST(mem_.alloc(&ulo_, 3 * ld));
+      ST(mem_.alloc(&dx_, 3 * ld));
+      CK(cudaMemset(Ulo_, 0, ld * sizeof(T)));
+      CK(cudaMemset(ulo_, 0, 3 * ld * sizeof(T)));
+    }
+    ST(mem_.alloc(&utmp_, 3 * ld));
+    ST(mem_.alloc(&uin_, 3 * ld));
+    ST(mem_.alloc(&uin2_, 3 * ld));
+    CK(cudaMemset(sig0_, 0, 6 * ld * sizeof(T)));
+    CK(cudaMemset(utmp_, 0, 3 * ld * sizeof(T)));
+    CK(cudaMemset(uin_, 0, 3 * ld * sizeof(T)));
+    CK(cudaMemset(uin2_, 0, 3 * ld * sizeof(T)));
     {
       std::vector<float> a(ops.Agg.begin(), ops.Agg.end()), at(ops.AggT.begin(), ops.AggT.end());
       ST(mem_.alloc(&agg_, (int64_t)a.size()));
@@ -243,6 +263,8 @@ class Engine final : public EngineBase {
     ST(mem_.alloc(&tout_, 3 * ld));
     ST(mem_.alloc(&cg_, (int64_t)kSolveSlots * nseg_));
     ST(mem_.alloc(&proj_, 6 * (int64_t)nseg_));
+    ST(mem_.alloc(&tres_, 4 * (int64_t)nseg_));
+    CK(cudaMemset(tres_, 0, 4 * nseg_ * sizeof(double)));
     ST(mem_.alloc(&bad_, (int64_t)nseg_));
     CK(cudaMemset(bad_, 0, nseg_ * sizeof(int)));
     CK(cudaMallocHost(&host_bad_, nseg_ * sizeof(int)));
@@ -265,8 +287,8 @@ class Engine final : public EngineBase {
     CK(cudaMemset(hd_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(E_, 0, 6 * ld * sizeof(T)));
     CK(cudaMemset(U_, 0, ld * sizeof(T)));
-    CK(cudaMemset(u_, 0, 3 * n * sizeof(T)));
-    CK(cudaMemset(u2_, 0, 3 * n * sizeof(T)));
+    CK(cudaMemset(u_, 0, 3 * ld * sizeof(T)));
+    CK(cudaMemset(u2_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(x_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(r_, 0, 3 * ld * sizeof(T)));
     CK(cudaMemset(b_, 0, 3 * ld * sizeof(T)));
@@ -301,16 +323,16 @@ class Engine final : public EngineBase {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    auto time_variant = [&](int B, const T* val, int var, float* ms) -> int {
-      CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var));
+    auto time_variant = [&](int B, const T* val, int var, float* ms, int diff = 1) -> int {
+      CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var, diff));
       CK(cudaEventRecord(e0, L_.stream));
-      for (int k = 0; k < 5; ++k) CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var));
+      for (int k = 0; k < 5; ++k) CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var, diff));
       CK(cudaEventRecord(e1, L_.stream));
       CK(cudaEventSynchronize(e1));
       CK(cudaEventElapsedTime(ms, e0, e1));
       return GSPM_OK;
     };
-    float best_b = 1e30f, best_s = 1e30f;
+    float best_b = 1e30f, best_s = 1e30f, best_g = 1e30f;
     for (int v = 0; v < kSpmvVariants; ++v) {
       float t = 0.f;
       ST(time_variant(9, Kmech_, v, &t));
@@ -319,6 +341,9 @@ class Engine final : public EngineBase {
       ST(time_variant(1, Kms_, v, &t));
       tune_ms_scalar_[v] = t / 5.f;
       if (t < best_s) { best_s = t; var_scalar_ = v; }
+      // the GSPM operators are not in difference form: their own schedule
+      ST(time_variant(1, Aeps_, v, &t, 0));
+      if (t < best_g) { best_g = t; var_gs_ = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -427,10 +452,12 @@ class Engine final : public EngineBase {
     if (st) {
       CK(cudaMemcpyAsync(host_scal_, scal_, 13 * nseg_ * sizeof(double), cudaMemcpyDeviceToHost,
                          L_.stream));
+      ST(read_true_res());
       CK(cudaStreamSynchronize(L_.stream));
       for (int sg = 0; sg < nseg_; ++sg) {
         for (int a = 0; a < 3; ++a) acc[sg].m_bar[a] = host_scal_[3 * sg + a];
         acc[sg].dm_last = host_scal_[12 * nseg_ + sg];
+        true_res_of(sg, &acc[sg]);
         st[sg] = acc[sg];
       }
     }
@@ -461,19 +488,19 @@ class Engine final : public EngineBase {
     // a1 volume average of m (Sec. 2.4)
     TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 3, m_, ld, 1, nullptr, w_, mbar(), nullptr, red_));
     // a2 b^ms / m_s = F^ms m (Eq. RHS_b), a3 CG on pinned K^ms, x0 = previous U
-    TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, SG_, F_, m_, ld, b_, pinned_));
-    ST(solve_general(kSlotMs, Kms_, 1, b_, U_, opt_.rtol_ms, &si->ims));
+    TK(GSPM_KCLASS_RHS_MS, launch_fdiv<T>(L_, A_, SG_, F_, m_, ld, b_, pinned_));
+    ST(solve_system(kSlotMs, Kms_, 1, b_, U_, Ulo_, opt_.rtol_ms, &si->ims));
     // a4 local demagnetising field h~_d = -grad U
-    TK(GSPM_KCLASS_ROWOPS, launch_fgrad<T>(L_, A_, F_, U_, invML_, hd_, ld));
+    TK(GSPM_KCLASS_GRAD_MS, launch_fgrad<T>(L_, A_, F_, U_, Ulo_, invML_, hd_, ld));
     // a5 E0(m), sigma0 = C E0, E_bar = <E0> + C^-1 sigma_ext
     TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, m_, ld, mag_, D, E0_, sig0_));
     TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
     // a6 b^mech = F^mech E0, a7 CG on pinned K^mech, x0 per the initial-guess mode
-    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
+    TK(GSPM_KCLASS_RHS_MECH, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
     ST(mech_initial_guess(m_, x0_mode_));
-    ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, opt_.rtol_mech, &si->imech));
+    ST(solve_system(kSlotMech, Kmech_, 9, b_, u_, ulo_, opt_.rtol_mech, &si->imech));
     // a8 strain E = E_bar + sym grad u
-    TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
+    TK(GSPM_KCLASS_STRAIN, launch_fstrain<T>(L_, A_, SG_, F_, u_, ulo_, invML_, ebar(), E_, ld));
     // a9 h(m^n)
     TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, m_, hd_, E_, ld, mbar(), hz(), mag_, D, 0, 0.0, h_, nullptr));
     // a10 Gauss-Seidel stages (Algorithm B.1 steps 1-2), (M + eps K) g = M f, x0 = f
@@ -501,14 +528,14 @@ class Engine final : public EngineBase {
     if (resolve_) {
       // variant: the magnetostatic and mechanical equilibria solved again at m* (x0 = the
       // step-n solutions), so h[m*] is the whole effective field of m*
-      TK(GSPM_KCLASS_ROWOPS, launch_fdiv<T>(L_, A_, SG_, F_, ms_, ld, b_, pinned_));
-      ST(solve_general(kSlotMs, Kms_, 1, b_, U_, opt_.rtol_ms, &si->ims2));
-      TK(GSPM_KCLASS_ROWOPS, launch_fgrad<T>(L_, A_, F_, U_, invML_, hd_, ld));
+      TK(GSPM_KCLASS_RHS_MS, launch_fdiv<T>(L_, A_, SG_, F_, ms_, ld, b_, pinned_));
+      ST(solve_system(kSlotMs, Kms_, 1, b_, U_, Ulo_, opt_.rtol_ms, &si->ims2));
+      TK(GSPM_KCLASS_GRAD_MS, launch_fgrad<T>(L_, A_, F_, U_, Ulo_, invML_, hd_, ld));
       TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, ms_, ld, mag_, D, E0_, sig0_));
       TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
-      TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
-      ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, opt_.rtol_mech, &si->imech2));
-      TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
+      TK(GSPM_KCLASS_RHS_MECH, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
+      ST(solve_system(kSlotMech, Kmech_, 9, b_, u_, ulo_, opt_.rtol_mech, &si->imech2));
+      TK(GSPM_KCLASS_STRAIN, launch_fstrain<T>(L_, A_, SG_, F_, u_, ulo_, invML_, ebar(), E_, ld));
     }
     TK(GSPM_KCLASS_POINTWISE, launch_hfield<T>(L_, n, SG_, ms_, hd_, E_, ld, mbar_s(), hz(), mag_, D, 1, P_.alpha * P_.dtau, nullptr, x_));
     // a12 (M + alpha eps K) m** = M f, three right-hand sides
@@ -529,6 +556,40 @@ class Engine final : public EngineBase {
   int set_graph(int on) override {
     graph_on_ = on != 0;
     return GSPM_OK;
+  }
+
+  int set_true_residual(int on) override {
+    tres_on_ = on != 0;
+    return GSPM_OK;
+  }
+
+  // new stopping tolerances (<= 0 keeps one); a captured graph is captured again
+  int set_rtol(double gs, double ms, double mech) override {
+    if (!(gs < 1.0) || !(ms < 1.0) || !(mech < 1.0)) {
+      set_error("set_rtol: tolerances must be below 1");
+      return GSPM_EINVAL;
+    }
+    if (gs > 0) opt_.rtol_gs = gs;
+    if (ms > 0) opt_.rtol_ms = ms;
+    if (mech > 0) opt_.rtol_mech = mech;
+    ++cfg_gen_;
+    return GSPM_OK;
+  }
+
+  // the true residuals of the last K^ms and K^mech solves into host_scal_[13 nseg ..) (async)
+  int read_true_res() {
+    if (tres_on_)
+      CK(cudaMemcpyAsync(host_scal_ + 13 * nseg_, tres_, 4 * nseg_ * sizeof(double),
+                         cudaMemcpyDeviceToHost, L_.stream));
+    return GSPM_OK;
+  }
+  void true_res_of(int sg, gspm_step_stats* a) const {
+    a->true_res_ms_last = a->true_res_mech_last = -1.0;
+    if (!tres_on_) return;
+    const double* t = host_scal_ + 13 * nseg_;
+    a->true_res_ms_last = t[2 * sg + 1] > 0 ? std::sqrt(t[2 * sg] / t[2 * sg + 1]) : 0.0;
+    a->true_res_mech_last =
+        t[2 * nseg_ + 2 * sg + 1] > 0 ? std::sqrt(t[2 * nseg_ + 2 * sg] / t[2 * nseg_ + 2 * sg + 1]) : 0.0;
   }
 
   int graph_alloc() {
@@ -583,6 +644,8 @@ class Engine final : public EngineBase {
     }
     graph_static_ = captured - graph_body_;
     gexec_x0_ = x0_mode_;
+    gexec_tres_ = tres_on_;
+    gexec_gen_ = cfg_gen_;
     return GSPM_OK;
   }
 
@@ -640,7 +703,8 @@ class Engine final : public EngineBase {
   }
 
   int step_graph(int n_steps, const DevParams& D, int printed, gspm_step_stats* st) {
-    if (!gexec_ || gexec_x0_ != x0_mode_) ST(build_graph(D, printed));
+    if (!gexec_ || gexec_x0_ != x0_mode_ || gexec_tres_ != tres_on_ || gexec_gen_ != cfg_gen_)
+      ST(build_graph(D, printed));
     CK(cudaMemsetAsync(gstats_, 0, 4 * (size_t)nseg_ * sizeof(long long), L_.stream));
     for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(gexec_, L_.stream));
     *L_.counter += graph_static_ * n_steps;
@@ -655,6 +719,7 @@ class Engine final : public EngineBase {
                        cudaMemcpyDeviceToHost, L_.stream));
     CK(cudaMemcpyAsync(host_scal_, scal_, 13 * nseg_ * sizeof(double), cudaMemcpyDeviceToHost,
                        L_.stream));
+    ST(read_true_res());
     CK(cudaStreamSynchronize(L_.stream));
     // kernels the loop bodies ran
     *L_.counter += (int64_t)(*hloops - loops_seen_);
@@ -676,8 +741,16 @@ class Engine final : public EngineBase {
       a.it_mech = hst[4 * sg + 1];
       a.it_gs = hst[4 * sg + 2];
       a.noconv = (int)hst[4 * sg + 3];
-      const SolveInfo ms = info_of(hcg[kSlotMs * nseg_ + sg], -1);
-      const SolveInfo me = info_of(hcg[kSlotMech * nseg_ + sg], -1);
+      SolveInfo ms = info_of(hcg[kSlotMs * nseg_ + sg], -1);
+      SolveInfo me = info_of(hcg[kSlotMech * nseg_ + sg], -1);
+      if (Ulo_) {  // refined solves: both CG loops, the residual of the correction solve
+        const SolveInfo ms2 = info_of(hcg[kSlotMs2 * nseg_ + sg], -1);
+        const SolveInfo me2 = info_of(hcg[kSlotMech2 * nseg_ + sg], -1);
+        ms.iters += ms2.iters;
+        ms.relres = ms2.relres;
+        me.iters += me2.iters;
+        me.relres = me2.relres;
+      }
       a.it_ms_last = ms.iters;
       a.it_mech_last = me.iters;
       a.res_ms_last = ms.relres;
@@ -689,6 +762,7 @@ class Engine final : public EngineBase {
       }
       for (int c = 0; c < 3; ++c) a.m_bar[c] = host_scal_[3 * sg + c];
       a.dm_last = host_scal_[12 * nseg_ + sg];
+      true_res_of(sg, &a);
       st[sg] = a;
     }
     CK(cudaGetLastError());
@@ -724,11 +798,11 @@ class Engine final : public EngineBase {
     }
     TK(GSPM_KCLASS_POINTWISE, launch_e0<T>(L_, n, ms_, ld, mag_, D, E0_, sig0_));
     TK(GSPM_KCLASS_POINTWISE, launch_wsum<T>(L_, SG_, 6, E0_, ld, 1, nullptr, w_, ebar(), eext(), red_));
-    TK(GSPM_KCLASS_ROWOPS, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
+    TK(GSPM_KCLASS_RHS_MECH, launch_gdiv<T>(L_, A_, SG_, G_, sig0_, b_, pinned_));
     std::vector<SolveInfo> info;
-    ST(solve_general(kSlotMech, Kmech_, 9, b_, u_, rtol > 0 ? rtol : opt_.rtol_mech, &info));
-    TK(GSPM_KCLASS_ROWOPS, launch_fstrain<T>(L_, A_, SG_, F_, u_, invML_, ebar(), E_, ld));
-    if (u) ST(export_field(u_, 1, 3, 3, u, where));
+    ST(solve_system(kSlotMech, Kmech_, 9, b_, u_, ulo_, rtol > 0 ? rtol : opt_.rtol_mech, &info));
+    TK(GSPM_KCLASS_STRAIN, launch_fstrain<T>(L_, A_, SG_, F_, u_, ulo_, invML_, ebar(), E_, ld));
+    if (u) ST(export_field(u_, 1, 3, 3, u, where, ulo_));
     CK(cudaStreamSynchronize(L_.stream));
     int it = 0, nc = 0;
     double rel = 0.0;
@@ -771,7 +845,7 @@ class Engine final : public EngineBase {
                      : op == GSPM_OP_A_AEPS ? Aaeps_ : M_;
         ST(import_field(x, where, 1, tin_, 1, 1, nullptr));
         if (op == GSPM_OP_K_MS) ST(pin_hide(1));
-        CK(launch_spmv<T>(L_, A_, val, 1, tin_, tout_, var_scalar_));
+        CK(launch_spmv<T>(L_, A_, val, 1, tin_, tout_, var_scalar_, op == GSPM_OP_K_MS ? 1 : 0));
         if (op == GSPM_OP_K_MS) ST(pin_restore(1));
         ST(export_field(tout_, 1, 1, 1, y, where));
         break;
@@ -779,7 +853,7 @@ class Engine final : public EngineBase {
       case GSPM_OP_K_MECH:
         ST(import_field(x, where, 3, tin_, 1, 3, nullptr));
         ST(pin_hide(3));
-        CK(launch_spmv<T>(L_, A_, Kmech_, 9, tin_, tout_, var_block_));
+        CK(launch_spmv<T>(L_, A_, Kmech_, 9, tin_, tout_, var_block_, 1));
         ST(pin_restore(3));
         ST(export_field(tout_, 1, 3, 3, y, where));
         break;
@@ -790,7 +864,7 @@ class Engine final : public EngineBase {
         break;
       case GSPM_OP_GRAD:
         ST(import_field(x, where, 1, r_, 1, 1, nullptr));
-        CK(launch_fgrad<T>(L_, A_, F_, r_, invML_, tout_, ld));
+        CK(launch_fgrad<T>(L_, A_, F_, r_, nullptr, invML_, tout_, ld));
         ST(export_field(tout_, ld, 1, 3, y, where));
         break;
       default:
@@ -830,14 +904,18 @@ class Engine final : public EngineBase {
     switch (field) {
       case GSPM_FIELD_M: ST(import_field(data, where, 3, m_, ld, 1, mag_)); break;
       case GSPM_FIELD_U:
-        ST(import_field(data, where, 1, U_, 1, 1, nullptr));
-        for (int sg = 0; sg < nseg_; ++sg)
+        ST(import_field(data, where, 1, U_, 1, 1, nullptr, Ulo_));
+        for (int sg = 0; sg < nseg_; ++sg) {
           CK(cudaMemsetAsync(U_ + hb_.seg_pin[sg], 0, sizeof(T), L_.stream));
+          if (Ulo_) CK(cudaMemsetAsync(Ulo_ + hb_.seg_pin[sg], 0, sizeof(T), L_.stream));
+        }
         break;
       case GSPM_FIELD_DISP:
-        ST(import_field(data, where, 3, u_, 1, 3, nullptr));
-        for (int sg = 0; sg < nseg_; ++sg)
+        ST(import_field(data, where, 3, u_, 1, 3, nullptr, ulo_));
+        for (int sg = 0; sg < nseg_; ++sg) {
           CK(cudaMemsetAsync(u_ + 3 * hb_.seg_pin[sg], 0, 3 * sizeof(T), L_.stream));
+          if (ulo_) CK(cudaMemsetAsync(ulo_ + 3 * hb_.seg_pin[sg], 0, 3 * sizeof(T), L_.stream));
+        }
         break;
       case GSPM_FIELD_DISP_PREV:
         ST(import_field(data, where, 3, u2_, 1, 3, nullptr));
@@ -860,8 +938,8 @@ class Engine final : public EngineBase {
     }
     switch (field) {
       case GSPM_FIELD_M: ST(export_field(m_, ld, 1, 3, data, where)); break;
-      case GSPM_FIELD_U: ST(export_field(U_, 1, 1, 1, data, where)); break;
-      case GSPM_FIELD_DISP: ST(export_field(u_, 1, 3, 3, data, where)); break;
+      case GSPM_FIELD_U: ST(export_field(U_, 1, 1, 1, data, where, Ulo_)); break;
+      case GSPM_FIELD_DISP: ST(export_field(u_, 1, 3, 3, data, where, ulo_)); break;
       case GSPM_FIELD_DISP_PREV: ST(export_field(u2_, 1, 3, 3, data, where)); break;
       case GSPM_FIELD_HD: ST(export_field(hd_, ld, 1, 3, data, where)); break;
       case GSPM_FIELD_STRAIN: ST(export_field(E_, ld, 1, 6, data, where)); break;
@@ -1025,8 +1103,13 @@ class Engine final : public EngineBase {
   }
 
  private:
+  // kSlotMs2 / kSlotMech2: the correction solves of the refinement (mixed precision)
   static constexpr int kSlotMs = 0, kSlotMech = 1, kSlotGs0 = 2, kSlotGs1 = 3, kSlotGs2 = 4,
-                       kSlotGsD = 5, kSolveSlots = 6;
+                       kSlotGsD = 5, kSlotMs2 = 6, kSlotMech2 = 7, kSolveSlots = 8;
+  // stopping tolerance of the first FP32 solve of a refined K^ms / K^mech solve (the correction
+  // solve then reaches the requested one); above the recursive-vs-true residual gap of FP32 CG
+  // on these operators (5e-5 of ||b|| at 3M nodes)
+  static constexpr double kRtolInner = 1e-4;
 
   template <typename X>
   int upload(T** dst, const std::vector<X>& src) {
@@ -1060,7 +1143,7 @@ class Engine final : public EngineBase {
   // host/device [n][nc] float64 (unique order) -> internal array dst(i, c) = dst[i*ns + c*cs]
   template <typename X>
   int import_field(const double* src, int where, int nc, X* dst, int64_t cs, int64_t ns,
-                   const uint8_t* mask) {
+                   const uint8_t* mask, X* lo = nullptr) {
     const double* s = src;
     if (where == GSPM_HOST) {
       CK(cudaMemcpyAsync(stage_, src, nodes_ * nc * sizeof(double), cudaMemcpyHostToDevice,
@@ -1070,16 +1153,17 @@ class Engine final : public EngineBase {
       set_error("bad `where` %d", where);
       return GSPM_EINVAL;
     }
-    CK(launch_import<X>(L_, n_, nc, s, perm_, dst, cs, ns, mask));
+    CK(launch_import<X>(L_, n_, nc, s, perm_, dst, cs, ns, mask, lo));
     return GSPM_OK;
   }
 
   template <typename X>
-  int export_field(const X* src, int64_t cs, int64_t ns, int nc, double* dst, int where) {
+  int export_field(const X* src, int64_t cs, int64_t ns, int nc, double* dst, int where,
+                   const X* lo = nullptr) {
     if (where == GSPM_DEVICE) {
-      CK(launch_export<X>(L_, n_, nc, src, cs, ns, perm_, dst));
+      CK(launch_export<X>(L_, n_, nc, src, cs, ns, perm_, dst, lo));
     } else if (where == GSPM_HOST) {
-      CK(launch_export<X>(L_, n_, nc, src, cs, ns, perm_, stage_));
+      CK(launch_export<X>(L_, n_, nc, src, cs, ns, perm_, stage_, lo));
       CK(cudaMemcpyAsync(dst, stage_, nodes_ * nc * sizeof(double), cudaMemcpyDeviceToHost,
                          L_.stream));
     } else {
@@ -1130,8 +1214,47 @@ class Engine final : public EngineBase {
     return GSPM_OK;
   }
 
-  // K x = b for the pinned Omega_c systems (B = 1 scalar K^ms, B = 9 block K^mech)
-  int solve_general(int slot, const T* val, int B, const T* b, T* x, double rtol,
+  // K x = b for one K^ms (B = 1) or K^mech (B = 9) solve.  Mixed precision: iterative
+  // refinement (Wilkinson's scheme with the working-precision solver run in FP32): a first FP32
+  // CG solve to kRtolInner leaves x; a second CG restarts from x, its initial residual b - K x
+  // formed to twice the working precision (k_cg_init), and accumulates the correction in the
+  // separate array dx_ from zero until ||r|| < rtol ||b||; then (x, xlo) = x + dx as an
+  // unevaluated FP32 sum, so the solution keeps the digits that FP32 rounding of x would lose.
+  // The recursive residual of a single FP32 solve drifts from b - K x by about
+  // eps_32 ||K|| ||x|| (5e-5 of ||b|| at 3M nodes); the correction solve's drift is that of the
+  // much smaller dx.  FP64 (xlo == NULL): one solve.
+  int solve_system(int slot, const T* val, int B, const T* b, T* x, T* xlo, double rtol,
+                   std::vector<SolveInfo>* info) {
+    const int epr = B == 9 ? 3 : 1;
+    const int slot2 = slot == kSlotMs ? kSlotMs2 : kSlotMech2;
+    if (!xlo) {
+      ST(solve_general(slot, val, B, b, x, x, rtol, info));
+    } else {
+      const int64_t len = epr * n_;
+      std::vector<SolveInfo> i1, i2;
+      CK(cudaMemsetAsync(xlo, 0, len * sizeof(T), L_.stream));
+      ST(solve_general(slot, val, B, b, x, x, std::max(rtol, kRtolInner), &i1));
+      CK(cudaMemsetAsync(dx_, 0, len * sizeof(T), L_.stream));
+      ST(solve_general(slot2, val, B, b, x, dx_, rtol, &i2));
+      TK(GSPM_KCLASS_CG_INIT, launch_refine_add<T>(L_, len, x, xlo, dx_));
+      if (!capturing_) {
+        info->assign(nseg_, SolveInfo());
+        for (int sg = 0; sg < nseg_; ++sg) {
+          (*info)[sg].iters = i1[sg].iters + i2[sg].iters;
+          (*info)[sg].relres = i2[sg].relres;
+          (*info)[sg].noconv = i1[sg].noconv + i2[sg].noconv;
+        }
+      }
+    }
+    if (tres_on_)
+      TK(GSPM_KCLASS_CG_INIT, launch_true_res<T>(L_, A_, SG_, val, B, b, x, xlo, red_, tres_ + (B == 9 ? 2 * nseg_ : 0)));
+    return GSPM_OK;
+  }
+
+  // CG for K x = b (B = 1 scalar K^ms, B = 9 block K^mech), pinned or singular form, started from
+  // x0 (read only) with the iterates accumulated into x: x == x0 is the plain solve; x != x0
+  // (zero on entry) is the correction solve of solve_system, whose solution is x0 + x
+  int solve_general(int slot, const T* val, int B, const T* b, const T* x0, T* x, double rtol,
                     std::vector<SolveInfo>* info) {
     Trace trace(B == 9 ? "cg_mech" : "cg_ms");
     CGState* st = cg_ + (int64_t)slot * nseg_;
@@ -1141,15 +1264,17 @@ class Engine final : public EngineBase {
     double* bmean = proj_;
     double* xpin = proj_ + 3 * nseg_;
     CK(cudaMemsetAsync(na, 0, sizeof(int), L_.stream));
+    const bool restart = x != x0;
     if (pinned_) {
       // the pinned system (Sec. 2.5): x0 moved to zero at the pinned node
-      TK(GSPM_KCLASS_CG_INIT, launch_pin_shift<T>(L_, A_, SG_, epr, x, xpin));
+      if (!restart) TK(GSPM_KCLASS_CG_INIT, launch_pin_shift<T>(L_, A_, SG_, epr, x, xpin));
     } else {
-      // the consistent singular system: x0 minus its per-segment mean of each component (the
-      // constants only add rounding noise to K x0: with K in FP32, K 1 is not 0), and b minus
-      // its mean
-      TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, x, 1, epr, nullptr, wmean_, xpin, nullptr, red_));
-      TK(GSPM_KCLASS_CG_INIT, launch_seg_shift<T>(L_, A_, SG_, epr, x, xpin));
+      // the consistent singular system: x0 minus its per-segment mean of each component, and b
+      // minus its mean
+      if (!restart) {
+        TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, x, 1, epr, nullptr, wmean_, xpin, nullptr, red_));
+        TK(GSPM_KCLASS_CG_INIT, launch_seg_shift<T>(L_, A_, SG_, epr, x, xpin));
+      }
       TK(GSPM_KCLASS_CG_INIT, launch_wsum<T>(L_, SG_, epr, b, 1, epr, nullptr, wmean_, bmean, nullptr, red_));
     }
     // two-level preconditioned CG on the singular systems (the pinned form stays plain)
@@ -1164,12 +1289,12 @@ class Engine final : public EngineBase {
       TK(GSPM_KCLASS_CG_VEC, launch_pcg_z<T>(L_, SG_, CC_, epr, r_, dinv, ec_, z, st, init, red_));
       return GSPM_OK;
     };
-    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x, r_, p_, st, na, rtol, opt_.max_iter, red_, pinned_ ? nullptr : bmean, pinned_, pc ? 1 : 0));
+    TK(GSPM_KCLASS_CG_INIT, launch_cg_init<T>(L_, A_, SG_, val, B, b, x0, r_, p_, st, na, rtol, opt_.max_iter, red_, pinned_ ? nullptr : bmean, pinned_, pc ? 1 : 0));
     if (pc) ST(precondition(p_, 1));
     // singular system: p0 projected off the constants
     if (!pinned_) TK(GSPM_KCLASS_CG_INIT, launch_cg_psub<T>(L_, A_, SG_, epr, p_, st));
     auto iter = [&]() -> int {
-      TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_, pinned_));
+      TK(B == 9 ? GSPM_KCLASS_SPMV_MECH : GSPM_KCLASS_SPMV_MS, launch_cg_spmv<T>(L_, A_, SG_, val, B, 1, len, p_, q_, st, red_, B == 9 ? var_block_ : var_scalar_, pinned_, 1));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, epr, 1, len, x, r_, p_, q_, st, na, red_));
       if (pc) {
         // z into q (free after the update), then p = z + beta p
@@ -1201,7 +1326,7 @@ class Engine final : public EngineBase {
     const T* dinv = aval == Aeps_ ? dgs_eps_ : dgs_aeps_;  // NULL: plain CG
     TK(GSPM_KCLASS_CG_INIT, launch_cg_init_gs<T>(L_, A_, SG_, aval, M_, nr, ld_, x, r_, p_, st, na, opt_.rtol_gs, opt_.max_iter, red_, dinv));
     auto iter = [&]() -> int {
-      TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, SG_, aval, 1, nr, ld_, p_, q_, st, red_, var_scalar_, 0));
+      TK(GSPM_KCLASS_SPMV_GS, launch_cg_spmv<T>(L_, A_, SG_, aval, 1, nr, ld_, p_, q_, st, red_, var_gs_, 0, 0));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_update<T>(L_, SG_, 1, nr, ld_, x, r_, p_, q_, st, na, red_, dinv));
       TK(GSPM_KCLASS_CG_VEC, launch_cg_pupdate<T>(L_, SG_, 1, nr, ld_, r_, p_, st, loop_, dinv));
       return GSPM_OK;
@@ -1248,8 +1373,8 @@ class Engine final : public EngineBase {
         if (aor[row] >= 0) arows[fill[aor[row]]++] = (int32_t)row;
     }
     // the inverses' stored upper-triangle tiles (see launch_coarse_symv): the symmetric part of
-    // the FP64 inverse (its column solves leave the two triangles a few ulps apart), rounded once
-    // to the storage type
+    // the FP64 inverse rounded once to the storage type, checked positive definite after the
+    // rounding (coarse_round_spd)
     using S16 = typename CoarseStore<T>::type;
     constexpr int64_t TS = coarse_tile<T>();
     struct Tiles {
@@ -1266,7 +1391,7 @@ class Engine final : public EngineBase {
       X.q0.resize(S);
       for (int sg = 0; sg < S; ++sg) {
         const HostCoarse& hc = hb_.coarse[sg];
-        const std::vector<double>& inv = e == 3 ? hc.inv_mech : hc.inv_ms;
+        const std::vector<double>& inv = e == 3 ? hc.store_mech : hc.store_ms;
         const int64_t nc = e * hc.n_agg, Tn = (nc + TS - 1) / TS;
         X.t0[sg] = (int64_t)X.tseg.size();
         X.Tn[sg] = (int32_t)Tn;
@@ -1282,8 +1407,7 @@ class Engine final : public EngineBase {
             for (int64_t r = 0; r < TS && I * TS + r < nc; ++r)
               for (int64_t c = 0; c < TS && J * TS + c < nc; ++c) {
                 const int64_t gi = I * TS + r, gj = J * TS + c;
-                X.data[base + r * TS + c] =
-                    to_store<S16>(0.5 * (inv[gi * nc + gj] + inv[gj * nc + gi]));
+                X.data[base + r * TS + c] = to_store<S16>(inv[gi * nc + gj]);
               }
           }
       }
@@ -1631,12 +1755,13 @@ class Engine final : public EngineBase {
   T *m_ = nullptr, *ms_ = nullptr, *h_ = nullptr, *hd_ = nullptr, *E_ = nullptr, *E0_ = nullptr,
     *sig0_ = nullptr, *p_ = nullptr, *q_ = nullptr, *tin_ = nullptr, *tout_ = nullptr;
   T *U_ = nullptr, *u_ = nullptr, *b_ = nullptr, *r_ = nullptr, *x_ = nullptr;
+  T *Ulo_ = nullptr, *ulo_ = nullptr, *dx_ = nullptr;  // refinement (mixed precision only)
   double *stage_ = nullptr, *scal_ = nullptr;
   CGState* cg_ = nullptr;
   CGState* host_state_ = nullptr;
   Red red_{};
   int pred_[kSolveSlots];
-  int var_block_ = 0, var_scalar_ = 0;
+  int var_block_ = 0, var_scalar_ = 0, var_gs_ = 0;
   float tune_ms_block_[kSpmvVariants] = {}, tune_ms_scalar_[kSpmvVariants] = {};
   int seen_[kSolveSlots] = {};
   // K^ms / K^mech solves: pinned system (flag) or the consistent singular one (default)
@@ -1644,6 +1769,8 @@ class Engine final : public EngineBase {
   bool resolve_ = false;     // equilibria solved again at m* (Algorithm B.1 step 3 variant)
   double* wmean_ = nullptr;  // [n] 1 / (rows of the row's segment), 0 on padding rows
   double* proj_ = nullptr;   // [6 nseg] per-segment means of b, then pinned values of x
+  double* tres_ = nullptr;   // [4 nseg] ||b - K x||^2, ||b||^2 of the last K^ms, K^mech solves
+  bool tres_on_ = false;     // compute them after every K^ms / K^mech solve
   T* pinsave_ = nullptr;     // [3 nseg]
   int* bad_ = nullptr;       // [nseg] non-finite or zero m** met by the projection
   int* host_bad_ = nullptr;  // pinned copy
@@ -1662,6 +1789,8 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr;
   cudaGraphExec_t gexec_ = nullptr;
   int gexec_x0_ = -1;
+  bool gexec_tres_ = false;
+  int gexec_gen_ = -1, cfg_gen_ = 0;  // option generation the graph was captured with
   int64_t graph_static_ = 0;  // launches per replay outside the loop bodies
   int64_t graph_body_ = 0;    // launches captured inside loop bodies (once each)
   LoopCtl loop_{};            // loop control of the body being captured (zero otherwise)
@@ -1730,7 +1859,8 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
     coarse.resize(nmesh);
     for (int k = 0; k < nmesh; ++k) {
       const int64_t npa = coarse_nodes_of(opt->coarse_nodes, c->hm[k].n);
-      const int st = host_coarse_build(c->hm[k], hs[k], ops[k], npa, &coarse[k]);
+      const int st = host_coarse_build(c->hm[k], hs[k], ops[k], npa,
+                                       opt->precision == GSPM_PREC_MIXED ? 1 : 0, &coarse[k]);
       if (st != GSPM_OK) return st;
     }
   }
@@ -1756,6 +1886,8 @@ static int load_batch(const gspm_mesh_desc* meshes, int nmesh, const gspm_materi
     for (auto& hc : c->hb.coarse) {
       hc.inv_mech = std::vector<double>();
       hc.inv_ms = std::vector<double>();
+      hc.store_mech = std::vector<double>();
+      hc.store_ms = std::vector<double>();
       hc.dinv_mech = std::vector<double>();
       hc.dinv_ms = std::vector<double>();
     }
@@ -1821,7 +1953,11 @@ int gspm_mesh_info_get(const gspm_ctx* ctx, gspm_mesh_info* out) {
   out->dtau = ctx->P.dtau;
   out->device_bytes = ctx->eng ? ctx->eng->device_bytes() : 0;
   out->n_aggregates = 0;
-  for (const auto& hc : ctx->hb.coarse) out->n_aggregates += hc.n_agg;
+  for (const auto& hc : ctx->hb.coarse) {
+    out->n_aggregates += hc.n_agg;
+    out->coarse_shift_ms = std::max(out->coarse_shift_ms, hc.shift_ms);
+    out->coarse_shift_mech = std::max(out->coarse_shift_mech, hc.shift_mech);
+  }
   if (ctx->eng) {
     float tb[kSpmvVariants], ts[kSpmvVariants];
     int vb = 0, vs = 0, is = 0;
@@ -1866,7 +2002,9 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
     case GSPM_EXPORT_COARSE_K_MS:
     case GSPM_EXPORT_COARSE_K_MECH:
     case GSPM_EXPORT_COARSE_INV_MS:
-    case GSPM_EXPORT_COARSE_INV_MECH: {
+    case GSPM_EXPORT_COARSE_INV_MECH:
+    case GSPM_EXPORT_COARSE_STORED_MS:
+    case GSPM_EXPORT_COARSE_STORED_MECH: {
       if (ctx->hb.coarse.empty()) {
         set_error("mesh_export: the context has no two-level preconditioner");
         return GSPM_ESTATE;
@@ -1879,6 +2017,15 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
         const std::vector<double>& v = what == GSPM_EXPORT_COARSE_INV_MS ? hc.inv_ms : hc.inv_mech;
         if (v.empty()) {
           set_error("mesh_export: coarse inverses are kept by host-only contexts only");
+          return GSPM_ESTATE;
+        }
+        return put(v.data(), (int64_t)v.size(), 8);
+      }
+      if (what == GSPM_EXPORT_COARSE_STORED_MS || what == GSPM_EXPORT_COARSE_STORED_MECH) {
+        const std::vector<double>& v =
+            what == GSPM_EXPORT_COARSE_STORED_MS ? hc.store_ms : hc.store_mech;
+        if (v.empty()) {
+          set_error("mesh_export: stored coarse inverses are kept by host-only contexts only");
           return GSPM_ESTATE;
         }
         return put(v.data(), (int64_t)v.size(), 8);
@@ -1904,6 +2051,20 @@ int gspm_mesh_export(const gspm_ctx* ctx, int what, void* out, int64_t count) {
       return GSPM_ESTATE;                                          \
     }                                                              \
   } while (0)
+
+int gspm_coarse_round(const double* A, int64_t n, int bf16, double* out, double* shift) {
+  if (!A || !out || n < 1 || (bf16 != 0 && bf16 != 1)) {
+    set_error("coarse_round: need A, out, n >= 1 and bf16 in {0, 1}");
+    return GSPM_EINVAL;
+  }
+  std::vector<double> st;
+  double sh = 0.0;
+  const int rc = coarse_round_spd(A, n, bf16, &st, &sh);
+  if (rc != GSPM_OK) return rc;
+  memcpy(out, st.data(), (size_t)(n * n) * sizeof(double));
+  if (shift) *shift = sh;
+  return GSPM_OK;
+}
 
 int gspm_set_field(gspm_ctx* ctx, int field, const double* data, int where) {
   NEED_ENGINE(ctx);
@@ -1954,6 +2115,22 @@ int64_t gspm_launch_count(const gspm_ctx* ctx) { return ctx ? ctx->launches : 0;
 int gspm_set_graph(gspm_ctx* ctx, int on) {
   NEED_ENGINE(ctx);
   return ctx->eng->set_graph(on);
+}
+
+int gspm_set_true_residual(gspm_ctx* ctx, int on) {
+  NEED_ENGINE(ctx);
+  return ctx->eng->set_true_residual(on);
+}
+
+int gspm_set_rtol(gspm_ctx* ctx, double rtol_gs, double rtol_ms, double rtol_mech) {
+  NEED_ENGINE(ctx);
+  const int rc = ctx->eng->set_rtol(rtol_gs, rtol_ms, rtol_mech);
+  if (rc == GSPM_OK) {
+    if (rtol_gs > 0) ctx->opt.rtol_gs = rtol_gs;
+    if (rtol_ms > 0) ctx->opt.rtol_ms = rtol_ms;
+    if (rtol_mech > 0) ctx->opt.rtol_mech = rtol_mech;
+  }
+  return rc;
 }
 
 int gspm_set_x0_mode(gspm_ctx* ctx, int mode) {

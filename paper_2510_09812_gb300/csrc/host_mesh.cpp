@@ -805,8 +805,45 @@ static bool spd_inverse(std::vector<double>& A, int64_t n, std::vector<double>* 
   return true;
 }
 
+double bf16_round(double v) {
+  const float f = (float)v;
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof(u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  float r;
+  std::memcpy(&r, &u, sizeof(r));
+  return (double)r;
+}
+
+int coarse_round_spd(const double* A, int64_t n, int bf16, std::vector<double>* stored,
+                     double* shift) {
+  stored->assign(n * n, 0.0);
+  *shift = 0.0;
+  double dmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) dmax = std::max(dmax, std::fabs(A[i * n + i]));
+  std::vector<double> work;
+  // shifts 0, 2^-8 dmax, ..., dmax: a shift beyond max_i S_ii no longer repairs rounding
+  for (int attempt = 0; attempt <= 9; ++attempt) {
+    const double sh = *shift;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        const double v = 0.5 * (A[i * n + j] + A[j * n + i]) + (i == j ? sh : 0.0);
+        (*stored)[i * n + j] = bf16 ? bf16_round(v) : v;
+      }
+    if (!bf16 && attempt == 0) return GSPM_OK;  // FP64 storage: the symmetric part itself
+    work = *stored;
+    if (n == 0 || chol_blocked(work, n)) return GSPM_OK;
+    *shift = sh > 0.0 ? 2.0 * sh : std::ldexp(dmax, -8);
+  }
+  set_error("coarse inverse: not positive definite after rounding with any diagonal shift up to "
+            "its largest diagonal entry");
+  return GSPM_EMESH;
+}
+
 int host_coarse_build(const HostMesh& hm, const HostSell& s, const HostOps& ops,
-                      int64_t nodes_per_agg, HostCoarse* c) {
+                      int64_t nodes_per_agg, int bf16, HostCoarse* c) {
   const int64_t n = hm.n;
   std::vector<int64_t> bin_of;
   coarse_bins(hm, nodes_per_agg, c->nb, &bin_of);
@@ -863,6 +900,17 @@ int host_coarse_build(const HostMesh& hm, const HostSell& s, const HostOps& ops,
       !regularised_inverse(c->Kc_ms, na, 1, &c->inv_ms)) {
     set_error("mesh_load: coarse operator of the preconditioner is not positive definite");
     return GSPM_EMESH;
+  }
+  // the device's copies: checked positive definite after rounding (one aggregate: no coarse
+  // correction, the inverse is all zero and stays so)
+  if (na > 1) {
+    const int st1 = coarse_round_spd(c->inv_mech.data(), n3, bf16, &c->store_mech, &c->shift_mech);
+    if (st1 != GSPM_OK) return st1;
+    const int st2 = coarse_round_spd(c->inv_ms.data(), na, bf16, &c->store_ms, &c->shift_ms);
+    if (st2 != GSPM_OK) return st2;
+  } else {
+    c->store_mech = c->inv_mech;
+    c->store_ms = c->inv_ms;
   }
   return GSPM_OK;
 }

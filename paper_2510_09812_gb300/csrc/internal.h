@@ -104,9 +104,24 @@ struct HostCoarse {
   std::vector<double> Kc_mech, Kc_ms;  // [3 n_agg]^2, [n_agg]^2 row-major, unregularised
   std::vector<double> inv_mech, inv_ms;
   std::vector<double> dinv_mech, dinv_ms;  // [3 n], [n]
+  // the inverses as the device stores them (coarse_round_spd), widened to FP64, and the
+  // diagonal shift that made the rounded matrix positive definite (0 when it already was)
+  std::vector<double> store_mech, store_ms;
+  double shift_mech = 0.0, shift_ms = 0.0;
 };
+// bf16: the device keeps the coarse inverses in bfloat16 (mixed precision), else in FP64
 int host_coarse_build(const HostMesh& hm, const HostSell& s, const HostOps& ops,
-                      int64_t nodes_per_agg, HostCoarse* c);
+                      int64_t nodes_per_agg, int bf16, HostCoarse* c);
+
+// Storage of a dense symmetric positive definite matrix (the coarse inverse): its symmetric part
+// S = (A + A^T) / 2, rounded entry by entry to bfloat16 (round to nearest even of the FP32 value)
+// when bf16, else kept in FP64.  The rounded matrix (widened to FP64) must pass a Cholesky
+// factorisation; if it does not, a diagonal shift s is added before rounding, s = 2^-8 max_i
+// S_ii and doubled until it does.  Returns GSPM_OK with `stored` [n*n] and `shift`, or
+// GSPM_EMESH if no shift up to max_i S_ii succeeds (A is not positive definite).
+int coarse_round_spd(const double* A, int64_t n, int bf16, std::vector<double>* stored,
+                     double* shift);
+double bf16_round(double v);  // the value of v rounded to bfloat16 (nearest even), as FP64
 
 // A batch of meshes ("segments") concatenated slice-aligned: segment s owns the rows
 // [seg_row0[s], seg_row0[s] + seg_nrow[s]) (its last slice padded with empty rows when another

@@ -172,23 +172,38 @@ __device__ __forceinline__ bool seg_reduce_hl(const T (&hi)[NC], const T (&lo)[N
   }
 }
 
+// The difference forms sum_j A_ij (x_j - x_i) of the zero-row-sum operators (K^ms, K^mech, F^ms,
+// G) are used in FP32, where they keep smooth fields from cancelling; in FP64 the plain products
+// are accurate enough and each extra subtraction costs FP64 issue slots.
+template <typename T>
+constexpr int kDiff = std::is_same<T, float>::value ? 1 : 0;
+
 __device__ __forceinline__ bool row_valid(const DSeg& G, int seg, int64_t row) {
   return row - G.seg_row0[seg] < G.seg_nrow[seg];
 }
 
 // y_r(row) = sum_k A(row, k) x_r(col(row, k)) for one row of a scalar SELL matrix, neighbours
-// k = k0, k0 + kstep, ...
+// k = k0, k0 + kstep, ...  diff != 0 (an operator whose rows sum to zero: K^ms, K^mech): formed as
+// sum_k A(row, k) (x_r(col) - x_r(row)), equal in exact arithmetic; a smooth x then does not
+// cancel in the sum, and the FP32 rounding of the values cannot make the operator act on the
+// constants (its rows' rounded sums no longer enter).
 template <typename V, typename X, typename Acc, int NR, int VAR = 0>
 __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restrict__ val,
                                                 int64_t s, int lane, const X* __restrict__ x,
                                                 int64_t ld, const int (&skip)[NR],
-                                                Acc (&acc)[NR], int k0 = 0, int kstep = 1) {
+                                                Acc (&acc)[NR], int k0 = 0, int kstep = 1,
+                                                int diff = 0) {
   const int64_t base = A.sptr[s];
   const int len = A.slen[s];
   const int32_t* cp = A.col + base + lane;
   const V* vp = val + base + lane;
+  const int64_t row = s * 32 + lane;
+  X xi[NR];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
+  for (int r = 0; r < NR; ++r) {
+    acc[r] = Acc(0);
+    xi[r] = diff && row < A.n ? x[r * ld + row] : X(0);
+  }
   if (VAR == 1 || VAR == 3) {
     // eight neighbours per round: their columns and values first, then the gathers, then the
     // FMAs (more loads in flight per thread)
@@ -207,7 +222,7 @@ __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restr
         if (!skip[r]) {
           X g[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = __ldg(x + r * ld + j[u]);
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(x + r * ld + j[u]) - xi[r];
 #pragma unroll
           for (int u = 0; u < 8; ++u) acc[r] += (Acc)w[u] * (Acc)g[u];
         }
@@ -220,38 +235,45 @@ __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restr
     const Acc a = (Acc)__ldcs(vp + (int64_t)k * 32);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      if (!skip[r]) acc[r] += a * (Acc)__ldg(x + r * ld + j);
+      if (!skip[r]) acc[r] += a * (Acc)(__ldg(x + r * ld + j) - xi[r]);
   }
 }
 
 // 3x3-block row: y(row, a) = sum_k sum_b A(row, k)_ab x(col, b); x, y arrays of [n][3].
+// diff != 0: sum_k A(row, k) (x(col) - x(row)), as in sell_scalar_row.
 template <typename V, typename X, typename Acc, int VAR>
 __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restrict__ val,
                                                int64_t s, int lane, const X* __restrict__ x,
-                                               Acc (&acc)[3], int k0 = 0, int kstep = 1) {
+                                               Acc (&acc)[3], int k0 = 0, int kstep = 1,
+                                               int diff = 0) {
   const int64_t base = A.sptr[s];
   const int len = A.slen[s];
   const int32_t* cp = A.col + base + lane;
   const V* vp = val + base * 9 + lane;
+  const int64_t row = s * 32 + lane;
+  const bool own = diff && row < A.n;
+  const X xi0 = own ? x[3 * row] : X(0), xi1 = own ? x[3 * row + 1] : X(0),
+          xi2 = own ? x[3 * row + 2] : X(0);
   acc[0] = acc[1] = acc[2] = Acc(0);
   if (VAR == 1 || VAR == 3) {
     // five neighbours per round: all loads first, then the FMAs
     for (int kb = k0; kb < len; kb += 5 * kstep) {
-      int64_t j[5];
+      int j[5];  // 32-bit: five fewer registers than 64-bit indices in this unrolled round
       V w[5][9];
 #pragma unroll
       for (int u = 0; u < 5; ++u) {
         const int k = kb + u * kstep;
         const bool ok = k < len;
-        j[u] = ok ? (int64_t)__ldcs(cp + (int64_t)k * 32) : 0;
+        j[u] = ok ? __ldcs(cp + (int64_t)k * 32) : 0;
         const V* bp = vp + (int64_t)(ok ? k : 0) * 288;
 #pragma unroll
         for (int e = 0; e < 9; ++e) w[u][e] = ok ? __ldcs(bp + e * 32) : V(0);
       }
 #pragma unroll
       for (int u = 0; u < 5; ++u) {
-        const Acc x0 = (Acc)__ldg(x + 3 * j[u]), x1 = (Acc)__ldg(x + 3 * j[u] + 1),
-                  x2 = (Acc)__ldg(x + 3 * j[u] + 2);
+        const X* xj = x + 3 * (int64_t)j[u];
+        const Acc x0 = (Acc)(__ldg(xj) - xi0), x1 = (Acc)(__ldg(xj + 1) - xi1),
+                  x2 = (Acc)(__ldg(xj + 2) - xi2);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
           acc[a] += (Acc)w[u][3 * a] * x0 + (Acc)w[u][3 * a + 1] * x1 + (Acc)w[u][3 * a + 2] * x2;
@@ -262,8 +284,8 @@ __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restri
     for (int k = k0; k < len; k += kstep) {
       const int64_t j = __ldcs(cp + (int64_t)k * 32);
       const V* bp = vp + (int64_t)k * 288;
-      const Acc x0 = (Acc)__ldg(x + 3 * j), x1 = (Acc)__ldg(x + 3 * j + 1),
-                x2 = (Acc)__ldg(x + 3 * j + 2);
+      const Acc x0 = (Acc)(__ldg(x + 3 * j) - xi0), x1 = (Acc)(__ldg(x + 3 * j + 1) - xi1),
+                x2 = (Acc)(__ldg(x + 3 * j + 2) - xi2);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         acc[a] += (Acc)__ldcs(bp + (3 * a + 0) * 32) * x0;
@@ -300,32 +322,41 @@ template <int NR>
 __device__ __forceinline__ void sell_scalar_row_dot2(const DSell& A, const float* __restrict__ val,
                                                      int64_t s, int lane,
                                                      const float* __restrict__ x, int64_t ld,
-                                                     Dot2 (&acc)[NR]) {
+                                                     Dot2 (&acc)[NR], int diff = 0) {
   const int64_t base = A.sptr[s];
   const int len = A.slen[s];
   const int32_t* cp = A.col + base + lane;
   const float* vp = val + base + lane;
+  const int64_t row = s * 32 + lane;
+  float xi[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) xi[r] = diff && row < A.n ? x[r * ld + row] : 0.f;
 #pragma unroll 4
   for (int k = 0; k < len; ++k) {
     const int j = __ldcs(cp + (int64_t)k * 32);
     const float a = __ldcs(vp + (int64_t)k * 32);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r].add(a, __ldg(x + r * ld + j));
+    for (int r = 0; r < NR; ++r) acc[r].add(a, __fsub_rn(__ldg(x + r * ld + j), xi[r]));
   }
 }
 __device__ __forceinline__ void sell_block_row_dot2(const DSell& A, const float* __restrict__ val,
                                                     int64_t s, int lane,
                                                     const float* __restrict__ x,
-                                                    Dot2 (&acc)[3]) {
+                                                    Dot2 (&acc)[3], int diff = 0) {
   const int64_t base = A.sptr[s];
   const int len = A.slen[s];
   const int32_t* cp = A.col + base + lane;
   const float* vp = val + base * 9 + lane;
+  const int64_t row = s * 32 + lane;
+  const bool own = diff && row < A.n;
+  const float xi0 = own ? x[3 * row] : 0.f, xi1 = own ? x[3 * row + 1] : 0.f,
+              xi2 = own ? x[3 * row + 2] : 0.f;
 #pragma unroll 2
   for (int k = 0; k < len; ++k) {
     const int64_t j = __ldcs(cp + (int64_t)k * 32);
     const float* bp = vp + (int64_t)k * 288;
-    const float x0 = __ldg(x + 3 * j), x1 = __ldg(x + 3 * j + 1), x2 = __ldg(x + 3 * j + 2);
+    const float x0 = __fsub_rn(__ldg(x + 3 * j), xi0), x1 = __fsub_rn(__ldg(x + 3 * j + 1), xi1),
+                x2 = __fsub_rn(__ldg(x + 3 * j + 2), xi2);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       acc[a].add(__ldcs(bp + (3 * a + 0) * 32), x0);
@@ -407,7 +438,8 @@ __global__ void __launch_bounds__(kBlock) k_wsum(DSeg G, ItemList IL, int nc, co
 // ------------------------------------------------------------------------------------------
 template <typename T, int VAR>
 __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv1(DSell A, const T* __restrict__ val,
-                                                  const T* __restrict__ x, T* __restrict__ y) {
+                                                  const T* __restrict__ x, T* __restrict__ y,
+                                                  int diff) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   const int skip[1] = {0};
@@ -416,7 +448,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv1(DSell A, co
     int sl, k0, ks;
     unit_row<VAR>(u, lane, s, sl, k0, ks);
     T acc[1];
-    sell_scalar_row<T, T, T, 1, VAR>(A, val, s, sl, x, 0, skip, acc, k0, ks);
+    sell_scalar_row<T, T, T, 1, VAR>(A, val, s, sl, x, 0, skip, acc, k0, ks, diff);
     const int64_t row = s * 32 + sl;
     if (unit_combine<VAR>(acc, lane) && row < A.n) y[row] = acc[0];
   }
@@ -424,7 +456,8 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv1(DSell A, co
 
 template <typename T, int VAR>
 __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv9(DSell A, const T* __restrict__ val,
-                                                  const T* __restrict__ x, T* __restrict__ y) {
+                                                  const T* __restrict__ x, T* __restrict__ y,
+                                                  int diff) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = gstride() >> 5;
   for (int64_t u = gtid() >> 5; u < A.nslices * units_per_slice<VAR>(); u += nw) {
@@ -432,7 +465,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_spmv9(DSell A, co
     int sl, k0, ks;
     unit_row<VAR>(u, lane, s, sl, k0, ks);
     T acc[3];
-    sell_block_row<T, T, T, VAR>(A, val, s, sl, x, acc, k0, ks);
+    sell_block_row<T, T, T, VAR>(A, val, s, sl, x, acc, k0, ks, diff);
     const int64_t row = s * 32 + sl;
     if (unit_combine<VAR>(acc, lane) && row < A.n) {
       y[3 * row] = acc[0];
@@ -513,11 +546,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
         double acc[1];
         if constexpr (std::is_same<T, float>::value) {
           Dot2 d[1];
-          sell_scalar_row_dot2<1>(A, val, s, lane, x, 0, d);
+          sell_scalar_row_dot2<1>(A, val, s, lane, x, 0, d, 1);
           acc[0] = d[0].value();
         } else {
           const int skip[1] = {0};
-          sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, acc);
+          sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, acc, 0, 1, kDiff<T>);
         }
         if (ok) {
           const double bv = (double)b[row] - bm[0];
@@ -532,10 +565,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(DSell A, DSeg G, ItemList IL
         double acc[3];
         if constexpr (std::is_same<T, float>::value) {
           Dot2 d[3];
-          sell_block_row_dot2(A, val, s, lane, x, d);
+          sell_block_row_dot2(A, val, s, lane, x, d, 1);
           for (int a = 0; a < 3; ++a) acc[a] = d[a].value();
         } else {
-          sell_block_row<T, T, double, 0>(A, val, s, lane, x, acc);
+          sell_block_row<T, T, double, 0>(A, val, s, lane, x, acc, 0, 1, kDiff<T>);
         }
         if (ok) {
 #pragma unroll
@@ -634,9 +667,65 @@ __global__ void __launch_bounds__(kBlock) k_cg_init_gs(DSell A, DSeg G, ItemList
   }
 }
 
+// True residual of a finished K^ms (B = 1) or K^mech (B = 9) solve, independent of the CG
+// recursion: per segment, over every row but the pinned one, sum (b - A x)^2 and b^2 into
+// out[2 seg] and out[2 seg + 1].  A x is accumulated in FP64 (a product of two FP32 values is
+// exact in FP64), so the result measures the solution against the operator as stored.  x is
+// zero at the pinned row, so on the other rows A x is the pinned operator's product too.
+template <typename T, int B>
+__global__ void __launch_bounds__(kBlock) k_true_res(DSell A, DSeg G, ItemList IL,
+                                                     const T* __restrict__ val,
+                                                     const T* __restrict__ b,
+                                                     const T* __restrict__ x,
+                                                     const T* __restrict__ xlo, Red red,
+                                                     double* out) {
+  constexpr int NC = B == 9 ? 3 : 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
+    const int seg = IL.seg[item];
+    const int64_t pin = G.seg_pin[seg];
+    double v[2] = {0.0, 0.0};
+    for (int64_t s = IL.sl0[item] + warp; s < IL.sl1[item]; s += kBlock / 32) {
+      const int64_t row = s * 32 + lane;
+      double acc[3] = {0.0, 0.0, 0.0};
+      if (B == 1) {
+        const int skip[1] = {0};
+        double a1[1];
+        sell_scalar_row<T, T, double, 1>(A, val, s, lane, x, 0, skip, a1, 0, 1, kDiff<T>);
+        acc[0] = a1[0];
+        if (xlo) {
+          sell_scalar_row<T, T, double, 1>(A, val, s, lane, xlo, 0, skip, a1, 0, 1, kDiff<T>);
+          acc[0] += a1[0];
+        }
+      } else {
+        sell_block_row<T, T, double, 0>(A, val, s, lane, x, acc, 0, 1, kDiff<T>);
+        if (xlo) {
+          double a3[3];
+          sell_block_row<T, T, double, 0>(A, val, s, lane, xlo, a3, 0, 1, kDiff<T>);
+          for (int a = 0; a < 3; ++a) acc[a] += a3[a];
+        }
+      }
+      if (row_valid(G, seg, row) && row != pin) {
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          const double bv = (double)b[NC * row + a], rv = bv - acc[a];
+          v[0] += rv * rv;
+          v[1] += bv * bv;
+        }
+      }
+    }
+    __shared__ double res[2];
+    if (seg_reduce<2>(v, item, seg, G, IL, red, res) && threadIdx.x == 0) {
+      out[2 * seg] = res[0];
+      out[2 * seg + 1] = res[1];
+    }
+  }
+}
+
 // q = A p with the p.q dot fused; the segment's last item forms alpha = rr / p.q.
 // pinned: q = 0 at the segment's pinned row (the pinned operator; p is 0 there).
-template <typename T, int B, int NR, int VAR>
+// DIFF: the operator's rows sum to zero (K^ms, K^mech), products in difference form
+template <typename T, int B, int NR, int VAR, int DIFF>
 __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, DSeg G, ItemList IL, const T* __restrict__ val,
                                                     int64_t ld, const T* __restrict__ p,
                                                     T* __restrict__ q, CGState* st, Red red,
@@ -665,7 +754,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
       const int64_t row = s * 32 + sl;
       if (B == 1) {
         T acc[NR];
-        sell_scalar_row<T, T, T, NR, VAR>(A, val, s, sl, p, ld, skip, acc, k0, ks);
+        sell_scalar_row<T, T, T, NR, VAR>(A, val, s, sl, p, ld, skip, acc, k0, ks, DIFF);
         if (row == pin) {
 #pragma unroll
           for (int k = 0; k < NR; ++k) acc[k] = T(0);
@@ -680,7 +769,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<VAR>()) k_cg_spmv(DSell A, 
         }
       } else {
         T acc[3];
-        sell_block_row<T, T, T, VAR>(A, val, s, sl, p, acc, k0, ks);
+        sell_block_row<T, T, T, VAR>(A, val, s, sl, p, acc, k0, ks, DIFF);
         if (row == pin) acc[0] = acc[1] = acc[2] = T(0);
         if (unit_combine<VAR>(acc, lane) && row_valid(G, seg, row)) {
           T pq = T(0);
@@ -1300,8 +1389,8 @@ __global__ void k_cg_zero(DSeg G, ItemList IL, int epr, T* x, const CGState* st)
   for (int item = blockIdx.x; item < IL.nitems; item += gridDim.x) {
     const int seg = IL.seg[item];
     if (!st[seg].zero_x) continue;
-    const int64_t e0 = (int64_t)IL.sl0[item] * 32 * epr;
-    const int64_t e1 = (int64_t)IL.sl1[item] * 32 * epr;
+    int64_t e0, e1;
+    item_elems(G, IL, item, seg, epr, e0, e1);
     for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) x[i] = T(0);
   }
 }
@@ -1309,6 +1398,12 @@ __global__ void k_cg_zero(DSeg G, ItemList IL, int epr, T* x, const CGState* st)
 // ------------------------------------------------------------------------------------------
 // F^ms / G operators (Sec. 2.3): right-hand sides and derivatives as row gathers
 // ------------------------------------------------------------------------------------------
+// Every row of F^ms and of G sums to zero (sum_j d_a phi_j = 0; the integral of d_a phi_i over
+// its patch vanishes), so in FP32 each product is formed as sum_j F_ij (x_j - x_i): the same
+// value in exact arithmetic, but a smooth or nearly uniform x (m, sigma0, U, u) no longer
+// cancels in the sum, and the rounding of F and G to FP32 does not turn a uniform x into a
+// spurious result (kDiff).
+//
 // b_i = sum_j F_{ij,a} m_{j,a}  (Eq. RHS_b divided by m_s); pin_zero: the segment's pinned
 // entry is 0 (right-hand side of the pinned system)
 template <typename T>
@@ -1322,16 +1417,20 @@ __global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, DSeg G, const T* __res
     const int len = A.slen[s];
     const int32_t* cp = A.col + base + lane;
     const T* vp = Fv + base * 3 + lane;
+    const int64_t row = s * 32 + lane;
+    const bool in = row < A.n;
+    const bool own = in && kDiff<T>;
+    const T m0 = own ? m[row] : T(0), m1 = own ? m[ld + row] : T(0),
+            m2 = own ? m[2 * ld + row] : T(0);
     T acc = T(0);
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
       const int64_t j = __ldcs(cp + (int64_t)k * 32);
       const T* fp = vp + (int64_t)k * 96;
-      acc += __ldcs(fp) * __ldg(m + j) + __ldcs(fp + 32) * __ldg(m + ld + j) +
-             __ldcs(fp + 64) * __ldg(m + 2 * ld + j);
+      acc += __ldcs(fp) * (__ldg(m + j) - m0) + __ldcs(fp + 32) * (__ldg(m + ld + j) - m1) +
+             __ldcs(fp + 64) * (__ldg(m + 2 * ld + j) - m2);
     }
-    const int64_t row = s * 32 + lane;
-    if (row < A.n) b[row] = pin_zero && row == G.seg_pin[G.seg_of_slice[s]] ? T(0) : acc;
+    if (in) b[row] = pin_zero && row == G.seg_pin[G.seg_of_slice[s]] ? T(0) : acc;
   }
 }
 
@@ -1339,6 +1438,7 @@ __global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, DSeg G, const T* __res
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_fgrad(DSell A, const T* __restrict__ Fv,
                                                   const T* __restrict__ U,
+                                                  const T* __restrict__ Ulo,
                                                   const double* __restrict__ invML,
                                                   T* __restrict__ hd, int64_t ld) {
   const int lane = threadIdx.x & 31;
@@ -1348,17 +1448,19 @@ __global__ void __launch_bounds__(kBlock) k_fgrad(DSell A, const T* __restrict__
     const int len = A.slen[s];
     const int32_t* cp = A.col + base + lane;
     const T* vp = Fv + base * 3 + lane;
+    const int64_t row = s * 32 + lane;
+    const T ui = kDiff<T> && row < A.n ? U[row] : T(0);
+    const T uil = Ulo && row < A.n ? Ulo[row] : T(0);
     T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
       const int64_t j = __ldcs(cp + (int64_t)k * 32);
       const T* fp = vp + (int64_t)k * 96;
-      const T u = (T)__ldg(U + j);
+      const T u = ((T)__ldg(U + j) - ui) + (Ulo ? __ldg(Ulo + j) - uil : T(0));
       a0 += __ldcs(fp) * u;
       a1 += __ldcs(fp + 32) * u;
       a2 += __ldcs(fp + 64) * u;
     }
-    const int64_t row = s * 32 + lane;
     if (row < A.n) {
       const T im = (T)invML[row];
       hd[row] = a0 * im;
@@ -1373,6 +1475,7 @@ __global__ void __launch_bounds__(kBlock) k_fgrad(DSell A, const T* __restrict__
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, DSeg G, const T* __restrict__ Fv,
                                                     const T* __restrict__ u,
+                                                    const T* __restrict__ ulo,
                                                     const double* __restrict__ invML,
                                                     const double* __restrict__ Ebar,
                                                     T* __restrict__ E, int64_t ld) {
@@ -1383,20 +1486,32 @@ __global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, DSeg G, const T* __
     const int len = A.slen[s];
     const int32_t* cp = A.col + base + lane;
     const T* vp = Fv + base * 3 + lane;
+    const int64_t row = s * 32 + lane;
+    const bool in = row < A.n;
+    const bool own = in && kDiff<T>;
+    const T ui[3] = {own ? u[3 * row] : T(0), own ? u[3 * row + 1] : T(0),
+                     own ? u[3 * row + 2] : T(0)};
+    const bool lo = ulo && in;
+    const T uil[3] = {lo ? ulo[3 * row] : T(0), lo ? ulo[3 * row + 1] : T(0),
+                      lo ? ulo[3 * row + 2] : T(0)};
     T g[3][3] = {};
 #pragma unroll 2
     for (int k = 0; k < len; ++k) {
       const int64_t j = __ldcs(cp + (int64_t)k * 32);
       const T* fp = vp + (int64_t)k * 96;
       const T f[3] = {__ldcs(fp), __ldcs(fp + 32), __ldcs(fp + 64)};
-      const T uj[3] = {(T)__ldg(u + 3 * j), (T)__ldg(u + 3 * j + 1), (T)__ldg(u + 3 * j + 2)};
+      T uj[3] = {(T)__ldg(u + 3 * j) - ui[0], (T)__ldg(u + 3 * j + 1) - ui[1],
+                 (T)__ldg(u + 3 * j + 2) - ui[2]};
+      if (ulo) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) uj[b] += __ldg(ulo + 3 * j + b) - uil[b];
+      }
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) g[a][b] += f[a] * uj[b];
     }
-    const int64_t row = s * 32 + lane;
-    if (row < A.n) {
+    if (in) {
       const double* eb = Ebar + 6 * G.seg_of_slice[s];
       const T im = -(T)invML[row];  // g[a][b] * im = d_a u_b
       E[row] = (T)eb[0] + g[0][0] * im;
@@ -1422,6 +1537,11 @@ __global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, DSeg G, const T* __res
     const int len = A.slen[s];
     const int32_t* cp = A.col + base + lane;
     const T* vp = Gv + base * 3 + lane;
+    const int64_t row = s * 32 + lane;
+    const bool in = row < A.n;
+    T si[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) si[c] = in && kDiff<T> ? sig0[6 * row + c] : T(0);
     T b0 = T(0), b1 = T(0), b2 = T(0);
 #pragma unroll 2
     for (int k = 0; k < len; ++k) {
@@ -1429,14 +1549,14 @@ __global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, DSeg G, const T* __res
       const T* gp = vp + (int64_t)k * 96;
       const T g0 = __ldcs(gp), g1 = __ldcs(gp + 32), g2 = __ldcs(gp + 64);
       const T* sj = sig0 + 6 * j;
-      const T s11 = __ldg(sj), s22 = __ldg(sj + 1), s33 = __ldg(sj + 2), s23 = __ldg(sj + 3),
-              s13 = __ldg(sj + 4), s12 = __ldg(sj + 5);
+      const T s11 = __ldg(sj) - si[0], s22 = __ldg(sj + 1) - si[1], s33 = __ldg(sj + 2) - si[2],
+              s23 = __ldg(sj + 3) - si[3], s13 = __ldg(sj + 4) - si[4],
+              s12 = __ldg(sj + 5) - si[5];
       b0 += g0 * s11 + g1 * s12 + g2 * s13;
       b1 += g0 * s12 + g1 * s22 + g2 * s23;
       b2 += g0 * s13 + g1 * s23 + g2 * s33;
     }
-    const int64_t row = s * 32 + lane;
-    if (row < A.n) {
+    if (in) {
       const bool pz = pin_zero && row == G.seg_pin[G.seg_of_slice[s]];
       b[3 * row] = pz ? T(0) : b0;
       b[3 * row + 1] = pz ? T(0) : b1;
@@ -1691,7 +1811,7 @@ __global__ void __launch_bounds__(kBlock) k_project(DSeg G, ItemList IL, int64_t
     double v[1] = {0.0};
     const int64_t r0 = (int64_t)IL.sl0[item] * 32, r1 = (int64_t)IL.sl1[item] * 32;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      if (!mag[i]) continue;
+      if (!row_valid(G, seg, i) || !mag[i]) continue;
       const T a = x[i], b = x[ld + i], c = x[2 * ld + i];
       const T n2 = a * a + b * b + c * c;
       if (!(n2 > T(0)) || !isfinite(n2)) atomicAdd(bad + seg, 1);
@@ -1713,24 +1833,33 @@ __global__ void __launch_bounds__(kBlock) k_project(DSeg G, ItemList IL, int64_t
 // layout changes between the ABI ([n][nc] float64, unique-node order) and internal arrays;
 // perm[i] < 0 marks a padding row (no node)
 // ------------------------------------------------------------------------------------------
+// lo != NULL: the field is kept as an unevaluated sum dst + lo (the refined solutions of the
+// mixed path): dst = v rounded to T, lo = the rest
 template <typename T>
 __global__ void k_import(int64_t n, int nc, const double* __restrict__ src,
                          const int64_t* __restrict__ perm, T* __restrict__ dst, int64_t cs,
-                         int64_t ns, const uint8_t* __restrict__ mask) {
+                         int64_t ns, const uint8_t* __restrict__ mask, T* __restrict__ lo) {
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const int64_t o = perm[i];
     const bool z = o < 0 || (mask && !mask[i]);
-    for (int c = 0; c < nc; ++c) dst[i * ns + c * cs] = z ? T(0) : (T)src[o * nc + c];
+    for (int c = 0; c < nc; ++c) {
+      const double v = z ? 0.0 : src[o * nc + c];
+      const T h = (T)v;
+      dst[i * ns + c * cs] = h;
+      if (lo) lo[i * ns + c * cs] = (T)(v - (double)h);
+    }
   }
 }
 
 template <typename T>
 __global__ void k_export(int64_t n, int nc, const T* __restrict__ src, int64_t cs, int64_t ns,
-                         const int64_t* __restrict__ perm, double* __restrict__ dst) {
+                         const int64_t* __restrict__ perm, double* __restrict__ dst,
+                         const T* __restrict__ lo) {
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const int64_t o = perm[i];
     if (o < 0) continue;
-    for (int c = 0; c < nc; ++c) dst[o * nc + c] = (double)src[i * ns + c * cs];
+    for (int c = 0; c < nc; ++c)
+      dst[o * nc + c] = (double)src[i * ns + c * cs] + (lo ? (double)lo[i * ns + c * cs] : 0.0);
   }
 }
 
@@ -1834,33 +1963,35 @@ cudaError_t launch_wsum(const Launch& L, const DSeg& G, int nc, const T* f, int6
 }
 
 template <typename T, int VAR>
-static void spmv_variant(const Launch& L, const DSell& A, const T* val, int B, const T* x, T* y) {
+static void spmv_variant(const Launch& L, const DSell& A, const T* val, int B, const T* x, T* y,
+                         int diff) {
   const int64_t threads = (VAR == 2 ? 64 : 32) * A.nslices;
   if (B == 1) {
     auto k = k_spmv1<T, VAR>;
-    k<<<GSPM_GRID(L, threads, k), kBlock, 0, L.stream>>>(A, val, x, y);
+    k<<<GSPM_GRID(L, threads, k), kBlock, 0, L.stream>>>(A, val, x, y, diff);
   } else {
     auto k = k_spmv9<T, VAR>;
-    k<<<GSPM_GRID(L, threads, k), kBlock, 0, L.stream>>>(A, val, x, y);
+    k<<<GSPM_GRID(L, threads, k), kBlock, 0, L.stream>>>(A, val, x, y, diff);
   }
 }
 
 template <typename T>
 cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, const T* x, T* y,
-                        int variant) {
+                        int variant, int diff) {
   (*L.counter) += 1;
+  diff = diff && kDiff<T>;
   switch (variant) {
-    case 1: spmv_variant<T, 1>(L, A, val, B, x, y); break;
-    case 2: spmv_variant<T, 2>(L, A, val, B, x, y); break;
-    case 3: spmv_variant<T, 3>(L, A, val, B, x, y); break;
-    default: spmv_variant<T, 0>(L, A, val, B, x, y); break;
+    case 1: spmv_variant<T, 1>(L, A, val, B, x, y, diff); break;
+    case 2: spmv_variant<T, 2>(L, A, val, B, x, y, diff); break;
+    case 3: spmv_variant<T, 3>(L, A, val, B, x, y, diff); break;
+    default: spmv_variant<T, 0>(L, A, val, B, x, y, diff); break;
   }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
-                           const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
+                           const T* b, const T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
                            int max_iter, Red red, const double* bmean, int pinned, int pc) {
   (*L.counter) += 1;
   if (B == 1) {
@@ -1874,6 +2005,52 @@ cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const
     k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, r, p, st, nactive, rtol,
                                         max_iter, red, bmean, pinned, pc);
   }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_true_res(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
+                            const T* b, const T* x, const T* xlo, Red red, double* out) {
+  (*L.counter) += 1;
+  if (B == 1) {
+    auto k = k_true_res<T, 1>;
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, xlo, red, out);
+  } else {
+    auto k = k_true_res<T, 9>;
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    k<<<ig.grid, kBlock, 0, L.stream>>>(A, G, ig.list, val, b, x, xlo, red, out);
+  }
+  return cudaGetLastError();
+}
+
+// (hi, lo) <- hi + dx as an unevaluated sum: Knuth's TwoSum of hi and dx, so that hi + lo keeps
+// the correction below the last bit of hi (lo is zero on entry)
+template <typename T>
+__global__ void k_refine_add(int64_t len, T* __restrict__ hi, T* __restrict__ lo,
+                             const T* __restrict__ dx) {
+  for (int64_t i = gtid(); i < len; i += gstride()) {
+    const T a = hi[i], b = dx[i];
+    T s, e;
+    if constexpr (std::is_same<T, float>::value) {
+      s = __fadd_rn(a, b);
+      const T bp = __fsub_rn(s, a), ap = __fsub_rn(s, bp);
+      e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+    } else {
+      s = __dadd_rn(a, b);
+      const T bp = __dsub_rn(s, a), ap = __dsub_rn(s, bp);
+      e = __dadd_rn(__dsub_rn(a, ap), __dsub_rn(b, bp));
+    }
+    hi[i] = s;
+    lo[i] = e;
+  }
+}
+
+template <typename T>
+cudaError_t launch_refine_add(const Launch& L, int64_t len, T* hi, T* lo, const T* dx) {
+  (*L.counter) += 1;
+  auto k = k_refine_add<T>;
+  k<<<GSPM_GRID(L, len, k), kBlock, 0, L.stream>>>(len, hi, lo, dx);
   return cudaGetLastError();
 }
 
@@ -1912,39 +2089,42 @@ cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, co
 template <typename T, int VAR>
 static cudaError_t cg_spmv_variant(const Launch& L, const DSell& A, const DSeg& G, const T* val,
                                    int B, int nr, int64_t ld, const T* p, T* q, CGState* st,
-                                   Red red, int pinned) {
+                                   Red red, int pinned, int diff) {
   if (B == 9) {
-    auto k = k_cg_spmv<T, 9, 1, VAR>;
+    auto k = k_cg_spmv<T, 9, 1, VAR, kDiff<T>>;
+    const ItemGrid ig = GSPM_IGRID(L, G, k);
+    return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
+  } else if (nr == 1 && diff && kDiff<T>) {
+    auto k = k_cg_spmv<T, 1, 1, VAR, 1>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
     return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 1) {
-    auto k = k_cg_spmv<T, 1, 1, VAR>;
+    auto k = k_cg_spmv<T, 1, 1, VAR, 0>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
     return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 2) {
-    auto k = k_cg_spmv<T, 1, 2, VAR>;
+    auto k = k_cg_spmv<T, 1, 2, VAR, 0>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
     return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else if (nr == 3) {
-    auto k = k_cg_spmv<T, 1, 3, VAR>;
+    auto k = k_cg_spmv<T, 1, 3, VAR, 0>;
     const ItemGrid ig = GSPM_IGRID(L, G, k);
     return launch_pdl(k, ig.grid, L.stream, A, G, ig.list, val, ld, p, q, st, red, pinned);
   } else {
     return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
-                           int variant, int pinned) {
+                           int variant, int pinned, int diff) {
   (*L.counter) += 1;
   switch (variant) {
-    case 1: return cg_spmv_variant<T, 1>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
-    case 2: return cg_spmv_variant<T, 2>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
-    case 3: return cg_spmv_variant<T, 3>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
-    default: return cg_spmv_variant<T, 0>(L, A, G, val, B, nr, ld, p, q, st, red, pinned);
+    case 1: return cg_spmv_variant<T, 1>(L, A, G, val, B, nr, ld, p, q, st, red, pinned, diff);
+    case 2: return cg_spmv_variant<T, 2>(L, A, G, val, B, nr, ld, p, q, st, red, pinned, diff);
+    case 3: return cg_spmv_variant<T, 3>(L, A, G, val, B, nr, ld, p, q, st, red, pinned, diff);
+    default: return cg_spmv_variant<T, 0>(L, A, G, val, B, nr, ld, p, q, st, red, pinned, diff);
   }
 }
 
@@ -2123,21 +2303,22 @@ cudaError_t launch_fdiv(const Launch& L, const DSell& A, const DSeg& G, const T*
 }
 
 template <typename T>
-cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U,
+cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U, const T* Ulo,
                          const double* invML, T* hd, int64_t ld) {
   (*L.counter) += 1;
   auto k = k_fgrad<T>;
-  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, Fv, U, invML, hd, ld);
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, Fv, U, Ulo, invML, hd, ld);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fstrain(const Launch& L, const DSell& A, const DSeg& G, const T* Fv,
-                           const T* u, const double* invML, const double* Ebar, T* E,
-                           int64_t ld) {
+                           const T* u, const T* ulo, const double* invML, const double* Ebar,
+                           T* E, int64_t ld) {
   (*L.counter) += 1;
   auto k = k_fstrain<T>;
-  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Fv, u, invML, Ebar, E, ld);
+  k<<<GSPM_GRID(L, A.nslices * 32, k), kBlock, 0, L.stream>>>(A, G, Fv, u, ulo, invML, Ebar, E,
+                                                               ld);
   return cudaGetLastError();
 }
 
@@ -2203,19 +2384,19 @@ cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* 
 template <typename T>
 cudaError_t launch_import(const Launch& L, int64_t n, int nc, const double* src,
                           const int64_t* perm, T* dst, int64_t cs, int64_t ns,
-                          const uint8_t* mask) {
+                          const uint8_t* mask, T* lo) {
   (*L.counter) += 1;
   auto k = k_import<T>;
-  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, nc, src, perm, dst, cs, ns, mask);
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, nc, src, perm, dst, cs, ns, mask, lo);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_export(const Launch& L, int64_t n, int nc, const T* src, int64_t cs,
-                          int64_t ns, const int64_t* perm, double* dst) {
+                          int64_t ns, const int64_t* perm, double* dst, const T* lo) {
   (*L.counter) += 1;
   auto k = k_export<T>;
-  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, nc, src, cs, ns, perm, dst);
+  k<<<GSPM_GRID(L, n, k), kBlock, 0, L.stream>>>(n, nc, src, cs, ns, perm, dst, lo);
   return cudaGetLastError();
 }
 
@@ -2249,10 +2430,13 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
                                       int64_t, const int64_t*, const double*, double*,            \
                                       const double*, Red);                                        \
   template cudaError_t launch_spmv<T>(const Launch&, const DSell&, const T*, int, const T*, T*,   \
-                                      int);                                                       \
+                                      int, int);                                                  \
   template cudaError_t launch_cg_init<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
-                                         const T*, T*, T*, T*, CGState*, int*, double, int, Red,  \
+                                         const T*, const T*, T*, T*, CGState*, int*, double, int, Red,  \
                                          const double*, int, int);                                \
+  template cudaError_t launch_true_res<T>(const Launch&, const DSell&, const DSeg&, const T*, int,  \
+                                          const T*, const T*, const T*, Red, double*);            \
+  template cudaError_t launch_refine_add<T>(const Launch&, int64_t, T*, T*, const T*);            \
   template cudaError_t launch_restrict<T>(const Launch&, const DCoarse&, int, const T*,           \
                                           const int64_t*, T*);                                    \
   template cudaError_t launch_coarse_symv<T>(const Launch&, const DCoarse&, const DSymTiles&, int, \
@@ -2264,7 +2448,7 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
                                             const T*, int, int64_t, T*, T*, T*, CGState*, int*,   \
                                             double, int, Red, const T*);                          \
   template cudaError_t launch_cg_spmv<T>(const Launch&, const DSell&, const DSeg&, const T*, int, \
-                                         int, int64_t, const T*, T*, CGState*, Red, int, int);    \
+                                         int, int64_t, const T*, T*, CGState*, Red, int, int, int); \
   template cudaError_t launch_cg_update<T>(const Launch&, const DSeg&, int, int, int64_t, T*, T*, \
                                            const T*, const T*, CGState*, int*, Red, const T*);    \
   template cudaError_t launch_cg_pupdate<T>(const Launch&, const DSeg&, int, int, int64_t,        \
@@ -2273,10 +2457,11 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
   template cudaError_t launch_cg_zero<T>(const Launch&, const DSeg&, int, T*, const CGState*);    \
   template cudaError_t launch_fdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
                                       const T*, int64_t, T*, int);                                \
-  template cudaError_t launch_fgrad<T>(const Launch&, const DSell&, const T*, const T*,           \
+  template cudaError_t launch_fgrad<T>(const Launch&, const DSell&, const T*, const T*, const T*, \
                                        const double*, T*, int64_t);                               \
   template cudaError_t launch_fstrain<T>(const Launch&, const DSell&, const DSeg&, const T*,      \
-                                         const T*, const double*, const double*, T*, int64_t);    \
+                                         const T*, const T*, const double*, const double*, T*,    \
+                                         int64_t);                                                \
   template cudaError_t launch_gdiv<T>(const Launch&, const DSell&, const DSeg&, const T*,         \
                                       const T*, T*, int);                                         \
   template cudaError_t launch_pin_shift<T>(const Launch&, const DSell&, const DSeg&, int, T*,     \
@@ -2297,9 +2482,9 @@ cudaError_t launch_scaled_diff(const Launch& L, int64_t len, const T* a, const T
   template cudaError_t launch_project<T>(const Launch&, const DSeg&, int64_t, const T*,           \
                                          const uint8_t*, T*, double*, const double*, Red, int*);  \
   template cudaError_t launch_import<T>(const Launch&, int64_t, int, const double*,               \
-                                        const int64_t*, T*, int64_t, int64_t, const uint8_t*);    \
+                                        const int64_t*, T*, int64_t, int64_t, const uint8_t*, T*); \
   template cudaError_t launch_export<T>(const Launch&, int64_t, int, const T*, int64_t, int64_t,  \
-                                        const int64_t*, double*);                                 \
+                                        const int64_t*, double*, const T*);                       \
   template cudaError_t launch_extrapolate<T>(const Launch&, int64_t, T*, T*);                     \
   template cudaError_t launch_scaled_diff<T>(const Launch&, int64_t, const T*, const T*,          \
                                              const T*, double, float*);

@@ -134,7 +134,9 @@ cudaError_t launch_wsum(const Launch& L, const DSeg& G, int nc, const T* f, int6
                         const double* add, Red red);  // out[seg * nc + c]
 template <typename T>
 cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, const T* x,
-                        T* y, int variant = 0);  // B = 1 scalar, B = 9 block (x, y AoS 3)
+                        T* y, int variant = 0, int diff = 0);  // B = 1 scalar, B = 9 block
+// (x, y AoS 3); diff != 0: the operator's rows sum to zero (K^ms, K^mech) and each row is
+// formed as sum_j A_ij (x_j - x_i)
 // CG pieces.  st and the arrival counters are per segment; nactive counts active segments.
 // epr = elements per row of the vectors (1: scalar, SoA with stride ld; 3: [n][3]).
 // bmean != NULL: solve the consistent singular system with b projected off the constants
@@ -146,9 +148,18 @@ cudaError_t launch_spmv(const Launch& L, const DSell& A, const T* val, int B, co
 // pinned: the pinned system (Sec. 2.5).
 template <typename T>
 cudaError_t launch_cg_init(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
-                           const T* b, T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
+                           const T* b, const T* x, T* r, T* p, CGState* st, int* nactive, double rtol,
                            int max_iter, Red red, const double* bmean, int pinned, int pc);
 // dinv != NULL: Jacobi-preconditioned CG (p = z = D^-1 r, fused into update and p-update)
+// ||b - A x||^2 and ||b||^2 per segment over the rows but the pinned one, A x accumulated in
+// FP64 (B = 1: K^ms, x and b [n]; B = 9: K^mech, [n][3]): out[2 seg], out[2 seg + 1]
+template <typename T>
+cudaError_t launch_true_res(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
+                            const T* b, const T* x, const T* xlo, Red red, double* out);
+// (hi, lo) <- hi + dx (TwoSum, lo zero on entry), len elements: the refined solutions of the
+// mixed path are unevaluated sums hi + lo
+template <typename T>
+cudaError_t launch_refine_add(const Launch& L, int64_t len, T* hi, T* lo, const T* dx);
 template <typename T>
 cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, const T* aval,
                               const T* mval, int nr, int64_t ld, T* x, T* r, T* p, CGState* st,
@@ -156,7 +167,7 @@ cudaError_t launch_cg_init_gs(const Launch& L, const DSell& A, const DSeg& G, co
 template <typename T>
 cudaError_t launch_cg_spmv(const Launch& L, const DSell& A, const DSeg& G, const T* val, int B,
                            int nr, int64_t ld, const T* p, T* q, CGState* st, Red red,
-                           int variant, int pinned);
+                           int variant, int pinned, int diff);
 // x(i, c) -= x(pin of i's segment, c) for x[i * epr + c]; xp: nseg * epr doubles of scratch
 template <typename T>
 cudaError_t launch_pin_shift(const Launch& L, const DSell& A, const DSeg& G, int epr, T* x,
@@ -240,12 +251,12 @@ template <typename T>
 cudaError_t launch_fdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Fv, const T* m,
                         int64_t ld, T* b, int pin_zero);
 template <typename T>
-cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U,
+cudaError_t launch_fgrad(const Launch& L, const DSell& A, const T* Fv, const T* U, const T* Ulo,
                          const double* invML, T* hd, int64_t ld);
 template <typename T>
 cudaError_t launch_fstrain(const Launch& L, const DSell& A, const DSeg& G, const T* Fv,
-                           const T* u, const double* invML, const double* Ebar, T* E,
-                           int64_t ld);
+                           const T* u, const T* ulo, const double* invML, const double* Ebar,
+                           T* E, int64_t ld);
 template <typename T>
 cudaError_t launch_gdiv(const Launch& L, const DSell& A, const DSeg& G, const T* Gv,
                         const T* sig0, T* b, int pin_zero);
@@ -274,10 +285,10 @@ cudaError_t launch_project(const Launch& L, const DSeg& G, int64_t ld, const T* 
 template <typename T>
 cudaError_t launch_import(const Launch& L, int64_t n, int nc, const double* src,
                           const int64_t* perm, T* dst, int64_t cs, int64_t ns,
-                          const uint8_t* mask);
+                          const uint8_t* mask, T* lo = nullptr);
 template <typename T>
 cudaError_t launch_export(const Launch& L, int64_t n, int nc, const T* src, int64_t cs,
-                          int64_t ns, const int64_t* perm, double* dst);
+                          int64_t ns, const int64_t* perm, double* dst, const T* lo = nullptr);
 template <typename S, typename D>
 cudaError_t launch_convert(const Launch& L, int64_t len, const S* src, D* dst);
 template <typename T>

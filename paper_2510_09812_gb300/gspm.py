@@ -22,7 +22,8 @@ FLAG_HOST_ONLY, FLAG_ROW2_PRINTED, FLAG_NO_AUTOTUNE, FLAG_GRAPH, FLAG_PINNED_CG 
 FLAG_RESOLVE_AT_MSTAR, FLAG_PLAIN_CG = 32, 64
 (EXPORT_UNIQUE_OF_STORED, EXPORT_ROWPTR, EXPORT_COLS, EXPORT_PERM, EXPORT_NODE_MAGNETIC,
  EXPORT_LUMPED_MASS, EXPORT_AGGREGATES, EXPORT_COARSE_K_MS, EXPORT_COARSE_K_MECH,
- EXPORT_COARSE_INV_MS, EXPORT_COARSE_INV_MECH) = range(11)
+ EXPORT_COARSE_INV_MS, EXPORT_COARSE_INV_MECH, EXPORT_COARSE_STORED_MS,
+ EXPORT_COARSE_STORED_MECH) = range(13)
 FIELD_M, FIELD_U, FIELD_DISP, FIELD_HD, FIELD_STRAIN, FIELD_H, FIELD_DISP_PREV = range(7)
 X0_PREV, X0_ZERO, X0_EXTRAPOLATE, X0_LEARNED = range(4)
 MPNN_PARAMS = 26051
@@ -30,12 +31,11 @@ MPNN_KEYS = [("W_in", (16, 64)), ("b_in", (64,)), ("W1", (128, 64)), ("b1", (64,
              ("W2", (128, 64)), ("b2", (64,)), ("W3", (128, 64)), ("b3", (64,)),
              ("W_out", (64, 3)), ("b_out", (3,))]
 OP_K_MS, OP_A_EPS, OP_A_AEPS, OP_M, OP_K_MECH, OP_DIV, OP_GRAD = range(7)
-KCLASS_NAMES = ["spmv_mech", "spmv_gs", "spmv_ms", "cg_vec", "cg_init", "rowops", "pointwise"]
+KCLASS_NAMES = ["spmv_mech", "spmv_gs", "spmv_ms", "cg_vec", "cg_init", "rhs_ms", "pointwise",
+                "learned", "grad_ms", "rhs_mech", "strain"]
 KCLASS = {name: k for k, name in enumerate(KCLASS_NAMES)}
 FIELD_NCOMP = {FIELD_M: 3, FIELD_U: 1, FIELD_DISP: 3, FIELD_HD: 3, FIELD_STRAIN: 6, FIELD_H: 3,
                FIELD_DISP_PREV: 3}
-KCLASS_NAMES.append("learned")
-KCLASS["learned"] = 7
 
 _dp = C.POINTER(C.c_double)
 
@@ -70,7 +70,8 @@ class MeshInfo(C.Structure):
                 ("device_bytes", C.c_int64), ("n_segments", C.c_int), ("item_slices", C.c_int),
                 ("spmv_schedule_block", C.c_int),
                 ("spmv_schedule_scalar", C.c_int), ("spmv_ms_block", C.c_double * 4),
-                ("spmv_ms_scalar", C.c_double * 4), ("n_aggregates", C.c_int64)]
+                ("spmv_ms_scalar", C.c_double * 4), ("n_aggregates", C.c_int64),
+                ("coarse_shift_ms", C.c_double), ("coarse_shift_mech", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -78,7 +79,8 @@ class StepStats(C.Structure):
                 ("it_gs", C.c_int64), ("it_ms_last", C.c_int), ("it_mech_last", C.c_int),
                 ("it_gs_last", C.c_int * 8), ("res_ms_last", C.c_double),
                 ("res_mech_last", C.c_double), ("dm_last", C.c_double),
-                ("m_bar", C.c_double * 3), ("noconv", C.c_int)]
+                ("m_bar", C.c_double * 3), ("noconv", C.c_int),
+                ("true_res_ms_last", C.c_double), ("true_res_mech_last", C.c_double)]
 
 
 def _load():
@@ -107,6 +109,9 @@ def _load():
         "gspm_volume_avg_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, vp, vp]),
         "gspm_set_x0_mode": (C.c_int, [vp, C.c_int]),
         "gspm_set_graph": (C.c_int, [vp, C.c_int]),
+        "gspm_set_true_residual": (C.c_int, [vp, C.c_int]),
+        "gspm_set_rtol": (C.c_int, [vp, C.c_double, C.c_double, C.c_double]),
+        "gspm_coarse_round": (C.c_int, [_dp, C.c_int64, C.c_int, _dp, _dp]),
         "gspm_batch_load": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
                                       C.POINTER(Options), C.POINTER(vp)]),
         "gspm_batch_segment": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int64),
@@ -274,7 +279,9 @@ class Context:
                        EXPORT_COARSE_K_MS: (inf["n_aggregates"] ** 2, np.float64),
                        EXPORT_COARSE_K_MECH: (9 * inf["n_aggregates"] ** 2, np.float64),
                        EXPORT_COARSE_INV_MS: (inf["n_aggregates"] ** 2, np.float64),
-                       EXPORT_COARSE_INV_MECH: (9 * inf["n_aggregates"] ** 2, np.float64)}[what]
+                       EXPORT_COARSE_INV_MECH: (9 * inf["n_aggregates"] ** 2, np.float64),
+                       EXPORT_COARSE_STORED_MS: (inf["n_aggregates"] ** 2, np.float64),
+                       EXPORT_COARSE_STORED_MECH: (9 * inf["n_aggregates"] ** 2, np.float64)}[what]
         out = np.empty(size, dtype=dtype)
         _check(lib.gspm_mesh_export(self._h, what, C.c_void_p(out.ctypes.data), size),
                "gspm_mesh_export")
@@ -379,6 +386,16 @@ class Context:
         """Replay each step as one captured CUDA graph (``gspm_set_graph``)."""
         _check(lib.gspm_set_graph(self._h, int(bool(on))), "gspm_set_graph")
 
+    def set_true_residual(self, on: bool):
+        """Report ||b - K x|| / ||b|| of the last K^ms / K^mech solves in the step stats
+        (``gspm_set_true_residual``)."""
+        _check(lib.gspm_set_true_residual(self._h, int(bool(on))), "gspm_set_true_residual")
+
+    def set_rtol(self, rtol_gs=0.0, rtol_ms=0.0, rtol_mech=0.0):
+        """New CG stopping tolerances for the following steps (<= 0 keeps one)."""
+        _check(lib.gspm_set_rtol(self._h, float(rtol_gs), float(rtol_ms), float(rtol_mech)),
+               "gspm_set_rtol")
+
     def set_x0_mode(self, mode: int):
         _check(lib.gspm_set_x0_mode(self._h, int(mode)), "gspm_set_x0_mode")
 
@@ -448,6 +465,18 @@ class Context:
         k = KCLASS[cls] if isinstance(cls, str) else int(cls)
         _check(lib.gspm_profile_read(self._h, k, C.byref(ms), C.byref(cnt)), "gspm_profile_read")
         return ms.value, cnt.value
+
+
+def coarse_round(A, bf16: bool):
+    """gspm_coarse_round: the storage of a dense SPD matrix as the coarse inverse (host code).
+    Returns (stored values as float64 [n][n], diagonal shift used)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    out = np.empty((n, n))
+    sh = C.c_double()
+    _check(lib.gspm_coarse_round(A.ctypes.data_as(_dp), n, int(bool(bf16)),
+                                 out.ctypes.data_as(_dp), C.byref(sh)), "gspm_coarse_round")
+    return out, sh.value
 
 
 def flatten_params(p: dict) -> np.ndarray:

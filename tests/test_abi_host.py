@@ -174,3 +174,68 @@ def test_host_coarse_operators_and_inverses(gspm_lib, ordering):
         inv = ctx.export(ei).reshape(nc, nc)
         assert np.abs(inv - inv.T).max() < 1e-12 * np.abs(inv).max()
         assert np.abs(A @ inv - np.eye(nc)).max() < 1e-10
+
+
+def _bf16_np(x):
+    """Round to bfloat16 (nearest even of the FP32 value), as float64: written from the format's
+    definition (sign, 8 exponent bits, 7 fraction bits), independently of the library."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_stored_coarse_inverses_are_positive_definite(gspm_lib, precision):
+    """The device keeps the coarse inverses rounded to its storage type (BF16 under mixed
+    precision).  Host-only contexts export the stored values: they are the rounding of the
+    symmetric part of the FP64 inverse (no shift needed on a real mesh) and pass a Cholesky
+    factorisation, so the preconditioner stays symmetric positive definite."""
+    g = gspm_lib
+    spec = MESHES[1]
+    mesh = synth.kuhn_box(spec["cells"], spec["box"], jitter=spec["jitter"], seed=spec["seed"],
+                          defects=spec["defects"])
+    ctx = g.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, precision=precision,
+                    host_only=True, coarse_nodes=8)
+    info = ctx.info()
+    na = info["n_aggregates"]
+    assert na > 16
+    assert info["coarse_shift_ms"] == 0.0 and info["coarse_shift_mech"] == 0.0
+    for ei, es, nc in ((g.EXPORT_COARSE_INV_MS, g.EXPORT_COARSE_STORED_MS, na),
+                       (g.EXPORT_COARSE_INV_MECH, g.EXPORT_COARSE_STORED_MECH, 3 * na)):
+        inv = ctx.export(ei).reshape(nc, nc)
+        st = ctx.export(es).reshape(nc, nc)
+        sym = 0.5 * (inv + inv.T)
+        expect = _bf16_np(sym) if precision == "mixed" else sym
+        assert np.array_equal(st, expect)
+        np.linalg.cholesky(st)  # raises if not positive definite
+        if precision == "mixed":
+            assert np.abs(st - sym).max() <= 2.0 ** -8 * np.abs(sym).max()
+
+
+def test_coarse_round_shifts_an_indefinite_rounding(gspm_lib):
+    """A symmetric positive definite matrix whose smallest eigenvalue lies far below the BF16
+    rounding of its entries: the rounded matrix is indefinite, so the rule adds the smallest
+    accepted diagonal shift 2^k * 2^-8 max A_ii before rounding; the result is positive
+    definite.  In FP64 storage the matrix is kept as it is (its symmetric part)."""
+    g = gspm_lib
+    rng = np.random.default_rng(5)
+    n = 96
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.geomspace(1e-7, 1.0, n)
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    assert np.linalg.eigvalsh(_bf16_np(A))[0] < 0.0  # plain rounding is indefinite
+    st, shift = g.coarse_round(A, bf16=True)
+    base = 2.0 ** -8 * np.abs(np.diag(A)).max()
+    k = np.log2(shift / base)
+    assert shift > 0.0 and abs(k - round(k)) < 1e-12
+    assert np.array_equal(st, _bf16_np(A + shift * np.eye(n)))
+    np.linalg.cholesky(st)
+    if shift > base:  # the next smaller shift was rejected
+        assert np.linalg.eigvalsh(_bf16_np(A + 0.5 * shift * np.eye(n)))[0] <= 0.0
+    st64, sh64 = g.coarse_round(A, bf16=False)
+    assert sh64 == 0.0 and np.array_equal(st64, A)
+    with pytest.raises(g.GSPMError) as e:
+        g.coarse_round(-np.eye(4), bf16=True)
+    assert e.value.code == g.EMESH
