@@ -1395,6 +1395,24 @@ __global__ void k_cg_zero(DSeg G, ItemList IL, int epr, T* x, const CGState* st)
   }
 }
 
+// One round of a row kernel over the F^ms / G values (three per entry): kRowRound neighbours'
+// columns and values loaded before any gather, so each lane has that many independent loads in
+// flight (entries past the row's length give column 0 and value 0).
+constexpr int kRowRound = 5;
+template <typename T>
+__device__ __forceinline__ void row_round(const int32_t* cp, const T* vp, int kb, int len,
+                                          int (&j)[kRowRound], T (&f)[kRowRound][3]) {
+#pragma unroll
+  for (int u = 0; u < kRowRound; ++u) {
+    const int k = kb + u;
+    const bool ok = k < len;
+    j[u] = ok ? __ldcs(cp + (int64_t)k * 32) : 0;
+    const T* fp = vp + (int64_t)(ok ? k : 0) * 96;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[u][a] = ok ? __ldcs(fp + 32 * a) : T(0);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // F^ms / G operators (Sec. 2.3): right-hand sides and derivatives as row gathers
 // ------------------------------------------------------------------------------------------
@@ -1423,12 +1441,14 @@ __global__ void __launch_bounds__(kBlock) k_fdiv(DSell A, DSeg G, const T* __res
     const T m0 = own ? m[row] : T(0), m1 = own ? m[ld + row] : T(0),
             m2 = own ? m[2 * ld + row] : T(0);
     T acc = T(0);
-#pragma unroll 4
-    for (int k = 0; k < len; ++k) {
-      const int64_t j = __ldcs(cp + (int64_t)k * 32);
-      const T* fp = vp + (int64_t)k * 96;
-      acc += __ldcs(fp) * (__ldg(m + j) - m0) + __ldcs(fp + 32) * (__ldg(m + ld + j) - m1) +
-             __ldcs(fp + 64) * (__ldg(m + 2 * ld + j) - m2);
+    for (int kb = 0; kb < len; kb += kRowRound) {
+      int j[kRowRound];
+      T f[kRowRound][3];
+      row_round(cp, vp, kb, len, j, f);
+#pragma unroll
+      for (int u = 0; u < kRowRound; ++u)
+        acc += f[u][0] * (__ldg(m + j[u]) - m0) + f[u][1] * (__ldg(m + ld + j[u]) - m1) +
+               f[u][2] * (__ldg(m + 2 * ld + j[u]) - m2);
     }
     if (in) b[row] = pin_zero && row == G.seg_pin[G.seg_of_slice[s]] ? T(0) : acc;
   }
@@ -1452,14 +1472,17 @@ __global__ void __launch_bounds__(kBlock) k_fgrad(DSell A, const T* __restrict__
     const T ui = kDiff<T> && row < A.n ? U[row] : T(0);
     const T uil = Ulo && row < A.n ? Ulo[row] : T(0);
     T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll 4
-    for (int k = 0; k < len; ++k) {
-      const int64_t j = __ldcs(cp + (int64_t)k * 32);
-      const T* fp = vp + (int64_t)k * 96;
-      const T u = ((T)__ldg(U + j) - ui) + (Ulo ? __ldg(Ulo + j) - uil : T(0));
-      a0 += __ldcs(fp) * u;
-      a1 += __ldcs(fp + 32) * u;
-      a2 += __ldcs(fp + 64) * u;
+    for (int kb = 0; kb < len; kb += kRowRound) {
+      int j[kRowRound];
+      T f[kRowRound][3];
+      row_round(cp, vp, kb, len, j, f);
+#pragma unroll
+      for (int u = 0; u < kRowRound; ++u) {
+        const T du = ((T)__ldg(U + j[u]) - ui) + (Ulo ? __ldg(Ulo + j[u]) - uil : T(0));
+        a0 += f[u][0] * du;
+        a1 += f[u][1] * du;
+        a2 += f[u][2] * du;
+      }
     }
     if (row < A.n) {
       const T im = (T)invML[row];
@@ -1495,21 +1518,24 @@ __global__ void __launch_bounds__(kBlock) k_fstrain(DSell A, DSeg G, const T* __
     const T uil[3] = {lo ? ulo[3 * row] : T(0), lo ? ulo[3 * row + 1] : T(0),
                       lo ? ulo[3 * row + 2] : T(0)};
     T g[3][3] = {};
-#pragma unroll 2
-    for (int k = 0; k < len; ++k) {
-      const int64_t j = __ldcs(cp + (int64_t)k * 32);
-      const T* fp = vp + (int64_t)k * 96;
-      const T f[3] = {__ldcs(fp), __ldcs(fp + 32), __ldcs(fp + 64)};
-      T uj[3] = {(T)__ldg(u + 3 * j) - ui[0], (T)__ldg(u + 3 * j + 1) - ui[1],
-                 (T)__ldg(u + 3 * j + 2) - ui[2]};
-      if (ulo) {
+    for (int kb = 0; kb < len; kb += kRowRound) {
+      int j[kRowRound];
+      T f[kRowRound][3];
+      row_round(cp, vp, kb, len, j, f);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) uj[b] += __ldg(ulo + 3 * j + b) - uil[b];
+      for (int q = 0; q < kRowRound; ++q) {
+        const T* uq = u + 3 * (int64_t)j[q];
+        T uj[3] = {uq[0] - ui[0], uq[1] - ui[1], uq[2] - ui[2]};
+        if (ulo) {
+          const T* lq = ulo + 3 * (int64_t)j[q];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) uj[b] += lq[b] - uil[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) g[a][b] += f[q][a] * uj[b];
       }
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) g[a][b] += f[a] * uj[b];
     }
     if (in) {
       const double* eb = Ebar + 6 * G.seg_of_slice[s];
@@ -1543,18 +1569,21 @@ __global__ void __launch_bounds__(kBlock) k_gdiv(DSell A, DSeg G, const T* __res
 #pragma unroll
     for (int c = 0; c < 6; ++c) si[c] = in && kDiff<T> ? sig0[6 * row + c] : T(0);
     T b0 = T(0), b1 = T(0), b2 = T(0);
-#pragma unroll 2
-    for (int k = 0; k < len; ++k) {
-      const int64_t j = __ldcs(cp + (int64_t)k * 32);
-      const T* gp = vp + (int64_t)k * 96;
-      const T g0 = __ldcs(gp), g1 = __ldcs(gp + 32), g2 = __ldcs(gp + 64);
-      const T* sj = sig0 + 6 * j;
-      const T s11 = __ldg(sj) - si[0], s22 = __ldg(sj + 1) - si[1], s33 = __ldg(sj + 2) - si[2],
-              s23 = __ldg(sj + 3) - si[3], s13 = __ldg(sj + 4) - si[4],
-              s12 = __ldg(sj + 5) - si[5];
-      b0 += g0 * s11 + g1 * s12 + g2 * s13;
-      b1 += g0 * s12 + g1 * s22 + g2 * s23;
-      b2 += g0 * s13 + g1 * s23 + g2 * s33;
+    for (int kb = 0; kb < len; kb += kRowRound) {
+      int j[kRowRound];
+      T gv[kRowRound][3];
+      row_round(cp, vp, kb, len, j, gv);
+#pragma unroll
+      for (int q = 0; q < kRowRound; ++q) {
+        const T* sj = sig0 + 6 * (int64_t)j[q];
+        const T g0 = gv[q][0], g1 = gv[q][1], g2 = gv[q][2];
+        const T s11 = __ldg(sj) - si[0], s22 = __ldg(sj + 1) - si[1],
+                s33 = __ldg(sj + 2) - si[2], s23 = __ldg(sj + 3) - si[3],
+                s13 = __ldg(sj + 4) - si[4], s12 = __ldg(sj + 5) - si[5];
+        b0 += g0 * s11 + g1 * s12 + g2 * s13;
+        b1 += g0 * s12 + g1 * s22 + g2 * s23;
+        b2 += g0 * s13 + g1 * s23 + g2 * s33;
+      }
     }
     if (in) {
       const bool pz = pin_zero && row == G.seg_pin[G.seg_of_slice[s]];
