@@ -117,11 +117,16 @@ extern "C" {
 typedef struct gspm_mesh_desc {
   int64_t n_nodes;               /* stored nodes (periodic images included)                    */
   const double* coords;          /* host, [n_nodes][3], nm                                      */
-  int64_t n_tets;
-  const int32_t* tets;           /* host, [n_tets][4], stored-node indices, det(J) > 0          */
+  int64_t n_tets;                /* elements                                                    */
+  const int32_t* tets;           /* host, [n_tets][nodes_per_elem], stored-node indices         */
   const uint8_t* elem_magnetic;  /* host, [n_tets]: 1 ferromagnetic host, 0 defect; NULL = all 1 */
   double box_lo[3], box_hi[3];   /* periodic box (nm); faces at box_hi wrap onto box_lo         */
   double wrap_tol;               /* nm; <= 0 selects 1e-6 x the shortest element edge           */
+  int32_t nodes_per_elem;        /* 4 (or 0): linear tetrahedra, det J > 0; 8: linear
+                                    (trilinear) hexahedra, vertices at reference corners
+                                    (-,-,-) (+,-,-) (+,+,-) (-,+,-) (-,-,+) (+,-,+) (+,+,+)
+                                    (-,+,+) in that order, det J > 0 at the 2x2x2 Gauss points,
+                                    integrals by 2x2x2 Gauss quadrature (Sec. 2.4)             */
 } gspm_mesh_desc;
 
 typedef struct gspm_material {
@@ -401,7 +406,8 @@ GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights,
  * m (3), E0(m) in Voigt order / lambda_s (6), u_prev / u_s (3), (u_prev - u_prev2) / u_s (3), 1,
  * with lambda_s = max(|lambda100|, |lambda111|) and u_s = lambda_s * (V(Omega_c)/n)^(1/3).
  * h0 = relu(f W_in + b_in); three layers h_l = relu([h, A h] W_l + b_l) with A the
- * element-message average (A_ij = sum_{e containing i,j} V_e / (16 M_L,i)); y = h3 W_out + b_out.
+ * element-message average (A_ij = sum_{e containing i,j} V_e / k over sum_{e containing i} V_e,
+ * k the element's vertices; V_e / (16 M_L,i) on tetrahedra); y = h3 W_out + b_out.
  * Prediction x0 = 2 u_prev - u_prev2 + u_s y.  Inference runs on the tensor cores (BF16 weights
  * and activations, FP32 accumulation); training (backward, Adam) in FP32.  CG still runs to the
  * same residual, so the prediction only changes the iteration count.

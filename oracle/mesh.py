@@ -10,11 +10,12 @@ import numpy as np
 
 
 def default_wrap_tol(coords: np.ndarray, tets: np.ndarray) -> float:
-    """1e-6 of the shortest element edge (absolute, in the coordinates' unit)."""
+    """1e-6 of the shortest distance between two vertices of an element."""
     X = coords[tets]
+    k = tets.shape[1]
     e = []
-    for a in range(4):
-        for b in range(a + 1, 4):
+    for a in range(k):
+        for b in range(a + 1, k):
             e.append(np.linalg.norm(X[:, a] - X[:, b], axis=1).min())
     return 1e-6 * float(min(e))
 
@@ -107,6 +108,44 @@ def element_geometry(coords: np.ndarray, tets: np.ndarray):
     return det / 6.0, grads, det
 
 
+# Linear hexahedron: reference corners s_a in the element's vertex order, 2x2x2 Gauss points
+# xi_q = s_q / sqrt(3) with unit weights
+HEX_SIGNS = np.array([(-1, -1, -1), (1, -1, -1), (1, 1, -1), (-1, 1, -1), (-1, -1, 1),
+                      (1, -1, 1), (1, 1, 1), (-1, 1, 1)], dtype=np.float64)
+HEX_GAUSS = HEX_SIGNS / np.sqrt(3.0)
+
+
+def hex_shape(xi):
+    """N_a(xi) = prod_d (1 + s_a,d xi_d) / 2 for points xi [..., 3] -> [..., 8]."""
+    xi = np.asarray(xi, dtype=np.float64)
+    return np.prod(0.5 * (1.0 + HEX_SIGNS * xi[..., None, :]), axis=-1)
+
+
+def hex_shape_dxi(xi):
+    """dN_a / dxi_d at points xi [..., 3] -> [..., 8, 3]."""
+    xi = np.asarray(xi, dtype=np.float64)
+    f = 0.5 * (1.0 + HEX_SIGNS * xi[..., None, :])           # [..., 8, 3]
+    out = np.empty(f.shape)
+    for d in range(3):
+        others = [e for e in range(3) if e != d]
+        out[..., d] = 0.5 * HEX_SIGNS[:, d] * f[..., others[0]] * f[..., others[1]]
+    return out
+
+
+def hex_geometry(coords: np.ndarray, hexes: np.ndarray):
+    """Trilinear hexahedron geometry at the 2x2x2 Gauss points from the stored vertices:
+    J_q = sum_a x_a (x) dN_a/dxi (J_ij = dx_i / dxi_j), weights w_eq = det J_q, physical
+    gradients grad N_a = J_q^-T dN_a/dxi.  Returns (w [Ne, 8], N [8 q, 8 a], G [Ne, 8 q, 8 a, 3],
+    detJ [Ne, 8])."""
+    X = coords[hexes]                                           # [Ne, 8, 3]
+    dN = hex_shape_dxi(HEX_GAUSS)                              # [8 q, 8 a, 3]
+    J = np.einsum("eai,qaj->eqij", X, dN)
+    det = np.linalg.det(J)
+    Jinv = np.linalg.inv(J)                                    # [Ne, 8, 3, 3] (j, i)
+    G = np.einsum("qaj,eqji->eqai", dN, Jinv)
+    return det, hex_shape(HEX_GAUSS), G, det
+
+
 def magnetic_nodes(tets_u: np.ndarray, elem_magnetic: np.ndarray, n: int) -> np.ndarray:
     """A node carries magnetisation iff it belongs to at least one ferromagnetic element."""
     mask = np.zeros(n, dtype=bool)
@@ -115,7 +154,9 @@ def magnetic_nodes(tets_u: np.ndarray, elem_magnetic: np.ndarray, n: int) -> np.
 
 
 class WrappedMesh:
-    """A stored mesh after the periodic wrap, with per-element geometry."""
+    """A stored mesh after the periodic wrap, with per-element geometry: linear tetrahedra
+    (``tets`` [Ne, 4]; V, grads, detJ) or trilinear hexahedra (``tets`` [Ne, 8]; Gauss weights
+    gw [Ne, 8], shape values gN [8, 8], gradients gG [Ne, 8, 8, 3], V = sum of the weights)."""
 
     def __init__(self, coords, tets, elem_magnetic, box_lo, box_hi, tol=None):
         coords = np.asarray(coords, dtype=np.float64)
@@ -123,12 +164,20 @@ class WrappedMesh:
         if tol is None or tol <= 0:
             tol = default_wrap_tol(coords, tets)
         self.tol = tol
+        self.nen = tets.shape[1]
         self.unique_of_stored, self.n = periodic_wrap(coords, box_lo, box_hi, tol)
         self.tets = self.unique_of_stored[tets]                  # wrapped connectivity
         self.elem_magnetic = np.asarray(elem_magnetic).astype(bool)
-        self.V, self.grads, self.detJ = element_geometry(coords, tets)
-        if np.any(self.detJ <= 0):
-            raise ValueError("mesh has a non-positively oriented tetrahedron")
+        if self.nen == 8:
+            self.gw, self.gN, self.gG, self.detJ = hex_geometry(coords, tets)
+            self.V = self.gw.sum(axis=1)
+            self.grads = None
+            if np.any(self.detJ <= 0):
+                raise ValueError("mesh has a hexahedron with det J <= 0 at a Gauss point")
+        else:
+            self.V, self.grads, self.detJ = element_geometry(coords, tets)
+            if np.any(self.detJ <= 0):
+                raise ValueError("mesh has a non-positively oriented tetrahedron")
         self.node_magnetic = magnetic_nodes(self.tets, self.elem_magnetic, self.n)
         self.volume = float(self.V.sum())
 

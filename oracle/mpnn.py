@@ -7,7 +7,9 @@ network is the build's own design and this file is its reference definition.
 Network (hidden width 64, three message-passing layers):
   messages   element message = mean of its 4 vertex features; a node receives the
              volume-weighted mean of the messages of its elements:
-             z_i = sum_j A_ij h_j,  A_ij = (sum_{e containing i and j} V_e / 4) / (4 M_L,i)
+             z_i = sum_j A_ij h_j,  A_ij = (sum_{e containing i and j} V_e / k) /
+             (sum_{e containing i} V_e), k the vertices per element (on tetrahedra the
+             denominator is 4 M_L,i)
   input      h0 = relu(f W_in + b_in)                     f: [n, 16] node features
   layer l    h_l = relu([h_{l-1}, A h_{l-1}] W_l + b_l)   W_l: [128, 64], l = 1..3
   output     y = h_3 W_out + b_out                         y: [n, 3]
@@ -29,11 +31,13 @@ LAYERS = 3
 
 
 def aggregation_matrix(wm):
-    """Row-stochastic element-message averaging A (see the module docstring)."""
+    """Row-stochastic element-message averaging A (see the module docstring); an element of k
+    vertices gives every pair of its vertices the weight V_e / k."""
     t = wm.tets
-    Be = np.repeat((wm.V / 4.0)[:, None, None], 16, axis=1).reshape(-1, 4, 4)
-    rows = np.repeat(t[:, :, None], 4, axis=2)
-    cols = np.repeat(t[:, None, :], 4, axis=1)
+    k = t.shape[1]
+    Be = np.repeat((wm.V / k)[:, None, None], k * k, axis=1).reshape(-1, k, k)
+    rows = np.repeat(t[:, :, None], k, axis=2)
+    cols = np.repeat(t[:, None, :], k, axis=1)
     B = sp.coo_matrix((Be.ravel(), (rows.ravel(), cols.ravel())), shape=(wm.n, wm.n)).tocsr()
     rs = np.asarray(B.sum(axis=1)).ravel()
     return (sp.diags(1.0 / rs) @ B).tocsr()

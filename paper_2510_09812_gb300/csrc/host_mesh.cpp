@@ -172,7 +172,82 @@ double tet_geometry(const double* x0, const double* x1, const double* x2, const 
   return det;
 }
 
+// Linear hexahedron at the 2x2x2 Gauss points xi_q = s_q / sqrt(3) (weights 1): with the
+// shape functions N_a = prod_d (1 + s_a,d xi_d) / 2, J_ij = dx_i / dxi_j = sum_a x_a,i dN_a/dxi_j,
+// w[q] = det J_q and g[(q * 8 + a) * 3 + i] = d_i N_a = sum_j dN_a/dxi_j (J^-1)_ji.  Returns the
+// smallest det J_q.
+double hex_geometry(const double* const x[8], double w[8], double g[8 * 8 * 3]) {
+  const double r = 1.0 / std::sqrt(3.0);
+  double dmin = INFINITY;
+  for (int q = 0; q < kHexGauss; ++q) {
+    double xi[3];
+    for (int d = 0; d < 3; ++d) xi[d] = r * kHexSign[q][d];
+    double dN[8][3];
+    for (int a = 0; a < kHexNodes; ++a)
+      for (int d = 0; d < 3; ++d) {
+        double v = 0.5 * kHexSign[a][d];
+        for (int e = 0; e < 3; ++e)
+          if (e != d) v *= 0.5 * (1.0 + kHexSign[a][e] * xi[e]);
+        dN[a][d] = v;
+      }
+    double J[3][3] = {};
+    for (int a = 0; a < kHexNodes; ++a)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] += x[a][i] * dN[a][j];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    dmin = std::min(dmin, det);
+    w[q] = det;
+    if (!(det > 0.0)) continue;
+    const double inv = 1.0 / det;
+    double Ji[3][3];  // J^-1
+    Ji[0][0] = c00 * inv;
+    Ji[1][0] = c01 * inv;
+    Ji[2][0] = c02 * inv;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * inv;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * inv;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * inv;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * inv;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * inv;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * inv;
+    for (int a = 0; a < kHexNodes; ++a)
+      for (int i = 0; i < 3; ++i) {
+        double v = 0.0;
+        for (int j = 0; j < 3; ++j) v += dN[a][j] * Ji[j][i];
+        g[(q * 8 + a) * 3 + i] = v;
+      }
+  }
+  return dmin;
+}
+
+// N_a at the Gauss points, [q][a]
+struct HexN {
+  double v[kHexGauss][kHexNodes];
+  HexN() {
+    const double r = 1.0 / std::sqrt(3.0);
+    for (int q = 0; q < kHexGauss; ++q) {
+      double xi[3];
+      for (int d = 0; d < 3; ++d) xi[d] = r * kHexSign[q][d];
+      for (int a = 0; a < kHexNodes; ++a) v[q][a] = hex_shape(a, xi);
+    }
+  }
+};
+const HexN& hex_n() {
+  static const HexN t;
+  return t;
+}
+
 }  // namespace
+
+const int kHexSign[kHexNodes][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                    {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+double hex_shape(int a, const double xi[3]) {
+  return 0.125 * (1.0 + kHexSign[a][0] * xi[0]) * (1.0 + kHexSign[a][1] * xi[1]) *
+         (1.0 + kHexSign[a][2] * xi[2]);
+}
 
 int64_t coarse_nodes_of(int64_t option, int64_t n) {
   return option > 0 ? option : std::max<int64_t>(512, (n + 5999) / 6000);
@@ -210,6 +285,13 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
     return GSPM_EINVAL;
   }
   const int64_t ns = d->n_nodes, nt = d->n_tets;
+  const int nen = d->nodes_per_elem == 0 ? 4 : d->nodes_per_elem;
+  if (nen != 4 && nen != kHexNodes) {
+    set_error("mesh_load: nodes_per_elem %d (4: tetrahedra, 8: hexahedra)", d->nodes_per_elem);
+    return GSPM_EINVAL;
+  }
+  const bool hex = nen == kHexNodes;
+  hm->nen = nen;
   hm->n_stored = ns;
   hm->n_tets = nt;
   for (int64_t i = 0; i < 3 * ns; ++i)
@@ -222,24 +304,38 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
       set_error("mesh_load: empty box along axis %d", a);
       return GSPM_EINVAL;
     }
-  for (int64_t i = 0; i < 4 * nt; ++i)
+  for (int64_t i = 0; i < nen * nt; ++i)
     if (d->tets[i] < 0 || d->tets[i] >= ns) {
-      set_error("mesh_load: tet %lld references node %d outside [0, %lld)", (long long)(i / 4),
-                d->tets[i], (long long)ns);
+      set_error("mesh_load: element %lld references node %d outside [0, %lld)",
+                (long long)(i / nen), d->tets[i], (long long)ns);
       return GSPM_EMESH;
     }
   // geometry from stored (unwrapped) coordinates
   hm->V.resize(nt);
-  hm->grads.resize(12 * nt);
+  if (hex) {
+    hm->hw.resize((int64_t)kHexGauss * nt);
+    hm->hg.resize((int64_t)kHexGauss * kHexNodes * 3 * nt);
+  } else {
+    hm->grads.resize(12 * nt);
+  }
   double min_edge = INFINITY;
   bool bad = false;
   int64_t bad_tet = -1;
 #pragma omp parallel for reduction(min : min_edge)
   for (int64_t e = 0; e < nt; ++e) {
-    const int32_t* t = d->tets + 4 * e;
-    const double* x[4] = {d->coords + 3 * (int64_t)t[0], d->coords + 3 * (int64_t)t[1],
-                          d->coords + 3 * (int64_t)t[2], d->coords + 3 * (int64_t)t[3]};
-    const double det = tet_geometry(x[0], x[1], x[2], x[3], &hm->grads[12 * e]);
+    const int32_t* t = d->tets + (int64_t)nen * e;
+    const double* x[8];
+    for (int k = 0; k < nen; ++k) x[k] = d->coords + 3 * (int64_t)t[k];
+    double det, vol;
+    if (hex) {
+      double* w = &hm->hw[(int64_t)kHexGauss * e];
+      det = hex_geometry(x, w, &hm->hg[(int64_t)kHexGauss * kHexNodes * 3 * e]);
+      vol = 0.0;
+      for (int q = 0; q < kHexGauss; ++q) vol += w[q];
+    } else {
+      det = tet_geometry(x[0], x[1], x[2], x[3], &hm->grads[12 * e]);
+      vol = det / 6.0;
+    }
     if (!(det > 0.0)) {
 #pragma omp critical
       {
@@ -247,15 +343,17 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
         bad = true;
       }
     }
-    hm->V[e] = det / 6.0;
-    for (int i = 0; i < 4; ++i)
-      for (int j = i + 1; j < 4; ++j) {
+    hm->V[e] = vol;
+    for (int i = 0; i < nen; ++i)
+      for (int j = i + 1; j < nen; ++j) {
         const double dx = x[i][0] - x[j][0], dy = x[i][1] - x[j][1], dz = x[i][2] - x[j][2];
         min_edge = std::min(min_edge, std::sqrt(dx * dx + dy * dy + dz * dz));
       }
   }
   if (bad) {
-    set_error("mesh_load: tet %lld has det(J) <= 0", (long long)bad_tet);
+    set_error(hex ? "mesh_load: hexahedron %lld has det(J) <= 0 at a Gauss point"
+                  : "mesh_load: tet %lld has det(J) <= 0",
+              (long long)bad_tet);
     return GSPM_EMESH;
   }
   // periodic wrap: hash map of quantised wrapped coordinates, ids by first occurrence
@@ -287,14 +385,15 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
     }
   }
   const int64_t n = hm->n;
-  hm->tets_u.resize(4 * nt);
+  hm->tets_u.resize(nen * nt);
   hm->elem_mag.resize(nt);
   for (int64_t e = 0; e < nt; ++e) {
-    for (int k = 0; k < 4; ++k) hm->tets_u[4 * e + k] = hm->unique_of_stored[d->tets[4 * e + k]];
-    for (int k = 0; k < 4; ++k)
-      for (int l = k + 1; l < 4; ++l)
-        if (hm->tets_u[4 * e + k] == hm->tets_u[4 * e + l]) {
-          set_error("mesh_load: tet %lld collapses under the periodic wrap", (long long)e);
+    int64_t* tu = &hm->tets_u[nen * e];
+    for (int k = 0; k < nen; ++k) tu[k] = hm->unique_of_stored[d->tets[nen * e + k]];
+    for (int k = 0; k < nen; ++k)
+      for (int l = k + 1; l < nen; ++l)
+        if (tu[k] == tu[l]) {
+          set_error("mesh_load: element %lld collapses under the periodic wrap", (long long)e);
           return GSPM_EMESH;
         }
     hm->elem_mag[e] = d->elem_magnetic ? (d->elem_magnetic[e] ? 1 : 0) : 1;
@@ -310,13 +409,21 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
     c += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
     s = t;
   };
+  const HexN& hn = hex_n();
   for (int64_t e = 0; e < nt; ++e) {
     nsum(vs, vc, hm->V[e]);
-    for (int k = 0; k < 4; ++k) hm->ML[hm->tets_u[4 * e + k]] += hm->V[e] / 4.0;
+    for (int k = 0; k < nen; ++k) {
+      double mk = hm->V[e] / 4.0;  // int phi_k
+      if (hex) {
+        mk = 0.0;
+        for (int q = 0; q < kHexGauss; ++q) mk += hm->hw[kHexGauss * e + q] * hn.v[q][k];
+      }
+      hm->ML[hm->tets_u[nen * e + k]] += mk;
+    }
     if (hm->elem_mag[e]) {
       nsum(ms, mc, hm->V[e]);
       ++hm->n_mag_tets;
-      for (int k = 0; k < 4; ++k) hm->node_mag[hm->tets_u[4 * e + k]] = 1;
+      for (int k = 0; k < nen; ++k) hm->node_mag[hm->tets_u[nen * e + k]] = 1;
     }
   }
   hm->volume = vs + vc;
@@ -324,21 +431,21 @@ int host_mesh_build(const gspm_mesh_desc* d, int ordering, int64_t coarse_nodes,
   hm->n_mag_nodes = 0;
   for (int64_t i = 0; i < n; ++i) hm->n_mag_nodes += hm->node_mag[i];
   // node graph (self included), ascending columns
-  std::vector<int64_t> ntp(n + 1, 0), nti(4 * nt);
+  std::vector<int64_t> ntp(n + 1, 0), nti(nen * nt);
   for (int64_t e = 0; e < nt; ++e)
-    for (int k = 0; k < 4; ++k) ++ntp[hm->tets_u[4 * e + k] + 1];
+    for (int k = 0; k < nen; ++k) ++ntp[hm->tets_u[nen * e + k] + 1];
   for (int64_t i = 0; i < n; ++i) ntp[i + 1] += ntp[i];
   {
     std::vector<int64_t> fill(ntp.begin(), ntp.end() - 1);
     for (int64_t e = 0; e < nt; ++e)
-      for (int k = 0; k < 4; ++k) nti[fill[hm->tets_u[4 * e + k]]++] = e;
+      for (int k = 0; k < nen; ++k) nti[fill[hm->tets_u[nen * e + k]]++] = e;
   }
   std::vector<std::vector<int64_t>> adj(n);
 #pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t i = 0; i < n; ++i) {
     std::vector<int64_t>& a = adj[i];
     for (int64_t q = ntp[i]; q < ntp[i + 1]; ++q)
-      for (int k = 0; k < 4; ++k) a.push_back(hm->tets_u[4 * nti[q] + k]);
+      for (int k = 0; k < nen; ++k) a.push_back(hm->tets_u[nen * nti[q] + k]);
     std::sort(a.begin(), a.end());
     a.erase(std::unique(a.begin(), a.end()), a.end());
   }
@@ -458,16 +565,20 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
   ops->invML.assign(n, 0.0);
   ops->mag.assign(n, 0);
   ops->pin = hm.iperm[0];
-  // node -> incident tets, ascending tet index
-  std::vector<int64_t> ntp(n + 1, 0), nti(4 * hm.n_tets);
+  // node -> incident elements, ascending element index
+  const int nen = hm.nen;
+  const bool hex = nen == kHexNodes;
+  const HexN& hn = hex_n();
+  std::vector<int64_t> ntp(n + 1, 0), nti(nen * hm.n_tets);
   for (int64_t e = 0; e < hm.n_tets; ++e)
-    for (int k = 0; k < 4; ++k) ++ntp[hm.tets_u[4 * e + k] + 1];
+    for (int k = 0; k < nen; ++k) ++ntp[hm.tets_u[nen * e + k] + 1];
   for (int64_t i = 0; i < n; ++i) ntp[i + 1] += ntp[i];
   {
     std::vector<int64_t> fill(ntp.begin(), ntp.end() - 1);
     for (int64_t e = 0; e < hm.n_tets; ++e)
-      for (int k = 0; k < 4; ++k) nti[fill[hm.tets_u[4 * e + k]]++] = e;
+      for (int k = 0; k < nen; ++k) nti[fill[hm.tets_u[nen * e + k]]++] = e;
   }
+  std::vector<double> vsum(n, 0.0);  // sum of the volumes of the elements at each row
   const double C11 = p.C11, C12 = p.C12, C44 = p.C44, eps = p.eps, aeps = p.alpha * p.eps;
 #pragma omp parallel
   {
@@ -480,49 +591,83 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
       kms.assign(len, 0.0); km.assign(len, 0.0); mm.assign(len, 0.0);
       f.assign(3 * len, 0.0); g.assign(3 * len, 0.0); k9.assign(9 * len, 0.0);
       bb.assign(len, 0.0);
-      double ml = 0.0;
+      double ml = 0.0, vs = 0.0;
+      // K_ab = sum_cd gk_c C_acbd gl_d; in the cube axes
+      // K_ab = d_ab [(C11 - C44) gk_a gl_a + C44 gk.gl] + (1 - d_ab)[C12 gk_a gl_b + C44 gk_b gl_a]
+      auto kmech_add = [&](double* k9p, double wq, const double* gk, const double* gl) {
+        const double dot = gk[0] * gl[0] + gk[1] * gl[1] + gk[2] * gl[2];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            double v;
+            if (p.rotated) {
+              v = 0.0;
+              for (int c = 0; c < 3; ++c)
+                for (int dd = 0; dd < 3; ++dd)
+                  v += gk[c] * p.Cm[((a * 3 + c) * 3 + b) * 3 + dd] * gl[dd];
+            } else {
+              v = a == b ? (C11 - C44) * gk[a] * gl[a] + C44 * dot
+                         : C12 * gk[a] * gl[b] + C44 * gk[b] * gl[a];
+            }
+            k9p[3 * a + b] += wq * v;
+          }
+      };
       for (int64_t q = ntp[o]; q < ntp[o + 1]; ++q) {
         const int64_t e = nti[q];
-        const int64_t* t = &hm.tets_u[4 * e];
+        const int64_t* t = &hm.tets_u[nen * e];
         int k = 0;
         while (t[k] != o) ++k;
         const double V = hm.V[e];
-        const double* gk = &hm.grads[12 * e + 3 * k];
         const bool me = hm.elem_mag[e] != 0;
-        ml += V / 4.0;
-        for (int l = 0; l < 4; ++l) {
-          const int32_t j = (int32_t)hm.iperm[t[l]];
-          int pos = 0;
-          while (rc[pos] != j) ++pos;
-          const double* gl = &hm.grads[12 * e + 3 * l];
-          const double dot = gk[0] * gl[0] + gk[1] * gl[1] + gk[2] * gl[2];
-          kms[pos] += V * dot;
-          bb[pos] += V / 4.0;  // B_ij = sum_{e containing i, j} V_e / 4
-          if (me) {
-            km[pos] += V * dot;
-            mm[pos] += V * (k == l ? 2.0 : 1.0) / 20.0;
-          }
-          for (int a = 0; a < 3; ++a) {
-            f[3 * pos + a] += -(V / 4.0) * gl[a];   // -int phi_i d_a phi_j
-            g[3 * pos + a] += (V / 4.0) * gk[a];    //  int phi_j d_a phi_i
-          }
-          // K_ab = sum_cd gk_c C_acbd gl_d; in the cube axes
-          // K_ab = d_ab [(C11 - C44) gk_a gl_a + C44 gk.gl] + (1 - d_ab)[C12 gk_a gl_b
-          //        + C44 gk_b gl_a]
-          for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-              double v;
-              if (p.rotated) {
-                v = 0.0;
-                for (int c = 0; c < 3; ++c)
-                  for (int dd = 0; dd < 3; ++dd)
-                    v += gk[c] * p.Cm[((a * 3 + c) * 3 + b) * 3 + dd] * gl[dd];
-              } else {
-                v = a == b ? (C11 - C44) * gk[a] * gl[a] + C44 * dot
-                           : C12 * gk[a] * gl[b] + C44 * gk[b] * gl[a];
-              }
-              k9[9 * pos + 3 * a + b] += V * v;
+        vs += V;
+        if (!hex) {
+          // linear tetrahedron: every integral in closed form
+          const double* gk = &hm.grads[12 * e + 3 * k];
+          ml += V / 4.0;
+          for (int l = 0; l < 4; ++l) {
+            const int32_t j = (int32_t)hm.iperm[t[l]];
+            int pos = 0;
+            while (rc[pos] != j) ++pos;
+            const double* gl = &hm.grads[12 * e + 3 * l];
+            const double dot = gk[0] * gl[0] + gk[1] * gl[1] + gk[2] * gl[2];
+            kms[pos] += V * dot;
+            bb[pos] += V / 4.0;  // B_ij = sum_{e containing i, j} V_e / (nodes per element)
+            if (me) {
+              km[pos] += V * dot;
+              mm[pos] += V * (k == l ? 2.0 : 1.0) / 20.0;
             }
+            for (int a = 0; a < 3; ++a) {
+              f[3 * pos + a] += -(V / 4.0) * gl[a];   // -int phi_i d_a phi_j
+              g[3 * pos + a] += (V / 4.0) * gk[a];    //  int phi_j d_a phi_i
+            }
+            kmech_add(&k9[9 * pos], V, gk, gl);
+          }
+        } else {
+          // trilinear hexahedron: the same integrals by 2x2x2 Gauss quadrature
+          const double* w = &hm.hw[(int64_t)kHexGauss * e];
+          const double* hg = &hm.hg[(int64_t)kHexGauss * kHexNodes * 3 * e];
+          for (int qq = 0; qq < kHexGauss; ++qq) ml += w[qq] * hn.v[qq][k];
+          for (int l = 0; l < kHexNodes; ++l) {
+            const int32_t j = (int32_t)hm.iperm[t[l]];
+            int pos = 0;
+            while (rc[pos] != j) ++pos;
+            bb[pos] += V / kHexNodes;
+            for (int qq = 0; qq < kHexGauss; ++qq) {
+              const double wq = w[qq], Nk = hn.v[qq][k], Nl = hn.v[qq][l];
+              const double* gk = hg + (qq * 8 + k) * 3;
+              const double* gl = hg + (qq * 8 + l) * 3;
+              const double dot = gk[0] * gl[0] + gk[1] * gl[1] + gk[2] * gl[2];
+              kms[pos] += wq * dot;
+              if (me) {
+                km[pos] += wq * dot;
+                mm[pos] += wq * Nk * Nl;
+              }
+              for (int a = 0; a < 3; ++a) {
+                f[3 * pos + a] += -wq * Nk * gl[a];
+                g[3 * pos + a] += wq * Nl * gk[a];
+              }
+              kmech_add(&k9[9 * pos], wq, gk, gl);
+            }
+          }
         }
       }
       const int64_t sl = i / kSell, lane = i % kSell;
@@ -539,8 +684,10 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
         }
         for (int b = 0; b < 9; ++b) ops->Kmech[vb * 9 + b * kSell + lane] = k9[9 * pos + b];
       }
+      // element-message average: A_ij = B_ij / (sum of the volumes of the elements at i)
       for (int pos = 0; pos < len; ++pos)
-        ops->Agg[s.sptr[sl] + (int64_t)pos * kSell + lane] = bb[pos] / (4.0 * ml);
+        ops->Agg[s.sptr[sl] + (int64_t)pos * kSell + lane] = bb[pos] / vs;
+      vsum[i] = vs;
       ops->ML[i] = ml;
       ops->w[i] = ml / hm.volume;
       ops->invML[i] = 1.0 / ml;
@@ -554,7 +701,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
       }
     }
   }
-  // A^T at (i, j) = A_ji = B_ij / (4 M_L,j)  (B is symmetric)
+  // A^T at (i, j) = A_ji = B_ij / vsum_j  (B is symmetric)
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     const int64_t sl = i / kSell, lane = i % kSell;
@@ -562,7 +709,7 @@ void host_assemble(const HostMesh& hm, const HostSell& s, const Params& p, HostO
     for (int pos = 0; pos < len; ++pos) {
       const int64_t ent = s.sptr[sl] + (int64_t)pos * kSell + lane;
       const int32_t j = s.ic[s.rp[i] + pos];
-      ops->AggT[ent] = ops->Agg[ent] * ops->ML[i] / ops->ML[j];
+      ops->AggT[ent] = ops->Agg[ent] * vsum[i] / vsum[j];
     }
   }
 }

@@ -36,13 +36,21 @@ struct Params {
 int make_params(const gspm_material* mat, const gspm_options* opt, Params* p);
 
 // Host-side mesh after validation, periodic wrap and (optional) renumbering.
+// Linear hexahedra: 2x2x2 Gauss points, reference corner signs and shape-function values
+constexpr int kHexNodes = 8, kHexGauss = 8;
+extern const int kHexSign[kHexNodes][3];
+double hex_shape(int a, const double xi[3]);  // N_a(xi)
+
 struct HostMesh {
-  int64_t n_stored = 0, n_tets = 0, n = 0;  // n = unique nodes
+  int64_t n_stored = 0, n_tets = 0, n = 0;  // n = unique nodes; n_tets = elements
+  int nen = 4;                               // nodes per element: 4 tetrahedra, 8 hexahedra
   std::vector<int64_t> unique_of_stored;     // [n_stored]
-  std::vector<int64_t> tets_u;               // [n_tets*4] unique (original) node ids
+  std::vector<int64_t> tets_u;               // [n_tets*nen] unique (original) node ids
   std::vector<uint8_t> elem_mag;             // [n_tets]
   std::vector<double> V;                     // [n_tets]
-  std::vector<double> grads;                 // [n_tets*12], (k*3 + a) = d_a phi_k
+  std::vector<double> grads;                 // tetrahedra: [n_tets*12], (k*3 + a) = d_a phi_k
+  std::vector<double> hw;                    // hexahedra: [n_tets*8] det J x weight per Gauss point
+  std::vector<double> hg;                    // hexahedra: [n_tets*8*8*3] (q, k, a) = d_a phi_k at q
   std::vector<uint8_t> node_mag;             // [n] original numbering
   std::vector<int64_t> rowptr, cols;         // node graph, original numbering, ascending
   std::vector<int64_t> perm, iperm;          // perm[internal] = original, iperm = inverse

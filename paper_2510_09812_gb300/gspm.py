@@ -43,7 +43,8 @@ _dp = C.POINTER(C.c_double)
 class MeshDesc(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("coords", _dp), ("n_tets", C.c_int64),
                 ("tets", C.POINTER(C.c_int32)), ("elem_magnetic", C.POINTER(C.c_uint8)),
-                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3), ("wrap_tol", C.c_double)]
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3), ("wrap_tol", C.c_double),
+                ("nodes_per_elem", C.c_int32)]
 
 
 class Material(C.Structure):
@@ -215,6 +216,7 @@ class Context:
             d.box_lo[:] = [float(v) for v in me.box_lo]
             d.box_hi[:] = [float(v) for v in me.box_hi]
             d.wrap_tol = float(wrap_tol)
+            d.nodes_per_elem = int(tets.shape[1])
         o = Options()
         o.precision = {"f64": PREC_F64, "mixed": PREC_MIXED}[precision]
         o.ordering = {"none": ORDER_NONE, "rcm": ORDER_RCM, "aggregate": ORDER_AGGREGATE}[ordering]

@@ -20,6 +20,9 @@ Stored mesh layout
   tetrahedron is positively oriented.  A jitter of at most 0.2 h per axis cannot invert one.
 * ``elem_magnetic`` uint8 [n_tets]: 0 when the element centroid lies inside a defect (periodic
   minimum image), else 1.
+* ``hex_box`` stores the same lattice as linear hexahedra instead: ``tets`` int32
+  [nx * ny * nz, 8], one element per cube with the vertices at the corners (0,0,0) (1,0,0)
+  (1,1,0) (0,1,0) (0,0,1) (1,0,1) (1,1,1) (0,1,1) in that order.
 * Per unique lattice node ``u = i + nx * (j + ny * k)`` (0 <= i < nx ...) fields such as the initial
   magnetisation are indexed in that order.
 """
@@ -89,7 +92,7 @@ def fe_like_material() -> dict:
 @dataclass
 class Mesh:
     coords: np.ndarray          # float64 [n_stored, 3], nm
-    tets: np.ndarray            # int32 [n_tets, 4]
+    tets: np.ndarray            # int32 [n_elements, 4] tetrahedra or [n_elements, 8] hexahedra
     elem_magnetic: np.ndarray   # uint8 [n_tets]
     box_lo: np.ndarray          # float64 [3]
     box_hi: np.ndarray          # float64 [3]
@@ -103,6 +106,10 @@ class Mesh:
     @property
     def n_tets(self) -> int:
         return self.tets.shape[0]
+
+    @property
+    def nodes_per_elem(self) -> int:
+        return self.tets.shape[1]
 
     @property
     def n_unique(self) -> int:
@@ -144,6 +151,29 @@ def _inside_defect(points: np.ndarray, d: dict, box: np.ndarray) -> np.ndarray:
         hs = np.asarray(d["half_sides"], dtype=np.float64)
         return np.all(np.abs(delta) < hs, axis=1)
     raise ValueError(f"unknown defect kind {kind!r}")
+
+
+# corner offsets of the hexahedron of a cube, in the element's vertex order
+_HEX = np.array([(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1),
+                 (0, 1, 1)], dtype=np.int64)
+
+
+def hex_box(n_cells, box, jitter: float = 0.0, seed: int = 0, defects=()) -> Mesh:
+    """Periodic lattice of ``n_cells`` cubes spanning ``[0, box]`` (nm), one linear hexahedron
+    per cube; nodes and jitter exactly as ``kuhn_box``."""
+    tm = kuhn_box(n_cells, box, jitter=jitter, seed=seed)
+    nx, ny, nz = tm.n_cells
+    ck, cj, ci = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cube = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)
+    vert = cube[:, None, :] + _HEX[None, :, :]
+    hexes = (vert[..., 0] + (nx + 1) * (vert[..., 1] + (ny + 1) * vert[..., 2])).astype(np.int32)
+    centroid = tm.coords[hexes].mean(axis=1)
+    L = tm.box_hi
+    mag = np.ones(hexes.shape[0], dtype=bool)
+    for d in defects:
+        mag &= ~_inside_defect(centroid, d, L)
+    return Mesh(coords=tm.coords, tets=hexes, elem_magnetic=mag.astype(np.uint8),
+                box_lo=tm.box_lo, box_hi=L, n_cells=tm.n_cells, defects=list(defects))
 
 
 def kuhn_box(n_cells, box, jitter: float = 0.0, seed: int = 0, defects=()) -> Mesh:

@@ -239,3 +239,41 @@ def test_coarse_round_shifts_an_indefinite_rounding(gspm_lib):
     with pytest.raises(g.GSPMError) as e:
         g.coarse_round(-np.eye(4), bf16=True)
     assert e.value.code == g.EMESH
+
+
+@pytest.mark.parametrize("ordering", ["none", "rcm", "aggregate"])
+def test_host_hex_mesh_matches_oracle(gspm_lib, ordering):
+    """Linear hexahedra (nodes_per_elem 8): wrap, node graph (27-point stencil on the lattice),
+    permutation, lumped mass (2x2x2 Gauss quadrature) and volume against the oracle."""
+    mesh = synth.hex_box((6, 5, 4), (24.0, 20.0, 16.0), jitter=0.2, seed=8,
+                         defects=[dict(kind="sphere", center=(12.0, 10.0, 8.0), radius=4.5)])
+    ctx = gspm_lib.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, ordering=ordering,
+                           host_only=True, coarse_nodes=16)
+    wm = WrappedMesh.from_synth(mesh)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_UNIQUE_OF_STORED), wm.unique_of_stored)
+    rowptr, cols = csr_pattern(wm.tets, wm.n)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_ROWPTR), rowptr)
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_COLS), cols)
+    assert (rowptr[1:] - rowptr[:-1]).max() == 27
+    assert np.array_equal(ctx.export(gspm_lib.EXPORT_NODE_MAGNETIC).astype(bool),
+                          wm.node_magnetic)
+    from oracle import fem
+    assert np.allclose(ctx.export(gspm_lib.EXPORT_LUMPED_MASS), fem.lumped_mass(wm), rtol=1e-13)
+    info = ctx.info()
+    assert info["volume"] == pytest.approx(24.0 * 20.0 * 16.0, rel=1e-13)
+    assert info["n_tets"] == 120
+
+
+def test_hex_inverted_and_bad_node_count_rejected(gspm_lib):
+    mat = synth.fe_like_material()
+    bad = synth.hex_box((3, 3, 3), (3.0, 3.0, 3.0))
+    bad.tets = bad.tets.copy()
+    bad.tets[4] = bad.tets[4][[1, 0, 3, 2, 5, 4, 7, 6]]            # mirrored: det J < 0
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(bad, mat, 1e-12, 0.5, host_only=True)
+    assert e.value.code == gspm_lib.EMESH and "hexahedron" in str(e.value)
+    odd = synth.kuhn_box((3, 3, 3), (3.0, 3.0, 3.0))
+    odd.tets = np.concatenate([odd.tets, odd.tets[:, :2]], axis=1)  # 6 nodes per element
+    with pytest.raises(gspm_lib.GSPMError) as e:
+        gspm_lib.Context(odd, mat, 1e-12, 0.5, host_only=True)
+    assert e.value.code == gspm_lib.EINVAL
