@@ -538,6 +538,85 @@ def run_contract(args):
 
 
 # ------------------------------------------------------------------------------------------
+# time-step study (separate invocation)
+# ------------------------------------------------------------------------------------------
+
+def run_dt_sweep(args):
+    """The time-step study of Sec. 4 on the structured hexahedral cuboid-defect workload: for
+    every dt, GSPM steps from m = e1 until <|m^n - m^(n-1)|> < 5e-10 over the magnetic nodes (or
+    --sweep-cap steps), in FP64 with every CG to 1e-7.  Steps go in chunks of 100 (graph
+    replay); the chunk whose last step meets the threshold is replayed step by step from its
+    start to find the first step that does.  Reported per dt: the steps taken, mean CG
+    iterations per step of K^ms, K^mech and per GSPM solve, the last <|dm|> and the wall time.
+    With --sweep-paper-form, the first 20 steps are also taken in the paper's form (pinned
+    systems, plain CG) for its iteration counts."""
+    import torch
+    from paper_2510_09812_gb300 import build
+    from paper_2510_09812_gb300 import gspm, synth
+    build.build()
+    torch.cuda.set_device(0)
+    cells = tuple(int(v) for v in args.sweep_cells.split(","))
+    cfg = synth.cuboid_defect_hex_box(n_cells=cells)
+    dts = [float(v) * 1e-12 for v in args.sweep_dt_ps.split(",")]
+    cap, chunk, tol = args.sweep_cap, 100, cfg["dm_tol"]
+    n = cfg["mesh"].n_unique
+    out = {"workload": cfg["name"], "nodes": n, "alpha": cfg["alpha"], "dm_tol": tol,
+           "precision": args.precision, "rtol": 1e-7, "cap": cap, "runs": []}
+
+    def reset(ctx):
+        ctx.set_field(gspm.FIELD_M, cfg["m0"])
+        ctx.set_field(gspm.FIELD_U, np.zeros(n))
+        for f in (gspm.FIELD_DISP, gspm.FIELD_DISP_PREV):
+            ctx.set_field(f, np.zeros((n, 3)))
+
+    for dt in dts:
+        ctx = gspm.Context(cfg["mesh"], cfg["material"], dt, cfg["alpha"],
+                           precision=args.precision, graph=True)
+        reset(ctx)
+        done, its = 0, {"it_ms": 0, "it_mech": 0, "it_gs": 0}
+        hist, dm, conv = [], float("nan"), False
+        t0 = time.perf_counter()
+        while done < cap and not conv:
+            k = min(chunk, cap - done)
+            snap = _snapshot(gspm, torch, ctx)
+            st = ctx.step(k, cfg["H"])
+            if st["dm_last"] < tol:
+                _restore(torch, ctx, snap)
+                for j in range(k):
+                    st = ctx.step(1, cfg["H"])
+                    for key in its:
+                        its[key] += st[key]
+                    if st["dm_last"] < tol:
+                        done += j + 1
+                        break
+                conv = True
+            else:
+                for key in its:
+                    its[key] += st[key]
+                done += k
+            dm = st["dm_last"]
+            if done % 1000 == 0 or conv:
+                hist.append([done, dm])
+        wall = time.perf_counter() - t0
+        row = {"dt_ps": round(dt * 1e12, 6), "steps": done, "converged": conv, "dm_last": dm,
+               "cg_per_step": {"ms": its["it_ms"] / done, "mech": its["it_mech"] / done,
+                               "gs_per_solve": its["it_gs"] / (7.0 * done)},
+               "wall_s": round(wall, 2), "dm_history": hist}
+        ctx.close()
+        if args.sweep_paper_form:
+            pc = gspm.Context(cfg["mesh"], cfg["material"], dt, cfg["alpha"],
+                              precision=args.precision, pinned_cg=True, plain_cg=True)
+            reset(pc)
+            st = pc.step(20, cfg["H"])
+            row["paper_form_first_20"] = {"ms": st["it_ms"] / 20.0, "mech": st["it_mech"] / 20.0,
+                                          "gs_per_solve": st["it_gs"] / 140.0}
+            pc.close()
+        out["runs"].append(row)
+        print(json.dumps({"dt_sweep_row": row}), flush=True)
+    print(json.dumps({"dt_sweep": out}), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # the headline
 # ------------------------------------------------------------------------------------------
 
@@ -886,11 +965,19 @@ def main():
                     help="run the mixed-precision contract (mixed vs FP64 trajectories) instead")
     ap.add_argument("--contract-cells", default="128,128,32")
     ap.add_argument("--contract-steps", type=int, default=1000)
+    ap.add_argument("--dt-sweep", action="store_true",
+                    help="run the time-step study on the hexahedral cuboid-defect workload instead")
+    ap.add_argument("--sweep-cells", default="32,32,8")
+    ap.add_argument("--sweep-dt-ps", default="2,3,4,5,6,7,8,9,10,11")
+    ap.add_argument("--sweep-cap", type=int, default=40000)
+    ap.add_argument("--sweep-paper-form", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and not args.contract:
+    if args.warmup < 3 and args.impl == "ours" and not (args.contract or args.dt_sweep):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.contract:
         run_contract(args)
+    elif args.dt_sweep:
+        run_dt_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -221,7 +221,8 @@ typedef struct gspm_step_stats {
 #define GSPM_EXPORT_COLS 2              /* int64 [nnz], ascending per row, unique-node order   */
 #define GSPM_EXPORT_PERM 3              /* int64 [n_unique], perm[internal] = unique index     */
 #define GSPM_EXPORT_NODE_MAGNETIC 4     /* uint8 [n_unique]                                    */
-#define GSPM_EXPORT_LUMPED_MASS 5       /* double [n_unique], M_L,i = sum_{e ni i} V_e / 4      */
+#define GSPM_EXPORT_LUMPED_MASS 5       /* double [n_unique], M_L,i = sum_e int_e N_i (V_e / 4
+                                           on a tetrahedron, a 2x2x2 Gauss sum on a hexahedron) */
 #define GSPM_EXPORT_AGGREGATES 6        /* int32 [n_unique] preconditioner aggregate per node   */
 #define GSPM_EXPORT_COARSE_K_MS 7       /* double [n_agg^2] P^T K^ms P (unpinned K), row-major  */
 #define GSPM_EXPORT_COARSE_K_MECH 8     /* double [(3 n_agg)^2] P^T K^mech P, index 3 I + a     */

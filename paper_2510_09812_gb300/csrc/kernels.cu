@@ -206,16 +206,18 @@ __device__ __forceinline__ void sell_scalar_row(const DSell& A, const V* __restr
   }
   if (VAR == 1 || VAR == 3) {
     // eight neighbours per round: their columns and values first, then the gathers, then the
-    // FMAs (more loads in flight per thread)
+    // FMAs (more loads in flight per thread).  Past the row's end the round re-reads entry kb
+    // (kb < len), so every load is unconditional and inside the slice, with weight 0.
     for (int kb = k0; kb < len; kb += 8 * kstep) {
       int j[8];
       V w[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int k = kb + u * kstep;
-        const bool ok = k < len;
-        j[u] = ok ? __ldcs(cp + (int64_t)k * 32) : 0;
-        w[u] = ok ? __ldcs(vp + (int64_t)k * 32) : V(0);
+        const int kc = k < len ? k : kb;
+        j[u] = __ldcs(cp + (int64_t)kc * 32);
+        const V wv = __ldcs(vp + (int64_t)kc * 32);
+        w[u] = k < len ? wv : V(0);
       }
 #pragma unroll
       for (int r = 0; r < NR; ++r)
@@ -256,7 +258,8 @@ __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restri
           xi2 = own ? x[3 * row + 2] : X(0);
   acc[0] = acc[1] = acc[2] = Acc(0);
   if (VAR == 1 || VAR == 3) {
-    // five neighbours per round: all loads first, then the FMAs
+    // five neighbours per round: all loads first, then the FMAs; past the row's end entry kb
+    // is re-read with weight 0 (unconditional loads, all inside the slice)
     for (int kb = k0; kb < len; kb += 5 * kstep) {
       int j[5];  // 32-bit: five fewer registers than 64-bit indices in this unrolled round
       V w[5][9];
@@ -264,10 +267,14 @@ __device__ __forceinline__ void sell_block_row(const DSell& A, const V* __restri
       for (int u = 0; u < 5; ++u) {
         const int k = kb + u * kstep;
         const bool ok = k < len;
-        j[u] = ok ? __ldcs(cp + (int64_t)k * 32) : 0;
-        const V* bp = vp + (int64_t)(ok ? k : 0) * 288;
+        const int kc = ok ? k : kb;
+        j[u] = __ldcs(cp + (int64_t)kc * 32);
+        const V* bp = vp + (int64_t)kc * 288;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) w[u][e] = ok ? __ldcs(bp + e * 32) : V(0);
+        for (int e = 0; e < 9; ++e) {
+          const V wv = __ldcs(bp + e * 32);
+          w[u][e] = ok ? wv : V(0);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 5; ++u) {
@@ -1129,6 +1136,82 @@ __global__ void __launch_bounds__(kBlock) k_restrict(DCoarse C, const T* __restr
 }
 
 
+// The same for contiguous aggregates (GSPM_ORDER_AGGREGATE): one warp per aggregate, no
+// barrier.  The aggregate's elements [e0, e1) of r are read as 16-byte packs, kRestrictPacks per
+// lane in flight, with the unaligned head and tail (fewer than one pack each) taken by single
+// lanes; element e has component e mod EPR.  Each lane sums its packs in order, the warp tree is
+// fixed, so the result does not depend on the grid.
+constexpr int kRestrictPacks = 8;
+template <typename T, int EPR>
+__global__ void __launch_bounds__(kBlock) k_restrict_contig(DCoarse C, const T* __restrict__ r,
+                                                            const int64_t* __restrict__ rc_off,
+                                                            T* __restrict__ rc) {
+  pdl_enter();
+  constexpr int W = Pack16<T>::W, U = kRestrictPacks;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < C.nagg;
+       I += nwarps) {
+    const int q0 = C.agg_ptr[I], q1 = C.agg_ptr[I + 1];
+    T acc[EPR];
+#pragma unroll
+    for (int a = 0; a < EPR; ++a) acc[a] = T(0);
+    if (q1 > q0) {
+      const int64_t e0 = (int64_t)C.agg_rows[q0] * EPR, e1 = e0 + (int64_t)(q1 - q0) * EPR;
+      int64_t a0 = (e0 + W - 1) / W * W;
+      if (a0 > e1) a0 = e1;
+      int64_t a1 = e1 / W * W;
+      if (a1 < a0) a1 = a0;
+      const int nh = (int)(a0 - e0), nt = (int)(e1 - a1);
+      if (lane < nh + nt) {
+        const int64_t e = lane < nh ? e0 + lane : a1 + (lane - nh);
+        acc[EPR == 1 ? 0 : (int)(e % EPR)] += r[e];
+      }
+      const int64_t np = (a1 - a0) / W;
+      const int cb0 = EPR == 1 ? 0 : (int)(a0 % EPR);
+      for (int64_t t0 = 0; t0 < np; t0 += 32 * U) {
+        T v[U][W];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t t = t0 + 32 * u + lane;
+          if (t < np) {
+            ld16(r + a0 + t * W, v[u]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < W; ++c) v[u][c] = T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t t = t0 + 32 * u + lane;
+          // component of the pack's first element: (a0 + t W) mod EPR
+          const int cb = EPR == 1 ? 0 : (int)((cb0 + (t % EPR) * (W % EPR)) % EPR);
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            if (EPR == 1) {
+              acc[0] += v[u][c];
+            } else {
+              const int cc = (cb + c) % EPR;
+#pragma unroll
+              for (int a = 0; a < EPR; ++a) acc[a] += cc == a ? v[u][c] : T(0);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < EPR; ++a) {
+      T v = acc[a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+      if (lane == 0) {
+        const int sg = C.agg_seg[I];
+        rc[rc_off[sg] + (I - C.seg_agg0[sg]) * EPR + a] = v;
+      }
+    }
+  }
+}
+
 // N contiguous values through 16-byte packs (N * sizeof(T) a multiple of 16, p aligned)
 template <typename T, int N>
 __device__ __forceinline__ void ldn(const T* p, T (&v)[N]) {
@@ -1397,7 +1480,8 @@ __global__ void k_cg_zero(DSeg G, ItemList IL, int epr, T* x, const CGState* st)
 
 // One round of a row kernel over the F^ms / G values (three per entry): kRowRound neighbours'
 // columns and values loaded before any gather, so each lane has that many independent loads in
-// flight (entries past the row's length give column 0 and value 0).
+// flight.  Entries past the row's length re-read entry kb (kb < len) and give value 0, so every
+// load is unconditional and inside the slice.
 constexpr int kRowRound = 5;
 template <typename T>
 __device__ __forceinline__ void row_round(const int32_t* cp, const T* vp, int kb, int len,
@@ -1406,10 +1490,14 @@ __device__ __forceinline__ void row_round(const int32_t* cp, const T* vp, int kb
   for (int u = 0; u < kRowRound; ++u) {
     const int k = kb + u;
     const bool ok = k < len;
-    j[u] = ok ? __ldcs(cp + (int64_t)k * 32) : 0;
-    const T* fp = vp + (int64_t)(ok ? k : 0) * 96;
+    const int kc = ok ? k : kb;
+    j[u] = __ldcs(cp + (int64_t)kc * 32);
+    const T* fp = vp + (int64_t)kc * 96;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) f[u][a] = ok ? __ldcs(fp + 32 * a) : T(0);
+    for (int a = 0; a < 3; ++a) {
+      const T fv = __ldcs(fp + 32 * a);
+      f[u][a] = ok ? fv : T(0);
+    }
   }
 }
 
@@ -2230,7 +2318,17 @@ template <typename T>
 cudaError_t launch_restrict(const Launch& L, const DCoarse& C, int epr, const T* r,
                             const int64_t* rc_off, T* rc) {
   (*L.counter) += 1;
-  if (epr == 3) {
+  if (C.contig && aligned16(r)) {
+    if (epr == 3) {
+      auto k = k_restrict_contig<T, 3>;
+      ST_CUDA(launch_pdl(k, GSPM_GRID(L, C.nagg * 32, k), L.stream, C, r, rc_off, rc));
+    } else if (epr == 1) {
+      auto k = k_restrict_contig<T, 1>;
+      ST_CUDA(launch_pdl(k, GSPM_GRID(L, C.nagg * 32, k), L.stream, C, r, rc_off, rc));
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  } else if (epr == 3) {
     auto k = k_restrict<T, 3>;
     ST_CUDA(launch_pdl(k, GSPM_GRID(L, C.nagg * kBlock, k), L.stream, C, r, rc_off, rc));
   } else if (epr == 1) {

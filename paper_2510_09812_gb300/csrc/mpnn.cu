@@ -23,6 +23,7 @@ constexpr int kRows = 128;      // rows per tile (8 warps x 16)
 constexpr int kThreads = 256;
 constexpr int kXs = 2 * kHid + 8;  // padded shared row stride (bf16) of the [h, z] tile
 constexpr int kWs = 2 * kHid + 8;  // padded shared row stride of W^T ([64][128])
+constexpr int kGather = 8;      // neighbour feature loads in flight per lane in k_layer
 
 __device__ __forceinline__ int64_t tid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t tstride() { return (int64_t)gridDim.x * blockDim.x; }
@@ -173,30 +174,59 @@ __global__ void __launch_bounds__(kThreads) k_layer(int64_t n, DSell S, const fl
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * kRows; base < n; base += (int64_t)gridDim.x * kRows) {
     __syncthreads();
-    // each warp fills 16 rows: lane covers features 2*lane, 2*lane+1
-    for (int rr = 0; rr < 16; ++rr) {
-      const int r = 16 * warp + rr;
+    // each warp fills its 16 rows (half a SELL slice) four at a time: lane group g = lane / 8
+    // takes row 4 rr + g, lane q = lane % 8 its features 8 q .. 8 q + 7 (16-byte loads); the
+    // neighbours go in batches of kGather, all their column loads before their feature loads, so
+    // a lane has kGather gathers in flight.  z sums the neighbours in column order.
+    const int grp = lane >> 3, q = lane & 7;
+    const int64_t s0 = (base + 16 * warp) >> 5;
+    const int64_t sb = s0 < S.nslices ? S.sptr[s0] : 0;
+    const int len = s0 < S.nslices ? S.slen[s0] : 0;
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = 16 * warp + 4 * rr + grp;
       const int64_t i = base + r;
-      float z0 = 0.f, z1 = 0.f;
-      uint32_t hi = 0;
+      float z[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) z[c] = 0.f;
+      uint4 hi = make_uint4(0u, 0u, 0u, 0u);
       if (i < n) {
-        hi = *reinterpret_cast<const uint32_t*>(Hin + i * kHid + 2 * lane);
-        const int64_t s = i >> 5, li = i & 31;
-        const int64_t sb = S.sptr[s];
-        const int len = S.slen[s];
-        for (int k = 0; k < len; ++k) {
-          const int64_t e = sb + (int64_t)k * 32 + li;
-          const int64_t j = S.col[e];
-          const float a = Aw[e];
-          const uint32_t hj = *reinterpret_cast<const uint32_t*>(Hin + j * kHid + 2 * lane);
-          z0 += a * __bfloat162float(__ushort_as_bfloat16((unsigned short)(hj & 0xffffu)));
-          z1 += a * __bfloat162float(__ushort_as_bfloat16((unsigned short)(hj >> 16)));
+        hi = *reinterpret_cast<const uint4*>(Hin + i * kHid + 8 * q);
+        const int64_t li = i & 31;
+        for (int k0 = 0; k0 < len; k0 += kGather) {
+          int64_t j[kGather];
+          float a[kGather];
+#pragma unroll
+          for (int u = 0; u < kGather; ++u) {
+            // past the row's end: entry k0 (k0 < len) again, weight 0; no load leaves the slice
+            const bool ok = k0 + u < len;
+            const int64_t e = sb + (int64_t)(ok ? k0 + u : k0) * 32 + li;
+            j[u] = (int64_t)S.col[e];
+            const float av = Aw[e];
+            a[u] = ok ? av : 0.f;
+          }
+          uint4 hj[kGather];
+#pragma unroll
+          for (int u = 0; u < kGather; ++u)
+            hj[u] = *reinterpret_cast<const uint4*>(Hin + j[u] * kHid + 8 * q);
+#pragma unroll
+          for (int u = 0; u < kGather; ++u) {
+            const uint32_t w[4] = {hj[u].x, hj[u].y, hj[u].z, hj[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              z[2 * c] += a[u] * __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[c] & 0xffffu)));
+              z[2 * c + 1] += a[u] * __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[c] >> 16)));
+            }
+          }
         }
       }
-      const uint32_t zp = pack2(__float2bfloat16_rn(z0), __float2bfloat16_rn(z1));
-      *reinterpret_cast<uint32_t*>(Xs + r * kXs + 2 * lane) = hi;
-      *reinterpret_cast<uint32_t*>(Xs + r * kXs + kHid + 2 * lane) = zp;
-      if (Zout && i < n) *reinterpret_cast<uint32_t*>(Zout + i * kHid + 2 * lane) = zp;
+      uint4 zp;
+      zp.x = pack2(__float2bfloat16_rn(z[0]), __float2bfloat16_rn(z[1]));
+      zp.y = pack2(__float2bfloat16_rn(z[2]), __float2bfloat16_rn(z[3]));
+      zp.z = pack2(__float2bfloat16_rn(z[4]), __float2bfloat16_rn(z[5]));
+      zp.w = pack2(__float2bfloat16_rn(z[6]), __float2bfloat16_rn(z[7]));
+      *reinterpret_cast<uint4*>(Xs + r * kXs + 8 * q) = hi;
+      *reinterpret_cast<uint4*>(Xs + r * kXs + kHid + 8 * q) = zp;
+      if (Zout && i < n) *reinterpret_cast<uint4*>(Zout + i * kHid + 8 * q) = zp;
     }
     __syncthreads();
     float acc[8][4];

@@ -252,6 +252,24 @@ def sphere_inclusion_box(n_cells=(128, 128, 32), box=(512.0, 512.0, 128.0), radi
                 H=np.array([200.0, 0.0, 0.0]), alpha=0.5, dt=5e-12, steps=1000)
 
 
+def cuboid_defect_hex_box(n_cells=(128, 128, 32), h=4.0):
+    """Structured (unjittered) periodic lattice of linear hexahedra with edge h nm (128 x 128 x 32
+    cells = 524,288 nodes at the default, the size class of the time-step study of Sec. 4) and
+    one non-magnetic cuboid at the centre with a quarter of the box's edge on every side; m = e1,
+    H = 200 A/m along e1, alpha 0.15.  The enclosing body is a needle along e1 (N_d = diag(0,
+    1/2, 1/2)), so the uniform start is stable except for the defect's own stray field and
+    relaxes; with N_d = I/3 the far field drives the Fe-like box into moving domains instead.
+    The study varies dt; 3 ps is set here."""
+    L = h * np.asarray(n_cells, dtype=np.float64)
+    mesh = hex_box(n_cells, L, jitter=0.0,
+                   defects=[dict(kind="cuboid", center=L / 2, half_sides=L / 8)])
+    mat = fe_like_material()
+    mat["Nd"] = [0.0, 0, 0, 0, 0.5, 0, 0, 0, 0.5]
+    return dict(name=f"cuboid_defect_hex_{int(L[0])}x{int(L[1])}x{int(L[2])}nm_{mesh.n_unique}n",
+                mesh=mesh, material=mat, m0=uniform_m(mesh.n_unique),
+                H=np.array([200.0, 0.0, 0.0]), alpha=0.15, dt=3e-12, dm_tol=5e-10)
+
+
 def void_cuboids_box(n_cells=(228, 228, 57), box=(1024.0, 1024.0, 256.0), seed=2):
     """1024x1024x256 nm box (2.96M nodes at h ~ 4.49 nm), jitter 0.2 h, one seeded random
     axis-aligned ellipsoidal void (semi-axes U[40,120] x U[40,120] x U[20,60] nm) and 8 random
