@@ -185,8 +185,9 @@ typedef struct gspm_mesh_info {
                               0 thread per row, 1 thread per row with 5-deep load prefetch,
                               2 two threads per row, 3 = 1 with registers capped for three
                               resident blocks per SM                                            */
-  int spmv_schedule_scalar;/* ... and for the scalar operators                                 */
-  double spmv_ms_block[GSPM_SPMV_SCHEDULES]; /* ms per launch of each schedule (0 = not tuned) */
+  int spmv_schedule_scalar;/* ... and for K^ms                                                */
+  double spmv_ms_block[GSPM_SPMV_SCHEDULES]; /* ms per launch of each schedule as the CG loop
+                              runs it (product fused with p.Ap; 0 = not tuned)                 */
   double spmv_ms_scalar[GSPM_SPMV_SCHEDULES];
   int64_t n_aggregates;    /* aggregates of the two-level preconditioner, all meshes (0: none) */
   double coarse_shift_ms, coarse_shift_mech;
@@ -194,6 +195,9 @@ typedef struct gspm_mesh_info {
                               to the device storage to keep them positive definite (largest over
                               the meshes; 0 when the rounded inverse is positive definite as it
                               is, see gspm_coarse_round)                                      */
+  int spmv_schedule_gs;    /* schedule chosen for the GSPM operators M + c eps K               */
+  double spmv_ms_gs[GSPM_SPMV_SCHEDULES]; /* summed ms of one launch with 1, 2 and 3 right-hand
+                              sides, per schedule                                              */
 } gspm_mesh_info;
 
 typedef struct gspm_step_stats {

@@ -116,7 +116,8 @@ class EngineBase {
   virtual int set_field(int field, const double* data, int where) = 0;
   virtual int get_field(int field, double* data, int where) = 0;
   virtual int64_t device_bytes() const = 0;
-  virtual void tune_info(int* vb, int* vs, float* tb, float* ts, int* item_slices) const = 0;
+  virtual void tune_info(int* vb, int* vs, int* vg, float* tb, float* ts, float* tg,
+                         int* item_slices) const = 0;
   virtual int profile_enable(unsigned mask) = 0;
   virtual int profile_read(int cls, double* ms, int64_t* launches) = 0;
   virtual int set_x0_mode(int mode) = 0;
@@ -316,34 +317,64 @@ class Engine final : public EngineBase {
     return GSPM_OK;
   }
 
-  // Project autotuner: time every SpMV schedule on this mesh's own operators (K^mech for the
-  // 3x3-block kernels, K^ms for the scalar ones; five launches each after one warm-up, CUDA
-  // events on the context's stream) and keep the fastest.
+  // Project autotuner: time every SpMV schedule as the CG loops run it (the product fused with
+  // p.q and alpha, k_cg_spmv) on this mesh's own operators: K^mech for the 3x3-block solves,
+  // K^ms for the scalar ones, M + eps K with one, two and three right-hand sides for the GSPM
+  // solves (their summed time decides).  A scratch CG state with every segment active and a
+  // non-constant search direction (so that p.Ap > 0) is reset before each schedule; one warm-up
+  // and five timed launches with CUDA events on the context's stream; the fastest is kept.
   int autotune() {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    auto time_variant = [&](int B, const T* val, int var, float* ms, int diff = 1) -> int {
-      CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var, diff));
+    CGState* st = nullptr;
+    ST(mem_.alloc(&st, (int64_t)nseg_));
+    std::vector<CGState> hs(nseg_);
+    for (auto& c : hs) {
+      memset(&c, 0, sizeof(c));
+      c.nr = 3;
+      c.active = 1;
+      c.max_iter = 1 << 30;
+      for (int k = 0; k < 3; ++k) c.r[k].bb = c.r[k].rr = c.r[k].rz = 1.0;
+    }
+    {
+      std::vector<T> pv((size_t)3 * ld_);
+      for (size_t i = 0; i < pv.size(); ++i) pv[i] = (T)(1.0 + 0.5 * std::sin(0.37 * (double)i));
+      CK(cudaMemcpy(tin_, pv.data(), pv.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    const int pinned = (opt_.flags & GSPM_FLAG_PINNED_CG) ? 1 : 0;
+    auto time_variant = [&](const T* val, int B, int nr, int diff, int pin, int var,
+                            float* ms) -> int {
+      CK(cudaMemcpyAsync(st, hs.data(), nseg_ * sizeof(CGState), cudaMemcpyHostToDevice,
+                         L_.stream));
+      const int64_t ld = B == 9 ? 3 * n_ : (nr == 1 ? n_ : ld_);
+      CK(launch_cg_spmv<T>(L_, A_, SG_, val, B, nr, ld, tin_, tout_, st, red_, var, pin, diff));
       CK(cudaEventRecord(e0, L_.stream));
-      for (int k = 0; k < 5; ++k) CK(launch_spmv<T>(L_, A_, val, B, tin_, tout_, var, diff));
+      for (int k = 0; k < 5; ++k)
+        CK(launch_cg_spmv<T>(L_, A_, SG_, val, B, nr, ld, tin_, tout_, st, red_, var, pin, diff));
       CK(cudaEventRecord(e1, L_.stream));
       CK(cudaEventSynchronize(e1));
       CK(cudaEventElapsedTime(ms, e0, e1));
+      *ms /= 5.f;
       return GSPM_OK;
     };
     float best_b = 1e30f, best_s = 1e30f, best_g = 1e30f;
     for (int v = 0; v < kSpmvVariants; ++v) {
       float t = 0.f;
-      ST(time_variant(9, Kmech_, v, &t));
-      tune_ms_block_[v] = t / 5.f;
+      ST(time_variant(Kmech_, 9, 1, 1, pinned, v, &t));
+      tune_ms_block_[v] = t;
       if (t < best_b) { best_b = t; var_block_ = v; }
-      ST(time_variant(1, Kms_, v, &t));
-      tune_ms_scalar_[v] = t / 5.f;
+      ST(time_variant(Kms_, 1, 1, 1, pinned, v, &t));
+      tune_ms_scalar_[v] = t;
       if (t < best_s) { best_s = t; var_scalar_ = v; }
       // the GSPM operators are not in difference form: their own schedule
-      ST(time_variant(1, Aeps_, v, &t, 0));
-      if (t < best_g) { best_g = t; var_gs_ = v; }
+      float tg = 0.f;
+      for (int nr = 1; nr <= 3; ++nr) {
+        ST(time_variant(Aeps_, 1, nr, 0, 0, v, &t));
+        tg += t;
+      }
+      tune_ms_gs_[v] = tg;
+      if (tg < best_g) { best_g = tg; var_gs_ = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -351,13 +382,16 @@ class Engine final : public EngineBase {
   }
 
  public:
-  void tune_info(int* vb, int* vs, float* tb, float* ts, int* item_slices) const override {
+  void tune_info(int* vb, int* vs, int* vg, float* tb, float* ts, float* tg,
+                 int* item_slices) const override {
     *vb = var_block_;
     *vs = var_scalar_;
+    *vg = var_gs_;
     *item_slices = item_slices_;
     for (int v = 0; v < kSpmvVariants; ++v) {
       tb[v] = tune_ms_block_[v];
       ts[v] = tune_ms_scalar_[v];
+      tg[v] = tune_ms_gs_[v];
     }
   }
 
@@ -467,7 +501,21 @@ class Engine final : public EngineBase {
   }
 
   // GSPM_ENUMERIC if a projection of this call met a non-finite or zero m** (synchronises)
+  // the learned guess's tensor-core layers report a wait that gave up through mpnn_err_
+  int check_net() {
+    if (!mpnn_err_) return GSPM_OK;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, mpnn_err_, sizeof(int), cudaMemcpyDeviceToHost, L_.stream));
+    CK(cudaStreamSynchronize(L_.stream));
+    if (e) {
+      set_error("learned initial guess: a tensor-core layer did not complete within its wait limit");
+      return GSPM_ECUDA;
+    }
+    return GSPM_OK;
+  }
+
   int check_finite() {
+    ST(check_net());
     CK(cudaMemcpyAsync(host_bad_, bad_, nseg_ * sizeof(int), cudaMemcpyDeviceToHost, L_.stream));
     CK(cudaStreamSynchronize(L_.stream));
     for (int sg = 0; sg < nseg_; ++sg)
@@ -1017,7 +1065,7 @@ class Engine final : public EngineBase {
     }
     ST(export_field(utmp_, 1, 3, 3, out, where));
     CK(cudaStreamSynchronize(L_.stream));
-    return GSPM_OK;
+    return check_net();
   }
 
   int mpnn_dataset_reserve(int capacity) override {
@@ -1075,6 +1123,7 @@ class Engine final : public EngineBase {
     CK(cudaMemcpyAsync(&l, loss_, sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
     if (grad) CK(cudaMemcpyAsync(grad, grad_, kParams * sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
     CK(cudaStreamSynchronize(L_.stream));
+    ST(check_net());
     if (loss) *loss = (double)l / (3.0 * (double)n_);
     return GSPM_OK;
   }
@@ -1097,6 +1146,7 @@ class Engine final : public EngineBase {
     }
     CK(cudaMemcpyAsync(&ll, loss_, sizeof(float), cudaMemcpyDeviceToHost, L_.stream));
     CK(cudaStreamSynchronize(L_.stream));
+    ST(check_net());
     if (l0) *l0 = (double)lf / (3.0 * (double)n_);
     if (l1) *l1 = (double)ll / (3.0 * (double)n_);
     return GSPM_OK;
@@ -1617,6 +1667,9 @@ class Engine final : public EngineBase {
     net_.bout = params_ + kOffBout;
     net_.A = agg_;
     net_.At = aggT_;
+    ST(mem_.alloc(&mpnn_err_, 1));
+    CK(cudaMemset(mpnn_err_, 0, sizeof(int)));
+    net_.err = mpnn_err_;
     return GSPM_OK;
   }
 
@@ -1706,6 +1759,7 @@ class Engine final : public EngineBase {
   __nv_bfloat16* Z_[3] = {};
   int adam_t_ = 0, ds_cap_ = 0, ds_n_ = 0;
   MpnnDev net_{};
+  int* mpnn_err_ = nullptr;
   T *u2_ = nullptr, *utmp_ = nullptr, *uin_ = nullptr, *uin2_ = nullptr;
 
   // launch f() bracketed by CUDA events when class cls is being profiled
@@ -1762,7 +1816,8 @@ class Engine final : public EngineBase {
   Red red_{};
   int pred_[kSolveSlots];
   int var_block_ = 0, var_scalar_ = 0, var_gs_ = 0;
-  float tune_ms_block_[kSpmvVariants] = {}, tune_ms_scalar_[kSpmvVariants] = {};
+  float tune_ms_block_[kSpmvVariants] = {}, tune_ms_scalar_[kSpmvVariants] = {},
+        tune_ms_gs_[kSpmvVariants] = {};
   int seen_[kSolveSlots] = {};
   // K^ms / K^mech solves: pinned system (flag) or the consistent singular one (default)
   int pinned_ = 0;
@@ -1959,15 +2014,17 @@ int gspm_mesh_info_get(const gspm_ctx* ctx, gspm_mesh_info* out) {
     out->coarse_shift_mech = std::max(out->coarse_shift_mech, hc.shift_mech);
   }
   if (ctx->eng) {
-    float tb[kSpmvVariants], ts[kSpmvVariants];
-    int vb = 0, vs = 0, is = 0;
-    ctx->eng->tune_info(&vb, &vs, tb, ts, &is);
+    float tb[kSpmvVariants], ts[kSpmvVariants], tg[kSpmvVariants];
+    int vb = 0, vs = 0, vg = 0, is = 0;
+    ctx->eng->tune_info(&vb, &vs, &vg, tb, ts, tg, &is);
     out->spmv_schedule_block = vb;
     out->spmv_schedule_scalar = vs;
+    out->spmv_schedule_gs = vg;
     out->item_slices = is;
     for (int v = 0; v < kSpmvVariants && v < GSPM_SPMV_SCHEDULES; ++v) {
       out->spmv_ms_block[v] = tb[v];
       out->spmv_ms_scalar[v] = ts[v];
+      out->spmv_ms_gs[v] = tg[v];
     }
   }
   return GSPM_OK;

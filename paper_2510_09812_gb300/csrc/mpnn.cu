@@ -1,10 +1,10 @@
 // Learned warm start of the mechanical CG: a three-layer message-passing network over the mesh
 // (hidden width 64) that predicts the displacement correction on top of linear extrapolation.
 //
-// Forward layers run on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation)
-// with the element-message aggregation z_i = sum_j A_ij h_j fused into the tile load: a block
-// owns 128 rows, gathers [h_i, z_i] into shared memory as BF16 and multiplies by the layer's
-// weights held in shared memory.  Training (backward and Adam) runs in FP32 on CUDA cores with
+// Forward layers run on the Blackwell tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
+// accumulator in tensor memory) with the element-message aggregation z_i = sum_j A_ij h_j fused
+// into the tile load: a block owns 128 rows, gathers [h_i, z_i] into shared memory as BF16 and
+// multiplies by the layer's weights held in shared memory.  Training (backward and Adam) runs in FP32 on CUDA cores with
 // deterministic block partials.  The network definition (features, aggregation, loss) is the
 // one documented in include/gspm.h (gspm_mpnn_*).
 #include <cuda_bf16.h>
@@ -21,9 +21,7 @@ namespace {
 
 constexpr int kRows = 128;      // rows per tile (8 warps x 16)
 constexpr int kThreads = 256;
-constexpr int kXs = 2 * kHid + 8;  // padded shared row stride (bf16) of the [h, z] tile
-constexpr int kWs = 2 * kHid + 8;  // padded shared row stride of W^T ([64][128])
-constexpr int kGather = 8;      // neighbour feature loads in flight per lane in k_layer
+constexpr int kGather = 8;      // neighbour feature loads in flight per lane in k_tc_layer
 
 __device__ __forceinline__ int64_t tid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t tstride() { return (int64_t)gridDim.x * blockDim.x; }
@@ -32,66 +30,92 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// D = A (16x16, row) * B (16x8, col) + D, BF16 operands, FP32 accumulators
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
+// ---------------------------------------------------------------------------------------------
+// Blackwell tensor cores: tcgen05.mma with the FP32 accumulator in tensor memory (TMEM)
+// ---------------------------------------------------------------------------------------------
+// A layer's GEMM is one 128 x 64 tile per block and K step: A = the block's 128 rows of [h, z]
+// (or of the 16 input features), B = W^T (64 x K), both K-major in shared memory with the
+// 128-byte swizzle (rows of 64 bf16, eight-row groups 1024 bytes apart, 16-byte chunk c of row r
+// stored at chunk c ^ (r mod 8)).  One thread issues the K / 16 MMAs and commits them to an
+// mbarrier; the accumulator (row i in TMEM lane i, column j in TMEM column j) is read back with
+// tcgen05.ld by all eight warps (warp w: lanes 32 (w mod 4) .., columns 32 (w / 4) ..).
+constexpr int kTileA = kRows * 128;   // bytes of one 64-wide K-block of A
+constexpr int kTileB = kHid * 128;    // bytes of one 64-wide K-block of B
+constexpr int kTmemCols = 64;         // TMEM columns of the 128 x 64 FP32 accumulator
+constexpr size_t kTcSmem = 2 * kTileA + 2 * kTileB + kHid * 4 + 16 + 1024;  // + alignment slack
+// spin limit of the accumulator wait (each try_wait may also suspend for a while): far beyond the
+// microsecond an MMA group takes, so reaching it means the tensor-core work never completed
+constexpr uint32_t kSpinLimit = 1u << 22;
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B bf16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(kHid >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte offset of 16-byte chunk c (0..7) of row r in a 128-byte-swizzled K-block
+__device__ __forceinline__ uint32_t sw128(int r, int c) {
+  return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+}
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading byte offset >> 4
+// (bits 16-29; not used by a swizzled K-major operand), stride byte offset >> 4 = 1024 >> 4
+// between eight-row groups (bits 32-45), the fixed 0b001 at bits 46-48, 128-byte swizzle (2 at
+// bits 61-63).  The K-block starts on a 1024-byte boundary, so the base offset is 0 and a K step
+// inside the block advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
 }
-
-// One warp: rows [r0, r0+16) of X (shared, row stride xs, K columns) times W^T (shared [64][K],
-// row stride ws) -> acc[8][4] (8 n-tiles of 8 columns).  Fragment layout of mma.m16n8k16:
-// lane = 4*g + t; A regs {X[g][2t..], X[g+8][2t..], X[g][2t+8..], X[g+8][2t+8..]};
-// B regs {W^T[n=g][2t..], W^T[g][2t+8..]}; C {row g: cols 2t, 2t+1; row g+8: same}.
-template <int K>
-__device__ __forceinline__ void warp_gemm(const __nv_bfloat16* X, int xs, const __nv_bfloat16* Wt,
-                                          int ws, int r0, float (&acc)[8][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[4];
-    const __nv_bfloat16* xr0 = X + (r0 + g) * xs + k0 + 2 * t;
-    const __nv_bfloat16* xr1 = X + (r0 + g + 8) * xs + k0 + 2 * t;
-    a[0] = *reinterpret_cast<const uint32_t*>(xr0);
-    a[1] = *reinterpret_cast<const uint32_t*>(xr1);
-    a[2] = *reinterpret_cast<const uint32_t*>(xr0 + 8);
-    a[3] = *reinterpret_cast<const uint32_t*>(xr1 + 8);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const __nv_bfloat16* wr = Wt + (8 * j + g) * ws + k0 + 2 * t;
-      uint32_t b[2];
-      b[0] = *reinterpret_cast<const uint32_t*>(wr);
-      b[1] = *reinterpret_cast<const uint32_t*>(wr + 8);
-      mma16816(acc[j], a, b);
-    }
-  }
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   mbar)
+               : "memory");
 }
-
-// epilogue: out[row][col] = bf16(relu(acc + bias)) for the warp's 16 rows
-__device__ __forceinline__ void warp_store_relu(const float (&acc)[8][4], const float* bias,
-                                                int64_t row0, int64_t n, __nv_bfloat16* out) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int col = 8 * j + 2 * t;
-    const float b0 = bias[col], b1 = bias[col + 1];
-    const int64_t ra = row0 + g, rb = row0 + g + 8;
-    if (ra < n)
-      *reinterpret_cast<uint32_t*>(out + ra * kHid + col) =
-          pack2(__float2bfloat16_rn(fmaxf(acc[j][0] + b0, 0.f)),
-                __float2bfloat16_rn(fmaxf(acc[j][1] + b1, 0.f)));
-    if (rb < n)
-      *reinterpret_cast<uint32_t*>(out + rb * kHid + col) =
-          pack2(__float2bfloat16_rn(fmaxf(acc[j][2] + b0, 0.f)),
-                __float2bfloat16_rn(fmaxf(acc[j][3] + b1, 0.f)));
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void async_proxy_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// true once the mbarrier phase of parity `phase` has completed; false after kSpinLimit polls
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (done) return true;
   }
+  return false;
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -131,107 +155,178 @@ __global__ void k_features(int64_t n, const T* __restrict__ m, int64_t ld,
   }
 }
 
-// h0 = relu(F W_in + b_in)  (K = 16)
-__global__ void __launch_bounds__(kThreads) k_input(int64_t n, const __nv_bfloat16* __restrict__ F,
-                                                    const __nv_bfloat16* __restrict__ WinT,
-                                                    const float* __restrict__ b_in,
-                                                    __nv_bfloat16* __restrict__ H) {
-  constexpr int fs = kFeat + 8;
-  __shared__ __align__(16) __nv_bfloat16 Xs[kRows * fs];
-  __shared__ __align__(16) __nv_bfloat16 Ws[kHid * fs];
-  __shared__ float bs[kHid];
-  for (int k = threadIdx.x; k < kHid * kFeat; k += blockDim.x)
-    Ws[(k / kFeat) * fs + k % kFeat] = WinT[k];
-  for (int k = threadIdx.x; k < kHid; k += blockDim.x) bs[k] = b_in[k];
-  const int warp = threadIdx.x >> 5;
-  for (int64_t base = (int64_t)blockIdx.x * kRows; base < n; base += (int64_t)gridDim.x * kRows) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < kRows * kFeat; k += blockDim.x) {
-      const int r = k / kFeat, c = k % kFeat;
-      Xs[r * fs + c] = base + r < n ? F[(base + r) * kFeat + c] : __float2bfloat16_rn(0.f);
-    }
-    __syncthreads();
-    float acc[8][4];
-    warp_gemm<kFeat>(Xs, fs, Ws, fs, 16 * warp, acc);
-    warp_store_relu(acc, bs, base + 16 * warp, n, H);
-  }
-}
-
-// h_out = relu([h, A h] W + b) with the aggregation gathered into the tile; z optionally saved
-__global__ void __launch_bounds__(kThreads) k_layer(int64_t n, DSell S, const float* __restrict__ Aw,
-                                                    const __nv_bfloat16* __restrict__ Hin,
-                                                    const __nv_bfloat16* __restrict__ WT,
-                                                    const float* __restrict__ bias,
-                                                    __nv_bfloat16* __restrict__ Hout,
-                                                    __nv_bfloat16* __restrict__ Zout) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* Ws = Xs + kRows * kXs;
-  float* bs = reinterpret_cast<float*>(Ws + kHid * kWs);
-  for (int k = threadIdx.x; k < kHid * 2 * kHid; k += blockDim.x)
-    Ws[(k / (2 * kHid)) * kWs + k % (2 * kHid)] = WT[k];
-  for (int k = threadIdx.x; k < kHid; k += blockDim.x) bs[k] = bias[k];
+// One forward layer on the tensor cores.  MODE 0: h0 = relu(F W_in + b_in) (K = 16, the node
+// features); MODE 1: h_out = relu([h, A h] W + b) (K = 128) with the element-message aggregation
+// z = A h gathered into the A tile (z optionally saved for the backward pass).  A block owns
+// 128 rows per round; TMEM holds its 128 x 64 accumulator.  err (device int) is set when the
+// accumulator wait gives up; the block then waits once more (bounded) for its MMAs, frees its
+// TMEM and returns.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_tc_layer(int64_t n, DSell S,
+                                                       const float* __restrict__ Aw,
+                                                       const __nv_bfloat16* __restrict__ Hin,
+                                                       const __nv_bfloat16* __restrict__ WT,
+                                                       const float* __restrict__ bias,
+                                                       __nv_bfloat16* __restrict__ Hout,
+                                                       __nv_bfloat16* __restrict__ Zout,
+                                                       int* __restrict__ err) {
+  constexpr int K = MODE == 0 ? kFeat : 2 * kHid;
+  constexpr int KC = K / 8;  // 16-byte chunks per row
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_addr(smem_raw);
+  unsigned char* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  unsigned char* As = sm;                  // K-blocks 0 (h or F) and 1 (z)
+  unsigned char* Bs = sm + 2 * kTileA;     // W^T, K-blocks 0 and 1
+  float* bs = reinterpret_cast<float*>(Bs + 2 * kTileB);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(bs + kHid);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < kHid * KC; t += blockDim.x) {
+    const int o = t / KC, cc = t % KC;
+    const uint4 v = *reinterpret_cast<const uint4*>(WT + (int64_t)o * K + cc * 8);
+    *reinterpret_cast<uint4*>(Bs + (cc >> 3) * kTileB + sw128(o, cc & 7)) = v;
+  }
+  for (int k = threadIdx.x; k < kHid; k += blockDim.x) bs[k] = bias[k];
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  async_proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t bar = smem_addr(mbar);
+  uint32_t phase = 0;
+  int inflight = 0;
   for (int64_t base = (int64_t)blockIdx.x * kRows; base < n; base += (int64_t)gridDim.x * kRows) {
-    __syncthreads();
-    // each warp fills its 16 rows (half a SELL slice) four at a time: lane group g = lane / 8
-    // takes row 4 rr + g, lane q = lane % 8 its features 8 q .. 8 q + 7 (16-byte loads); the
-    // neighbours go in batches of kGather, all their column loads before their feature loads, so
-    // a lane has kGather gathers in flight.  z sums the neighbours in column order.
-    const int grp = lane >> 3, q = lane & 7;
-    const int64_t s0 = (base + 16 * warp) >> 5;
-    const int64_t sb = s0 < S.nslices ? S.sptr[s0] : 0;
-    const int len = s0 < S.nslices ? S.slen[s0] : 0;
-    for (int rr = 0; rr < 4; ++rr) {
-      const int r = 16 * warp + 4 * rr + grp;
-      const int64_t i = base + r;
-      float z[8];
+    if (MODE == 0) {
+      // 128 rows x 2 chunks of the features, one 16-byte load per thread
+      for (int t = threadIdx.x; t < kRows * KC; t += blockDim.x) {
+        const int r = t / KC, c = t % KC;
+        const int64_t i = base + r;
+        const uint4 v = i < n ? *reinterpret_cast<const uint4*>(Hin + i * kFeat + c * 8)
+                              : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(As + sw128(r, c)) = v;
+      }
+    } else {
+      // each warp fills its 16 rows (half a SELL slice) four at a time: lane group g = lane / 8
+      // takes row 4 rr + g, lane q = lane % 8 its features 8 q .. 8 q + 7 (one 16-byte chunk);
+      // the neighbours go in batches of kGather, all their column loads before their feature
+      // loads, so a lane has kGather gathers in flight.  z sums the neighbours in column order.
+      const int grp = lane >> 3, q = lane & 7;
+      const int64_t s0 = (base + 16 * warp) >> 5;
+      const int64_t sb = s0 < S.nslices ? S.sptr[s0] : 0;
+      const int len = s0 < S.nslices ? S.slen[s0] : 0;
+      for (int rr = 0; rr < 4; ++rr) {
+        const int r = 16 * warp + 4 * rr + grp;
+        const int64_t i = base + r;
+        float z[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) z[c] = 0.f;
-      uint4 hi = make_uint4(0u, 0u, 0u, 0u);
-      if (i < n) {
-        hi = *reinterpret_cast<const uint4*>(Hin + i * kHid + 8 * q);
-        const int64_t li = i & 31;
-        for (int k0 = 0; k0 < len; k0 += kGather) {
-          int64_t j[kGather];
-          float a[kGather];
+        for (int c = 0; c < 8; ++c) z[c] = 0.f;
+        uint4 hi = make_uint4(0u, 0u, 0u, 0u);
+        if (i < n) {
+          hi = *reinterpret_cast<const uint4*>(Hin + i * kHid + 8 * q);
+          const int64_t li = i & 31;
+          for (int k0 = 0; k0 < len; k0 += kGather) {
+            int64_t j[kGather];
+            float a[kGather];
 #pragma unroll
-          for (int u = 0; u < kGather; ++u) {
-            // past the row's end: entry k0 (k0 < len) again, weight 0; no load leaves the slice
-            const bool ok = k0 + u < len;
-            const int64_t e = sb + (int64_t)(ok ? k0 + u : k0) * 32 + li;
-            j[u] = (int64_t)S.col[e];
-            const float av = Aw[e];
-            a[u] = ok ? av : 0.f;
-          }
-          uint4 hj[kGather];
+            for (int u = 0; u < kGather; ++u) {
+              // past the row's end: entry k0 (k0 < len) again, weight 0; no load leaves the slice
+              const bool ok = k0 + u < len;
+              const int64_t e = sb + (int64_t)(ok ? k0 + u : k0) * 32 + li;
+              j[u] = (int64_t)S.col[e];
+              const float av = Aw[e];
+              a[u] = ok ? av : 0.f;
+            }
+            uint4 hj[kGather];
 #pragma unroll
-          for (int u = 0; u < kGather; ++u)
-            hj[u] = *reinterpret_cast<const uint4*>(Hin + j[u] * kHid + 8 * q);
+            for (int u = 0; u < kGather; ++u)
+              hj[u] = *reinterpret_cast<const uint4*>(Hin + j[u] * kHid + 8 * q);
 #pragma unroll
-          for (int u = 0; u < kGather; ++u) {
-            const uint32_t w[4] = {hj[u].x, hj[u].y, hj[u].z, hj[u].w};
+            for (int u = 0; u < kGather; ++u) {
+              const uint32_t w[4] = {hj[u].x, hj[u].y, hj[u].z, hj[u].w};
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              z[2 * c] += a[u] * __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[c] & 0xffffu)));
-              z[2 * c + 1] += a[u] * __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[c] >> 16)));
+              for (int c = 0; c < 4; ++c) {
+                z[2 * c] += a[u] * __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[c] & 0xffffu)));
+                z[2 * c + 1] += a[u] * __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[c] >> 16)));
+              }
             }
           }
         }
+        uint4 zp;
+        zp.x = pack2(__float2bfloat16_rn(z[0]), __float2bfloat16_rn(z[1]));
+        zp.y = pack2(__float2bfloat16_rn(z[2]), __float2bfloat16_rn(z[3]));
+        zp.z = pack2(__float2bfloat16_rn(z[4]), __float2bfloat16_rn(z[5]));
+        zp.w = pack2(__float2bfloat16_rn(z[6]), __float2bfloat16_rn(z[7]));
+        *reinterpret_cast<uint4*>(As + sw128(r, q)) = hi;
+        *reinterpret_cast<uint4*>(As + kTileA + sw128(r, q)) = zp;
+        if (Zout && i < n) *reinterpret_cast<uint4*>(Zout + i * kHid + 8 * q) = zp;
       }
-      uint4 zp;
-      zp.x = pack2(__float2bfloat16_rn(z[0]), __float2bfloat16_rn(z[1]));
-      zp.y = pack2(__float2bfloat16_rn(z[2]), __float2bfloat16_rn(z[3]));
-      zp.z = pack2(__float2bfloat16_rn(z[4]), __float2bfloat16_rn(z[5]));
-      zp.w = pack2(__float2bfloat16_rn(z[6]), __float2bfloat16_rn(z[7]));
-      *reinterpret_cast<uint4*>(Xs + r * kXs + 8 * q) = hi;
-      *reinterpret_cast<uint4*>(Xs + r * kXs + kHid + 8 * q) = zp;
-      if (Zout && i < n) *reinterpret_cast<uint4*>(Zout + i * kHid + 8 * q) = zp;
     }
+    // the A tile written by every thread becomes visible to the tensor cores; one thread issues
+    // the K / 16 MMAs of the tile and commits them to the mbarrier
+    async_proxy_fence();
     __syncthreads();
-    float acc[8][4];
-    warp_gemm<2 * kHid>(Xs, kXs, Ws, kWs, 16 * warp, acc);
-    warp_store_relu(acc, bs, base + 16 * warp, n, Hout);
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+#pragma unroll
+      for (int ks = 0; ks < K / 16; ++ks) {
+        const uint32_t koff = (uint32_t)((ks & 3) * 32);
+        tc_mma(tmem, sw128_desc(a0 + (ks >> 2) * kTileA + koff),
+               sw128_desc(b0 + (ks >> 2) * kTileB + koff), ks > 0 ? 1u : 0u);
+      }
+      tc_commit(bar);
+    }
+    inflight = 1;
+    if (!mbar_wait(bar, phase)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    inflight = 0;
+    phase ^= 1u;
+    tc_fence_after();
+    // epilogue: warp w reads lanes 32 (w mod 4) .. + 31 (its rows), columns 32 (w / 4) .. + 31
+    const int lg = warp & 3, ch = warp >> 2;
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * ch), v);
+    const int64_t row = base + 32 * lg + lane;
+    if (row < n) {
+      uint32_t pk[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = 32 * ch + 2 * c;
+        pk[c] = pack2(__float2bfloat16_rn(fmaxf(__uint_as_float(v[2 * c]) + bs[col], 0.f)),
+                      __float2bfloat16_rn(fmaxf(__uint_as_float(v[2 * c + 1]) + bs[col + 1], 0.f)));
+      }
+      uint4* dst = reinterpret_cast<uint4*>(Hout + row * kHid + 32 * ch);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+    }
+    // the accumulator and the A tile are consumed before the next round overwrites them
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    if (inflight) mbar_wait(bar, phase);  // bounded: give the MMAs a last chance to finish
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
   }
 }
 
@@ -522,9 +617,7 @@ static inline int grid_rows(const Launch& L, int64_t n) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-size_t mpnn_layer_smem() {
-  return (size_t)kRows * kXs * 2 + (size_t)kHid * kWs * 2 + kHid * 4;
-}
+size_t mpnn_layer_smem() { return kTcSmem; }
 size_t mpnn_layer_bwd_smem() { return (size_t)(2 * kHid * kHid + 8 * 2 * kHid + 8 * kHid) * 4; }
 
 template <typename T>
@@ -547,15 +640,16 @@ cudaError_t mpnn_forward(const Launch& L, int64_t n, const DSell& S, const MpnnD
                          const __nv_bfloat16* F, __nv_bfloat16* const H[4],
                          __nv_bfloat16* const Z[3]) {
   const int g = grid_rows(L, n);
+  const size_t sm = mpnn_layer_smem();
   (*L.counter) += 1;
-  k_input<<<g, kThreads, 0, L.stream>>>(n, F, W.WinT, W.b_in, H[0]);
+  k_tc_layer<0><<<g, kThreads, sm, L.stream>>>(n, S, W.A, F, W.WinT, W.b_in, H[0], nullptr,
+                                               W.err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t sm = mpnn_layer_smem();
   for (int l = 0; l < kLayers; ++l) {
     (*L.counter) += 1;
-    k_layer<<<g, kThreads, sm, L.stream>>>(n, S, W.A, H[l], W.WT[l], W.b[l], H[l + 1],
-                                           Z ? Z[l] : nullptr);
+    k_tc_layer<1><<<g, kThreads, sm, L.stream>>>(n, S, W.A, H[l], W.WT[l], W.b[l], H[l + 1],
+                                                 Z ? Z[l] : nullptr, W.err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -635,8 +729,11 @@ cudaError_t mpnn_refresh_bf16(const Launch& L, __nv_bfloat16* WinT, __nv_bfloat1
 }
 
 cudaError_t mpnn_setup_smem() {
-  cudaError_t e = cudaFuncSetAttribute(k_layer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_tc_layer<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)mpnn_layer_smem());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tc_layer<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mpnn_layer_smem());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)mpnn_layer_bwd_smem());

@@ -35,6 +35,7 @@ struct MpnnDev {
   const float* bout;
   const float* A;              // SELL weights of the element-message averaging
   const float* At;             // SELL weights of its transpose
+  int* err;                    // set by a forward layer whose tensor-core wait gave up
 };
 
 size_t mpnn_layer_smem();

@@ -72,7 +72,8 @@ class MeshInfo(C.Structure):
                 ("spmv_schedule_block", C.c_int),
                 ("spmv_schedule_scalar", C.c_int), ("spmv_ms_block", C.c_double * 4),
                 ("spmv_ms_scalar", C.c_double * 4), ("n_aggregates", C.c_int64),
-                ("coarse_shift_ms", C.c_double), ("coarse_shift_mech", C.c_double)]
+                ("coarse_shift_ms", C.c_double), ("coarse_shift_mech", C.c_double),
+                ("spmv_schedule_gs", C.c_int), ("spmv_ms_gs", C.c_double * 4)]
 
 
 class StepStats(C.Structure):
@@ -267,6 +268,7 @@ class Context:
         out = {k: getattr(i, k) for k, _ in MeshInfo._fields_}
         out["spmv_ms_block"] = list(i.spmv_ms_block)
         out["spmv_ms_scalar"] = list(i.spmv_ms_scalar)
+        out["spmv_ms_gs"] = list(i.spmv_ms_gs)
         return out
 
     def export(self, what: int) -> np.ndarray:

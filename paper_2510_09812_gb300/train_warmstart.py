@@ -87,8 +87,8 @@ def generate(ctx, torch, gspm, pairs, seed, k0, steps_per_traj=40, skip=2):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--pairs", type=int, default=1200)
-    ap.add_argument("--val", type=int, default=120)
+    ap.add_argument("--pairs", type=int, default=5000)
+    ap.add_argument("--val", type=int, default=200)
     ap.add_argument("--iters", type=int, default=6000)
     ap.add_argument("--cells", default="128,128,32")
     ap.add_argument("--seed", type=int, default=0)
