@@ -1480,8 +1480,8 @@ __global__ void k_cg_zero(DSeg G, ItemList IL, int epr, T* x, const CGState* st)
 
 // One round of a row kernel over the F^ms / G values (three per entry): kRowRound neighbours'
 // columns and values loaded before any gather, so each lane has that many independent loads in
-// flight.  Entries past the row's length re-read entry kb (kb < len) and give value 0, so every
-// load is unconditional and inside the slice.
+// flight.  Entries past the row's length give column 0 and value 0 without a load, and their
+// addresses are those of entry kb (kb < len), so no address leaves the slice either way.
 constexpr int kRowRound = 5;
 template <typename T>
 __device__ __forceinline__ void row_round(const int32_t* cp, const T* vp, int kb, int len,
@@ -1491,13 +1491,10 @@ __device__ __forceinline__ void row_round(const int32_t* cp, const T* vp, int kb
     const int k = kb + u;
     const bool ok = k < len;
     const int kc = ok ? k : kb;
-    j[u] = __ldcs(cp + (int64_t)kc * 32);
+    j[u] = ok ? __ldcs(cp + (int64_t)kc * 32) : 0;
     const T* fp = vp + (int64_t)kc * 96;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const T fv = __ldcs(fp + 32 * a);
-      f[u][a] = ok ? fv : T(0);
-    }
+    for (int a = 0; a < 3; ++a) f[u][a] = ok ? __ldcs(fp + 32 * a) : T(0);
   }
 }
 

@@ -111,6 +111,9 @@ def test_singular_form_needs_fewer_iterations(gspm_lib):
     (sp, mp, up), (ss, ms, us) = out[True], out[False]
     assert ss["it_mech"] < 0.75 * sp["it_mech"]
     assert ss["it_ms"] < sp["it_ms"]
+    # two different CG iterations stopped at the same relative residual 1e-7: their U and u
+    # differ by the solves' error (up to ~1e-6 of the fields), and four steps from a random m
+    # carry that into m at the 1e-5 level; the bound is the mixed-precision one
     assert _angle(ms, mp) < 1e-4
     assert np.all(us[0] == 0.0) and np.all(up[0] == 0.0)
     assert _relerr(us, up) < 1e-3
