@@ -252,6 +252,28 @@ def cpu_all_cores(cells=ORACLE_CELLS, steps=3):
             "nodes": res[0]["nodes"], "steps": steps}
 
 
+def run_cpu_scale(args):
+    """Check of the oracle's full-size model against a measurement: the oracle timed on the
+    benchmark recipe at --cpu-scale-cells cubes (one warm-up step and --cpu-scale-steps timed
+    steps, one thread), next to the model's prediction for that size from the usual 16,000-node
+    sample (and from the same sample with the measured iteration counts)."""
+    cells = tuple(int(v) for v in args.cpu_scale_cells.split(","))
+    t0 = time.perf_counter()
+    sample = _child_result(cpu_oracle_child())
+    big = _child_result(cpu_oracle_child(steps=args.cpu_scale_steps, warmup=1, cells=cells))
+    t_model, its_model, how = oracle_full_size_model(sample, big["nodes"], cells)
+    t_model_its, _, _ = oracle_full_size_model(sample, big["nodes"], cells, big["it_per_step"])
+    print(json.dumps({"cpu_scale": {
+        "sample": {"nodes": sample["nodes"], "s_per_step": sample["s_per_step"],
+                   "it_per_step": sample["it_per_step"]},
+        "measured": {"nodes": big["nodes"], "cells": list(cells), "steps": big["steps"],
+                     "s_per_step": big["s_per_step"], "it_per_step": big["it_per_step"],
+                     "s_per_iteration": big["s_per_iteration"]},
+        "model": {"s_per_step": t_model, "it_per_step": its_model, "how": how},
+        "model_with_measured_iterations": {"s_per_step": t_model_its},
+        "cores": 1, "wall_s": round(time.perf_counter() - t0, 1)}}), flush=True)
+
+
 # ------------------------------------------------------------------------------------------
 # helpers on contexts
 # ------------------------------------------------------------------------------------------
@@ -986,6 +1008,10 @@ def main():
                     help="run the mixed-precision contract (mixed vs FP64 trajectories) instead")
     ap.add_argument("--contract-cells", default="128,128,32")
     ap.add_argument("--contract-steps", type=int, default=1000)
+    ap.add_argument("--cpu-scale", action="store_true",
+                    help="time the CPU oracle at a larger size and compare with its model")
+    ap.add_argument("--cpu-scale-cells", default="96,96,24")
+    ap.add_argument("--cpu-scale-steps", type=int, default=1)
     ap.add_argument("--dt-sweep", action="store_true",
                     help="run the time-step study on the hexahedral cuboid-defect workload instead")
     ap.add_argument("--sweep-cells", default="64,64,16")
@@ -994,12 +1020,14 @@ def main():
     ap.add_argument("--sweep-rtol", type=float, default=1e-10)
     ap.add_argument("--sweep-skip-paper-form", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and not (args.contract or args.dt_sweep):
+    if args.warmup < 3 and args.impl == "ours" and not (args.contract or args.dt_sweep or args.cpu_scale):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.contract:
         run_contract(args)
     elif args.dt_sweep:
         run_dt_sweep(args)
+    elif args.cpu_scale:
+        run_cpu_scale(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
