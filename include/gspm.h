@@ -372,7 +372,7 @@ GSPM_API int64_t gspm_launch_count(const struct gspm_ctx* ctx);
  * definite and the CG's r.z stays positive; otherwise a diagonal shift s is added before
  * rounding (2^-8 max_i A_ii, doubled until accepted, at most max_i A_ii) and returned in *shift
  * (0 if none was needed; may be NULL).  mesh_load applies this rule to every coarse inverse.
- * The paper has no coarse level; this is part of the build's preconditioner (its Sec. 5 names
+ * The paper has no coarse level; this is part of the library's preconditioner (its Sec. 5 names
  * preconditioning as the next step).  Errors: GSPM_EINVAL (null pointer, n < 1, bf16 not 0/1),
  * GSPM_EMESH (no shift up to max_i A_ii is accepted: A is not positive definite). */
 GSPM_API int gspm_coarse_round(const double* A, int64_t n, int bf16, double* out, double* shift);
@@ -406,16 +406,18 @@ GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights,
                                      int ncomp, double* out, void* stream);
 
 /* ---- learned warm start of the mechanical CG ------------------------------------------- */
-/* A message-passing network over the mesh (the paper has none; this is the build's learned
+/* A message-passing network over the mesh (the paper has none; this is the library's learned
  * initial guess, checked against its own FP64 CPU definition).  Per node, 16 features:
  * m (3), E0(m) in Voigt order / lambda_s (6), u_prev / u_s (3), (u_prev - u_prev2) / u_s (3), 1,
  * with lambda_s = max(|lambda100|, |lambda111|) and u_s = lambda_s * (V(Omega_c)/n)^(1/3).
  * h0 = relu(f W_in + b_in); three layers h_l = relu([h, A h] W_l + b_l) with A the
  * element-message average (A_ij = sum_{e containing i,j} V_e / k over sum_{e containing i} V_e,
  * k the element's vertices; V_e / (16 M_L,i) on tetrahedra); y = h3 W_out + b_out.
- * Prediction x0 = 2 u_prev - u_prev2 + u_s y.  Inference runs on the tensor cores (BF16 weights
- * and activations, FP32 accumulation); training (backward, Adam) in FP32.  CG still runs to the
- * same residual, so the prediction only changes the iteration count.
+ * Prediction x0 = 2 u_prev - u_prev2 + u_s y.  Inference runs on the tcgen05 tensor cores (BF16
+ * weights and activations, FP32 accumulation in tensor memory); a layer whose wait for its
+ * accumulator gives up makes the call (or the step that used the guess) return GSPM_ECUDA.
+ * Training (backward, Adam) runs in FP32.  CG still runs to the same residual, so the
+ * prediction only changes the iteration count.
  * Parameter layout (float32, GSPM_MPNN_PARAMS values): W_in [16][64], b_in [64],
  * {W_l [128][64], b_l [64]} for l = 1..3, W_out [64][3], b_out [3]; all row-major [in][out]. */
 #define GSPM_MPNN_PARAMS 26051

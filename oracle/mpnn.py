@@ -2,7 +2,7 @@
 message-passing network over the tetrahedral mesh, its loss, and one Adam update.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  The paper has no learned component; the
-network is the build's own design and this file is its reference definition.
+network is the library's own design and this file is its reference definition.
 
 Network (hidden width 64, three message-passing layers):
   messages   element message = mean of its 4 vertex features; a node receives the
