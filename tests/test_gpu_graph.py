@@ -150,3 +150,34 @@ def test_graph_loop_stops_at_max_iter(gspm_lib, single):
     _same_stats(sd, sg)
     assert sg["it_mech_last"] == 14 and sg["it_ms_last"] == 14
     assert np.array_equal(d.get_field(gspm_lib.FIELD_M), g.get_field(gspm_lib.FIELD_M))
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_autotuner_times_every_schedule_of_the_cg_product(gspm_lib, single, prec):
+    """The autotuner times each SpMV schedule as the CG loops run it (the product fused with
+    p.Ap) for K^mech, K^ms and the GSPM operators (1 + 2 + 3 right-hand sides), keeps the
+    fastest, and a solve with the chosen schedules reaches the fixed-schedule solution."""
+    mesh, wm, m0 = single
+    g = gspm_lib
+    rtol = 1e-13 if prec == "f64" else 1e-7
+    ctx = g.Context(mesh, synth.fe_like_material(), 1e-12, 0.5, precision=prec,
+                    rtol_gs=rtol, rtol_ms=rtol, rtol_mech=rtol)
+    info = ctx.info()
+    for times, chosen in (("spmv_ms_block", "spmv_schedule_block"),
+                          ("spmv_ms_scalar", "spmv_schedule_scalar"),
+                          ("spmv_ms_gs", "spmv_schedule_gs")):
+        t = np.asarray(info[times])
+        assert t.shape == (4,) and np.all(t > 0.0), (times, t)
+        assert info[chosen] == int(np.argmin(t)), (chosen, t)
+    fixed = _ctx(g, mesh, prec, rtol=rtol)
+    untuned = fixed.info()
+    assert untuned["spmv_schedule_block"] == untuned["spmv_schedule_gs"] == 0
+    assert np.all(np.asarray(untuned["spmv_ms_gs"]) == 0.0)
+    H = np.array([2e4, 0.0, -1e4])
+    for c in (ctx, fixed):
+        c.set_field(g.FIELD_M, m0)
+        c.step(2, H)
+    # FP64: the same solution to rounding; mixed: two summation orders stopped at 1e-7
+    tol = 1e-10 if prec == "f64" else 1e-4
+    a, b = ctx.get_field(g.FIELD_M), fixed.get_field(g.FIELD_M)
+    assert np.abs(a - b).max() < tol
