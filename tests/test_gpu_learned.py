@@ -5,12 +5,13 @@ generates (train_warmstart.generate) on a small sphere-inclusion mesh, then used
 guess of the mechanical CG on trajectories it has not seen, from the same states as the
 previous solution and the extrapolation 2 u_prev - u_prev2 it corrects.  Measured outcome
 (stated in the asserts): training cuts the held-out squared error of the extrapolation in the
-network's target space by a quarter (this small mesh) to a half (the committed weights, trained
-on 0.5M nodes), yet the CG iterations change by 0 to +11 % against the extrapolation and by
-about 1 % against the previous solution: the displacement responds to the change of m across the whole body, which a
-three-layer local network does not see, and the two-level preconditioned CG needs almost as many
-iterations from any of these guesses (the right-hand side changes by most of its norm from one
-step to the next at dt = 5 ps).  The committed weights are evaluated the same way.
+network's target space by a quarter (this small mesh) to two fifths (the committed weights,
+trained on 5000 pairs from 0.5M-node meshes), yet the CG iterations change by 0 to +11 % against
+the extrapolation and by about 1 % against the previous solution: the displacement responds to
+the change of m across the whole body, which a three-layer local network does not see, and the
+two-level preconditioned CG needs almost as many iterations from any of these guesses (the
+right-hand side changes by most of its norm from one step to the next at dt = 5 ps).  The
+committed weights are evaluated the same way.
 """
 import os
 
