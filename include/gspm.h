@@ -415,7 +415,7 @@ GSPM_API int gspm_volume_avg_noalloc(const double* field, const double* weights,
  * k the element's vertices; V_e / (16 M_L,i) on tetrahedra); y = h3 W_out + b_out.
  * Prediction x0 = 2 u_prev - u_prev2 + u_s y.  Inference runs on the tcgen05 tensor cores (BF16
  * weights and activations, FP32 accumulation in tensor memory); a layer whose wait for its
- * accumulator gives up makes the call (or the step that used the guess) return GSPM_ECUDA.
+ * accumulator gives up makes the call (or the step that used the guess) return GSPM_ETIMEOUT.
  * Training (backward, Adam) runs in FP32.  CG still runs to the same residual, so the
  * prediction only changes the iteration count.
  * Parameter layout (float32, GSPM_MPNN_PARAMS values): W_in [16][64], b_in [64],

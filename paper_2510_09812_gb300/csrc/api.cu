@@ -509,7 +509,7 @@ class Engine final : public EngineBase {
     CK(cudaStreamSynchronize(L_.stream));
     if (e) {
       set_error("learned initial guess: a tensor-core layer did not complete within its wait limit");
-      return GSPM_ECUDA;
+      return GSPM_ETIMEOUT;
     }
     return GSPM_OK;
   }
